@@ -1,0 +1,799 @@
+/*
+ * gis_oracle.c -- plain FP64 CPU oracle of the graph-based invariant set (GIS)
+ * hot path (Decardi-Nelson & Liu, "An efficient implementation of graph-based
+ * invariant set algorithm for constrained nonlinear dynamical systems").
+ *
+ * TEST INFRASTRUCTURE. Only the tests, the smoke check and the CPU-baseline /
+ * reference leg of the benchmark load this library. The CUDA library never
+ * links, calls or includes anything from here, and this file includes nothing
+ * of it: the two share no code.
+ *
+ * What it computes, step by step, in the paper's order:
+ *   - the cell covering of X by closed boxes (Sec. 2.1);
+ *   - the one-step map f(x,u) of Eq. 1, for continuous models one RK4 period
+ *     of s classic RK4 substeps;
+ *   - a k^n inclusive lattice of sample points per cell, propagated for every
+ *     sampled control value, and its image bounding box, standing in for the
+ *     image F(B_i) of Eq. 2-3 (the paper leaves the image method open, Sec. 2.4);
+ *   - the symbolic image edges B_i -> B_j iff B_j meets the image (Def. 1,
+ *     closed cells), found by a descent of the subdivision tree (the R*-tree
+ *     query of Sec. 2.4 answers the same question);
+ *   - the pruning fixed point (Sec. 2.3, Def. 2-5, Prop. 1): rule OUTER keeps a
+ *     cell iff some edge leads to a kept cell, rule INNER keeps a cell iff some
+ *     control maps it inside X with every image cell kept;
+ *   - boundary classification (Sec. 3.1.1, Alg. 1, Remark 1) in its exact form:
+ *     a kept cell is a boundary cell iff its closed box touches the faces of X
+ *     or a removed cell;
+ *   - subdivision of the boundary cells into 2^n children (Sec. 2.1, Sec. 3.1).
+ *
+ * Compiled with -O2 -ffp-contract=off and without fast-math, so every
+ * floating-point expression rounds after each operation, in C's left-to-right
+ * evaluation order. Transcendentals are the C library's exp/sin/cos.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_MAXN 4
+#define ORC_MAXM 4
+#define ORC_NPARAM 32
+#define ORC_MAXLEVEL 16
+
+enum { ORC_LINMAP = 0, ORC_VDP = 1, ORC_CSTR_DL = 2, ORC_CARTPOLE = 3, ORC_CSTR_PAPER = 4 };
+enum { ORC_INNER = 0, ORC_OUTER = 1 };
+enum { ORC_DEAD = 0, ORC_ALIVE = 1, ORC_SPLIT = 2 };
+enum { ORC_F_INX = 1, ORC_F_TOUCH_DEAD = 2, ORC_F_NONFINITE = 4 };
+enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2, ORC_ESTATE = -3 };
+
+typedef struct {
+    int32_t dyn;        /* dynamics id */
+    int32_t n;          /* state dimension, 1..4 */
+    int32_t m;          /* control dimension, 1..4 */
+    int32_t substeps;   /* RK4 substeps per sampling period; 0: f is a discrete map */
+    double dt;          /* sampling period */
+    double p[ORC_NPARAM];
+    double lo[ORC_MAXN], hi[ORC_MAXN]; /* X = prod [lo_d, hi_d] */
+    int32_t n0[ORC_MAXN]; /* root cells per dimension */
+    int32_t k;          /* samples per dimension (k = 1: the cell centre) */
+    int32_t rule;       /* ORC_INNER or ORC_OUTER */
+} orc_problem;
+
+typedef struct {
+    int32_t level;
+    int32_t state;
+    int32_t idx[ORC_MAXN];
+    int64_t child;      /* first of 2^n consecutive children, -1 for a leaf */
+} orc_node;
+
+typedef struct {
+    orc_problem P;
+    double *u;          /* n_u x m control values */
+    int32_t n_u;
+    orc_node *nodes;
+    int64_t n_nodes, cap_nodes;
+    int32_t max_level;  /* finest level present in the tree */
+    int32_t have_graph, have_prune;
+    /* current covering: live leaves in canonical order (level, idx lexicographic) */
+    int64_t n_live;
+    int64_t *live;      /* slot -> node */
+    int64_t *slot_of;   /* node -> slot, -1 if not live */
+    /* graph of the current covering: pair p = slot * n_u + control */
+    int64_t *off;       /* n_live * n_u + 1 */
+    int32_t *tgt;       /* targets as live slots, ascending within a pair */
+    uint8_t *flag;
+    double *bbox;       /* per pair: ymin[0..n-1], ymax[0..n-1] */
+    uint8_t *kept;      /* per slot, after prune */
+    uint8_t *bnd;       /* per slot, after classify */
+} orc_solver;
+
+static int orc_threads = 1;
+
+int orc_set_threads(int t)
+{
+#ifdef _OPENMP
+    if (t < 1) t = omp_get_max_threads();
+    orc_threads = t;
+#else
+    (void)t;
+    orc_threads = 1;
+#endif
+    return orc_threads;
+}
+
+/* ------------------------------------------------------------------------
+ * Dynamics: the right-hand sides g(x,u) of the continuous models and the
+ * linear discrete map. The models are those of the workloads the method is
+ * run on; the dimensional CSTR is Eq. 4 with the parameters of Table 2.
+ * ---------------------------------------------------------------------- */
+static void orc_linmap(const orc_problem *P, const double *x, const double *u, double *y);
+
+static void orc_rhs_eval(const orc_problem *P, const double *x, const double *u, double *dx)
+{
+    const double *p = P->p;
+    switch (P->dyn) {
+    case ORC_LINMAP:
+        orc_linmap(P, x, u, dx);
+        break;
+    case ORC_VDP: {
+        /* controlled Van der Pol: x1' = x2, x2' = -x1 + mu (1 - x1^2) x2 + u */
+        double mu = p[0];
+        dx[0] = x[1];
+        dx[1] = -x[0] + mu * (1.0 - x[0] * x[0]) * x[1] + u[0];
+        break;
+    }
+    case ORC_CSTR_DL: {
+        /* dimensionless exothermic CSTR:
+         * r = Da (1 - x1) exp(x2 / (1 + x2/gamma))
+         * x1' = -x1 + r,  x2' = -x2 + B r - beta (x2 - u)            */
+        double Da = p[0], B = p[1], beta = p[2], gamma = p[3];
+        double e = exp(x[1] / (1.0 + x[1] / gamma));
+        double r = Da * (1.0 - x[0]) * e;
+        dx[0] = -x[0] + r;
+        dx[1] = -x[1] + B * r - beta * (x[1] - u[0]);
+        break;
+    }
+    case ORC_CARTPOLE: {
+        /* frictionless cart-pole, state (p, v, theta, omega), l = half pole
+         * length, force u on the cart (Barto, Sutton & Anderson 1983 form) */
+        double mc = p[0], mp = p[1], l = p[2], g = p[3];
+        double s = sin(x[2]), c = cos(x[2]);
+        double tot = mc + mp;
+        double pml = mp * l;
+        double temp = (u[0] + pml * x[3] * x[3] * s) / tot;
+        double thacc = (g * s - c * temp) / (l * (4.0 / 3.0 - mp * c * c / tot));
+        double xacc = temp - pml * thacc * c / tot;
+        dx[0] = x[1];
+        dx[1] = xacc;
+        dx[2] = x[3];
+        dx[3] = thacc;
+        break;
+    }
+    case ORC_CSTR_PAPER: {
+        /* Eq. 4, parameters of Table 2: q, V, c_Af, T_f, E/R, k0, -dH, UA, c_p, rho;
+         * state (c_A, T), control T_c */
+        double q = p[0], V = p[1], cAf = p[2], Tf = p[3], ER = p[4], k0 = p[5];
+        double mdH = p[6], UA = p[7], cp = p[8], rho = p[9];
+        double cA = x[0], T = x[1], Tc = u[0];
+        double rate = k0 * exp(-ER / T) * cA;
+        dx[0] = (q / V) * (cAf - cA) - rate;
+        dx[1] = (q / V) * (Tf - T) + (mdH / (rho * cp)) * rate + (UA / (V * rho * cp)) * (Tc - T);
+        break;
+    }
+    default:
+        for (int d = 0; d < P->n; d++) dx[d] = NAN;
+    }
+}
+
+/* Linear model A x + B u, A row-major n x n in p[0..n*n-1], B row-major n x m
+ * following it; each row accumulated left to right. With substeps = 0 it is the
+ * discrete map x+ = A x + B u, otherwise the right-hand side x' = A x + B u. */
+static void orc_linmap(const orc_problem *P, const double *x, const double *u, double *y)
+{
+    int n = P->n, m = P->m;
+    const double *A = P->p, *B = P->p + n * n;
+    for (int i = 0; i < n; i++) {
+        double acc = 0.0;
+        for (int j = 0; j < n; j++) acc = acc + A[i * n + j] * x[j];
+        for (int j = 0; j < m; j++) acc = acc + B[i * m + j] * u[j];
+        y[i] = acc;
+    }
+}
+
+/* One sampling period of Eq. 1: x+ = f(x,u). Continuous models: s classic RK4
+ * substeps of h = dt/s (weights 1/6, 2/6, 2/6, 1/6). */
+static void orc_step_eval(const orc_problem *P, const double *x0, const double *u, double *y)
+{
+    int n = P->n;
+    if (P->substeps == 0) {
+        if (P->dyn == ORC_LINMAP) orc_linmap(P, x0, u, y);
+        else for (int d = 0; d < n; d++) y[d] = NAN;
+        return;
+    }
+    double x[ORC_MAXN], k1[ORC_MAXN], k2[ORC_MAXN], k3[ORC_MAXN], k4[ORC_MAXN], xt[ORC_MAXN];
+    double h = P->dt / (double)P->substeps;
+    double hh = h * 0.5;
+    double h6 = h / 6.0;
+    for (int d = 0; d < n; d++) x[d] = x0[d];
+    for (int s = 0; s < P->substeps; s++) {
+        orc_rhs_eval(P, x, u, k1);
+        for (int d = 0; d < n; d++) xt[d] = x[d] + hh * k1[d];
+        orc_rhs_eval(P, xt, u, k2);
+        for (int d = 0; d < n; d++) xt[d] = x[d] + hh * k2[d];
+        orc_rhs_eval(P, xt, u, k3);
+        for (int d = 0; d < n; d++) xt[d] = x[d] + h * k3[d];
+        orc_rhs_eval(P, xt, u, k4);
+        for (int d = 0; d < n; d++) x[d] = x[d] + h6 * (k1[d] + 2.0 * k2[d] + 2.0 * k3[d] + k4[d]);
+    }
+    for (int d = 0; d < n; d++) y[d] = x[d];
+}
+
+/* ------------------------------------------------------------------------
+ * Grid geometry (Sec. 2.1): a level-L cell is a closed box of width
+ * w_L = (hi - lo) / (n0 * 2^L) per dimension, lower corner lo + idx * w_L.
+ * ---------------------------------------------------------------------- */
+static double orc_width(const orc_problem *P, int L, int d)
+{
+    return (P->hi[d] - P->lo[d]) / (double)((int64_t)P->n0[d] << L);
+}
+
+static int64_t orc_cells(const orc_problem *P, int L, int d)
+{
+    return (int64_t)P->n0[d] << L;
+}
+
+/* Sample lattice of one cell: k points per dimension, x_j = lo_cell + w (j/(k-1)),
+ * corners included; k = 1 is the cell centre. Sample s has digit j_d = (s / k^d) % k. */
+static void orc_sample(const orc_problem *P, int L, const int32_t *idx, int64_t s, double *x)
+{
+    int64_t r = s;
+    for (int d = 0; d < P->n; d++) {
+        int64_t j = r % P->k;
+        r /= P->k;
+        double w = orc_width(P, L, d);
+        double base = P->lo[d] + (double)idx[d] * w;
+        double frac = (P->k == 1) ? 0.5 : (double)j / (double)(P->k - 1);
+        x[d] = base + w * frac;
+    }
+}
+
+static int64_t orc_num_samples(const orc_problem *P)
+{
+    int64_t S = 1;
+    for (int d = 0; d < P->n; d++) S *= P->k;
+    return S;
+}
+
+/* Image bounding box of (cell, control): per-dimension min / max over the
+ * propagated samples. Returns 0 if every image coordinate is finite, else 1. */
+static int orc_image_bbox(const orc_problem *P, int L, const int32_t *idx, const double *u,
+                          double *ymin, double *ymax)
+{
+    int n = P->n, nonfinite = 0;
+    int64_t S = orc_num_samples(P);
+    for (int d = 0; d < n; d++) { ymin[d] = INFINITY; ymax[d] = -INFINITY; }
+    for (int64_t s = 0; s < S; s++) {
+        double x[ORC_MAXN], y[ORC_MAXN];
+        orc_sample(P, L, idx, s, x);
+        orc_step_eval(P, x, u, y);
+        for (int d = 0; d < n; d++) {
+            if (!isfinite(y[d])) { nonfinite = 1; continue; }
+            if (y[d] < ymin[d]) ymin[d] = y[d];
+            if (y[d] > ymax[d]) ymax[d] = y[d];
+        }
+    }
+    return nonfinite;
+}
+
+/* Index range of the level-L cells whose closed box meets the closed interval
+ * [ymin, ymax] along dimension d: with t = (y - lo)/w_L the cell i spans
+ * [i, i+1] in t, so it meets iff ceil(t_min) - 1 <= i <= floor(t_max); the
+ * range is then intersected with the cells of X. Empty if out[0] > out[1]. */
+static void orc_level_range(const orc_problem *P, int L, int d, double ymin, double ymax, int64_t *out)
+{
+    double w = orc_width(P, L, d);
+    double tmin = (ymin - P->lo[d]) / w;
+    double tmax = (ymax - P->lo[d]) / w;
+    double a = ceil(tmin) - 1.0;
+    double b = floor(tmax);
+    double last = (double)(orc_cells(P, L, d) - 1);
+    if (a < 0.0) a = 0.0;
+    if (b > last) b = last;
+    if (a > b) { out[0] = 1; out[1] = 0; return; }
+    out[0] = (int64_t)a;
+    out[1] = (int64_t)b;
+}
+
+/* ------------------------------------------------------------------------
+ * The covering as a subdivision tree: root cells are nodes 0..R-1 (row-major,
+ * dimension 0 most significant); a split node owns 2^n consecutive children
+ * with idx_child = 2 idx + bit_d.
+ * ---------------------------------------------------------------------- */
+static int orc_push_node(orc_solver *S, int level, const int32_t *idx, int state)
+{
+    if (S->n_nodes == S->cap_nodes) {
+        int64_t nc = S->cap_nodes ? 2 * S->cap_nodes : 1024;
+        orc_node *nn = (orc_node *)realloc(S->nodes, (size_t)nc * sizeof(orc_node));
+        if (!nn) return ORC_ENOMEM;
+        S->nodes = nn;
+        S->cap_nodes = nc;
+    }
+    orc_node *nd = &S->nodes[S->n_nodes++];
+    memset(nd, 0, sizeof(*nd));
+    nd->level = level;
+    nd->state = state;
+    for (int d = 0; d < S->P.n; d++) nd->idx[d] = idx[d];
+    nd->child = -1;
+    if (level > S->max_level) S->max_level = level;
+    return ORC_OK;
+}
+
+typedef struct {
+    int64_t rng[ORC_MAXLEVEL + 1][ORC_MAXN][2];
+} orc_ranges;
+
+typedef struct {
+    int32_t *out;       /* NULL: count only */
+    int64_t count;
+    int touch_dead;
+} orc_acc;
+
+static void orc_visit(const orc_solver *S, int64_t node, const orc_ranges *R, orc_acc *acc)
+{
+    const orc_node *nd = &S->nodes[node];
+    int L = nd->level;
+    for (int d = 0; d < S->P.n; d++)
+        if (nd->idx[d] < R->rng[L][d][0] || nd->idx[d] > R->rng[L][d][1]) return;
+    if (nd->state == ORC_SPLIT) {
+        int64_t nc = (int64_t)1 << S->P.n;
+        for (int64_t c = 0; c < nc; c++) orc_visit(S, nd->child + c, R, acc);
+    } else if (nd->state == ORC_ALIVE) {
+        if (acc->out) acc->out[acc->count] = (int32_t)S->slot_of[node];
+        acc->count++;
+    } else {
+        acc->touch_dead = 1;
+    }
+}
+
+/* Visit every leaf meeting the per-level ranges: loop over the root cells in
+ * the level-0 range, descend into split nodes. */
+static void orc_descend(const orc_solver *S, const orc_ranges *R, orc_acc *acc)
+{
+    int n = S->P.n;
+    int64_t lo[ORC_MAXN], hi[ORC_MAXN], cur[ORC_MAXN];
+    for (int d = 0; d < n; d++) {
+        lo[d] = R->rng[0][d][0];
+        hi[d] = R->rng[0][d][1];
+        if (lo[d] > hi[d]) return;
+        cur[d] = lo[d];
+    }
+    for (;;) {
+        int64_t r = 0;
+        for (int d = 0; d < n; d++) r = r * S->P.n0[d] + cur[d];
+        orc_visit(S, r, R, acc);
+        int d = n - 1;
+        while (d >= 0 && cur[d] == hi[d]) { cur[d] = lo[d]; d--; }
+        if (d < 0) break;
+        cur[d]++;
+    }
+}
+
+static int orc_cmp_nodes_ctx_n;
+static const orc_node *orc_cmp_nodes_ctx;
+
+static int orc_cmp_slots(const void *a, const void *b)
+{
+    const orc_node *x = &orc_cmp_nodes_ctx[*(const int64_t *)a];
+    const orc_node *y = &orc_cmp_nodes_ctx[*(const int64_t *)b];
+    if (x->level != y->level) return x->level < y->level ? -1 : 1;
+    for (int d = 0; d < orc_cmp_nodes_ctx_n; d++)
+        if (x->idx[d] != y->idx[d]) return x->idx[d] < y->idx[d] ? -1 : 1;
+    return 0;
+}
+
+static int orc_cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+static void orc_free_graph(orc_solver *S)
+{
+    free(S->live); S->live = NULL;
+    free(S->slot_of); S->slot_of = NULL;
+    free(S->off); S->off = NULL;
+    free(S->tgt); S->tgt = NULL;
+    free(S->flag); S->flag = NULL;
+    free(S->bbox); S->bbox = NULL;
+    free(S->kept); S->kept = NULL;
+    free(S->bnd); S->bnd = NULL;
+    S->n_live = 0;
+    S->have_graph = S->have_prune = 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Public API (ctypes).
+ * ---------------------------------------------------------------------- */
+int orc_rhs(const orc_problem *P, const double *x, const double *u, double *dx)
+{
+    if (!P || P->n < 1 || P->n > ORC_MAXN) return ORC_EINVAL;
+    orc_rhs_eval(P, x, u, dx);
+    return ORC_OK;
+}
+
+int orc_step(const orc_problem *P, const double *x, const double *u, double *y)
+{
+    if (!P || P->n < 1 || P->n > ORC_MAXN) return ORC_EINVAL;
+    orc_step_eval(P, x, u, y);
+    return ORC_OK;
+}
+
+int orc_cell_samples(const orc_problem *P, int32_t level, const int32_t *idx, double *out)
+{
+    int64_t S = orc_num_samples(P);
+    for (int64_t s = 0; s < S; s++) orc_sample(P, level, idx, s, out + s * P->n);
+    return ORC_OK;
+}
+
+int orc_pair_bbox(const orc_problem *P, int32_t level, const int32_t *idx, const double *u,
+                  double *ymin, double *ymax)
+{
+    return orc_image_bbox(P, level, idx, u, ymin, ymax);
+}
+
+int orc_range(const orc_problem *P, int32_t level, int32_t d, double ymin, double ymax, int64_t *out)
+{
+    orc_level_range(P, level, d, ymin, ymax, out);
+    return ORC_OK;
+}
+
+static int orc_valid(const orc_problem *P)
+{
+    if (P->n < 1 || P->n > ORC_MAXN || P->m < 1 || P->m > ORC_MAXM || P->k < 1) return 0;
+    if (P->substeps < 0) return 0;
+    for (int d = 0; d < P->n; d++)
+        if (P->n0[d] < 1 || !(P->hi[d] > P->lo[d])) return 0;
+    return 1;
+}
+
+orc_solver *orc_create(const orc_problem *P, const double *u, int32_t n_u)
+{
+    if (!P || !orc_valid(P) || n_u < 1 || !u) return NULL;
+    orc_solver *S = (orc_solver *)calloc(1, sizeof(orc_solver));
+    if (!S) return NULL;
+    S->P = *P;
+    S->n_u = n_u;
+    S->u = (double *)malloc((size_t)n_u * P->m * sizeof(double));
+    if (!S->u) { free(S); return NULL; }
+    memcpy(S->u, u, (size_t)n_u * P->m * sizeof(double));
+    int n = P->n;
+    int64_t R = 1;
+    for (int d = 0; d < n; d++) R *= P->n0[d];
+    for (int64_t r = 0; r < R; r++) {
+        int32_t idx[ORC_MAXN] = {0};
+        int64_t q = r;
+        for (int d = n - 1; d >= 0; d--) { idx[d] = (int32_t)(q % P->n0[d]); q /= P->n0[d]; }
+        if (orc_push_node(S, 0, idx, ORC_ALIVE) != ORC_OK) { free(S->u); free(S->nodes); free(S); return NULL; }
+    }
+    return S;
+}
+
+void orc_destroy(orc_solver *S)
+{
+    if (!S) return;
+    orc_free_graph(S);
+    free(S->nodes);
+    free(S->u);
+    free(S);
+}
+
+static void orc_pair_ranges(const orc_solver *S, const double *ymin, const double *ymax, orc_ranges *R)
+{
+    for (int L = 0; L <= S->max_level; L++)
+        for (int d = 0; d < S->P.n; d++)
+            orc_level_range(&S->P, L, d, ymin[d], ymax[d], R->rng[L][d]);
+}
+
+/* Symbolic image of the current covering (Def. 1): per (live cell, control)
+ * the image box, the in-X flag, and every live leaf meeting the box. */
+int orc_build_graph(orc_solver *S)
+{
+    if (!S) return ORC_EINVAL;
+    orc_free_graph(S);
+    int n = S->P.n, nu = S->n_u;
+    int64_t nl = 0;
+    for (int64_t i = 0; i < S->n_nodes; i++) nl += S->nodes[i].state == ORC_ALIVE;
+    S->live = (int64_t *)malloc((size_t)(nl ? nl : 1) * sizeof(int64_t));
+    S->slot_of = (int64_t *)malloc((size_t)S->n_nodes * sizeof(int64_t));
+    if (!S->live || !S->slot_of) return ORC_ENOMEM;
+    nl = 0;
+    for (int64_t i = 0; i < S->n_nodes; i++)
+        if (S->nodes[i].state == ORC_ALIVE) S->live[nl++] = i;
+    orc_cmp_nodes_ctx = S->nodes;
+    orc_cmp_nodes_ctx_n = n;
+    qsort(S->live, (size_t)nl, sizeof(int64_t), orc_cmp_slots);
+    for (int64_t i = 0; i < S->n_nodes; i++) S->slot_of[i] = -1;
+    for (int64_t s = 0; s < nl; s++) S->slot_of[S->live[s]] = s;
+    S->n_live = nl;
+
+    int64_t P = nl * nu;
+    S->off = (int64_t *)calloc((size_t)P + 1, sizeof(int64_t));
+    S->flag = (uint8_t *)calloc((size_t)(P ? P : 1), 1);
+    S->bbox = (double *)malloc((size_t)(P ? P : 1) * 2 * n * sizeof(double));
+    int64_t *cnt = (int64_t *)calloc((size_t)(P ? P : 1), sizeof(int64_t));
+    if (!S->off || !S->flag || !S->bbox || !cnt) { free(cnt); return ORC_ENOMEM; }
+
+    /* pass 1: image box, flags and target count of every pair */
+    #pragma omp parallel for schedule(dynamic, 64) num_threads(orc_threads)
+    for (int64_t p = 0; p < P; p++) {
+        const orc_node *nd = &S->nodes[S->live[p / nu]];
+        const double *u = S->u + (p % nu) * S->P.m;
+        double *ymin = S->bbox + p * 2 * n, *ymax = ymin + n;
+        int nonfinite = orc_image_bbox(&S->P, nd->level, nd->idx, u, ymin, ymax);
+        uint8_t f = 0;
+        if (nonfinite) {
+            f = ORC_F_NONFINITE;
+            cnt[p] = 0;
+        } else {
+            int inx = 1;
+            for (int d = 0; d < n; d++)
+                if (!(ymin[d] >= S->P.lo[d] && ymax[d] <= S->P.hi[d])) inx = 0;
+            if (inx) f |= ORC_F_INX;
+            orc_ranges R;
+            orc_pair_ranges(S, ymin, ymax, &R);
+            orc_acc acc = {NULL, 0, 0};
+            orc_descend(S, &R, &acc);
+            if (acc.touch_dead) f |= ORC_F_TOUCH_DEAD;
+            cnt[p] = acc.count;
+        }
+        S->flag[p] = f;
+    }
+    for (int64_t p = 0; p < P; p++) S->off[p + 1] = S->off[p] + cnt[p];
+    free(cnt);
+    int64_t E = S->off[P];
+    S->tgt = (int32_t *)malloc((size_t)(E ? E : 1) * sizeof(int32_t));
+    if (!S->tgt) return ORC_ENOMEM;
+
+    /* pass 2: the targets, ascending */
+    #pragma omp parallel for schedule(dynamic, 64) num_threads(orc_threads)
+    for (int64_t p = 0; p < P; p++) {
+        if (S->flag[p] & ORC_F_NONFINITE) continue;
+        const double *ymin = S->bbox + p * 2 * n, *ymax = ymin + n;
+        orc_ranges R;
+        orc_pair_ranges(S, ymin, ymax, &R);
+        orc_acc acc = {S->tgt + S->off[p], 0, 0};
+        orc_descend(S, &R, &acc);
+        qsort(S->tgt + S->off[p], (size_t)acc.count, sizeof(int32_t), orc_cmp_i32);
+    }
+    S->have_graph = 1;
+    return ORC_OK;
+}
+
+/* Greatest fixed point of the pruning rule on an explicit graph (Sec. 2.3).
+ *   OUTER: keep(i) <=> exists a control u and a target j of (i,u) with keep(j)
+ *          (repeated removal of out-degree-0 vertices, Def. 3-5).
+ *   INNER: keep(i) <=> exists u with (i,u) inside X, touching no removed
+ *          cell, and keep(j) for every target j of (i,u).
+ * Both operators are monotone, so the greatest fixed point is unique. It is
+ * reached by chaotic iteration: every cell starts kept; a cell is re-examined
+ * whenever one of its successors is removed, and removed when no control is
+ * viable any more. */
+static int orc_viable_pair(const int64_t *off, const int32_t *tgt, const uint8_t *flag,
+                           const uint8_t *kept, int64_t p, int rule)
+{
+    if (rule == ORC_OUTER) {
+        for (int64_t e = off[p]; e < off[p + 1]; e++)
+            if (kept[tgt[e]]) return 1;
+        return 0;
+    }
+    if (!(flag[p] & ORC_F_INX) || (flag[p] & (ORC_F_TOUCH_DEAD | ORC_F_NONFINITE))) return 0;
+    for (int64_t e = off[p]; e < off[p + 1]; e++)
+        if (!kept[tgt[e]]) return 0;
+    return 1;
+}
+
+int orc_prune_graph(int64_t n_cells, int32_t n_u, const int64_t *off, const int32_t *tgt,
+                    const uint8_t *flag, int32_t rule, uint8_t *kept, int64_t *n_kept)
+{
+    if (n_cells < 0 || n_u < 1) return ORC_EINVAL;
+    int64_t P = n_cells * n_u, E = off[P];
+    /* predecessors of every cell */
+    int64_t *poff = (int64_t *)calloc((size_t)n_cells + 1, sizeof(int64_t));
+    int64_t *pred = (int64_t *)malloc((size_t)(E ? E : 1) * sizeof(int64_t));
+    int64_t *queue = (int64_t *)malloc((size_t)(n_cells ? n_cells : 1) * sizeof(int64_t));
+    uint8_t *inq = (uint8_t *)malloc((size_t)(n_cells ? n_cells : 1));
+    if (!poff || !pred || !queue || !inq) { free(poff); free(pred); free(queue); free(inq); return ORC_ENOMEM; }
+    for (int64_t e = 0; e < E; e++) poff[tgt[e] + 1]++;
+    for (int64_t i = 0; i < n_cells; i++) poff[i + 1] += poff[i];
+    int64_t *fill = (int64_t *)malloc((size_t)(n_cells ? n_cells : 1) * sizeof(int64_t));
+    if (!fill) { free(poff); free(pred); free(queue); free(inq); return ORC_ENOMEM; }
+    for (int64_t i = 0; i < n_cells; i++) fill[i] = poff[i];
+    for (int64_t p = 0; p < P; p++)
+        for (int64_t e = off[p]; e < off[p + 1]; e++) pred[fill[tgt[e]]++] = p / n_u;
+    free(fill);
+
+    for (int64_t i = 0; i < n_cells; i++) { kept[i] = 1; queue[i] = i; inq[i] = 1; }
+    int64_t head = 0, size = n_cells;
+    while (size > 0) {
+        int64_t i = queue[head];
+        head = (head + 1) % (n_cells ? n_cells : 1);
+        size--;
+        inq[i] = 0;
+        if (!kept[i]) continue;
+        int viable = 0;
+        for (int32_t u = 0; u < n_u && !viable; u++)
+            viable = orc_viable_pair(off, tgt, flag, kept, i * n_u + u, rule);
+        if (viable) continue;
+        kept[i] = 0;
+        for (int64_t e = poff[i]; e < poff[i + 1]; e++) {
+            int64_t j = pred[e];
+            if (kept[j] && !inq[j]) {
+                queue[(head + size) % n_cells] = j;
+                size++;
+                inq[j] = 1;
+            }
+        }
+    }
+    int64_t nk = 0;
+    for (int64_t i = 0; i < n_cells; i++) nk += kept[i];
+    if (n_kept) *n_kept = nk;
+    free(poff); free(pred); free(queue); free(inq);
+    return ORC_OK;
+}
+
+int orc_prune(orc_solver *S, int64_t *n_kept)
+{
+    if (!S || !S->have_graph) return ORC_ESTATE;
+    free(S->kept);
+    S->kept = (uint8_t *)malloc((size_t)(S->n_live ? S->n_live : 1));
+    if (!S->kept) return ORC_ENOMEM;
+    int rc = orc_prune_graph(S->n_live, S->n_u, S->off, S->tgt, S->flag, S->P.rule, S->kept, n_kept);
+    if (rc == ORC_OK) S->have_prune = 1;
+    return rc;
+}
+
+/* Replace the prune result (tests build designed coverings with it). */
+int orc_set_kept(orc_solver *S, const uint8_t *kept)
+{
+    if (!S || !S->have_graph) return ORC_ESTATE;
+    if (!S->kept) S->kept = (uint8_t *)malloc((size_t)(S->n_live ? S->n_live : 1));
+    if (!S->kept) return ORC_ENOMEM;
+    memcpy(S->kept, kept, (size_t)S->n_live);
+    S->have_prune = 1;
+    return ORC_OK;
+}
+
+/* Exact boundary rule (Sec. 3.1.1, Alg. 1 with Remark 1's edge points, as the
+ * enlargement delta goes to 0): a kept cell is a boundary cell iff its closed
+ * box touches a face of X, or some leaf whose closed box meets it is removed.
+ * Neighbour ranges are exact integer arithmetic: a level-L' cell j meets the
+ * level-L cell i iff ceil(idx_i / 2^(L-L')) - 1 <= j <= floor((idx_i+1) / 2^(L-L'))
+ * for L' <= L, and idx_i 2^(L'-L) - 1 <= j <= (idx_i+1) 2^(L'-L) for L' > L. */
+static int orc_is_boundary(const orc_solver *S, const orc_node *nd)
+{
+    int n = S->P.n, L = nd->level;
+    for (int d = 0; d < n; d++)
+        if (nd->idx[d] == 0 || nd->idx[d] == orc_cells(&S->P, L, d) - 1) return 1;
+    orc_ranges R;
+    for (int Lp = 0; Lp <= S->max_level; Lp++) {
+        for (int d = 0; d < n; d++) {
+            int64_t a, b, i = nd->idx[d];
+            if (Lp <= L) {
+                int64_t s = (int64_t)1 << (L - Lp);
+                a = (i + s - 1) / s - 1;   /* ceil(i/s) - 1, i >= 0 */
+                b = (i + 1) / s;           /* floor((i+1)/s) */
+            } else {
+                int64_t s = (int64_t)1 << (Lp - L);
+                a = i * s - 1;
+                b = (i + 1) * s;
+            }
+            int64_t last = orc_cells(&S->P, Lp, d) - 1;
+            if (a < 0) a = 0;
+            if (b > last) b = last;
+            R.rng[Lp][d][0] = a;
+            R.rng[Lp][d][1] = b;
+        }
+    }
+    orc_acc acc = {NULL, 0, 0};
+    orc_descend(S, &R, &acc);
+    return acc.touch_dead;
+}
+
+/* Remove the cells the prune dropped, classify the kept ones. */
+int orc_classify(orc_solver *S, uint8_t *bnd_out, int64_t *n_bnd)
+{
+    if (!S || !S->have_prune) return ORC_ESTATE;
+    for (int64_t s = 0; s < S->n_live; s++)
+        if (!S->kept[s]) S->nodes[S->live[s]].state = ORC_DEAD;
+    free(S->bnd);
+    S->bnd = (uint8_t *)calloc((size_t)(S->n_live ? S->n_live : 1), 1);
+    if (!S->bnd) return ORC_ENOMEM;
+    int64_t nb = 0;
+    for (int64_t s = 0; s < S->n_live; s++) {
+        if (!S->kept[s]) continue;
+        S->bnd[s] = (uint8_t)orc_is_boundary(S, &S->nodes[S->live[s]]);
+        nb += S->bnd[s];
+    }
+    if (bnd_out) memcpy(bnd_out, S->bnd, (size_t)S->n_live);
+    if (n_bnd) *n_bnd = nb;
+    return ORC_OK;
+}
+
+/* Split every boundary cell into its 2^n children (Sec. 2.1, Sec. 3.1): the
+ * union of the covering is unchanged, removed cells stay removed. */
+int orc_subdivide(orc_solver *S, int64_t *n_split)
+{
+    int64_t nb = 0;
+    int rc = orc_classify(S, NULL, &nb);
+    if (rc != ORC_OK) return rc;
+    int n = S->P.n;
+    int64_t nc = (int64_t)1 << n;
+    for (int64_t s = 0; s < S->n_live; s++) {
+        if (!S->bnd[s]) continue;
+        int64_t parent = S->live[s];
+        int64_t first = S->n_nodes;
+        for (int64_t c = 0; c < nc; c++) {
+            int32_t idx[ORC_MAXN];
+            int L = S->nodes[parent].level;
+            for (int d = 0; d < n; d++) idx[d] = 2 * S->nodes[parent].idx[d] + (int32_t)((c >> (n - 1 - d)) & 1);
+            rc = orc_push_node(S, L + 1, idx, ORC_ALIVE);
+            if (rc != ORC_OK) return rc;
+        }
+        S->nodes[parent].state = ORC_SPLIT;
+        S->nodes[parent].child = first;
+    }
+    if (n_split) *n_split = nb;
+    S->have_graph = S->have_prune = 0;
+    return ORC_OK;
+}
+
+/* The loop of Sec. 2 / Sec. 3: per level build the graph, prune it, and (below
+ * the last level) split the boundary cells. Ends with the pruned graph of the
+ * final covering. */
+int orc_solve(orc_solver *S, int32_t levels)
+{
+    if (!S || levels < 0 || levels > ORC_MAXLEVEL) return ORC_EINVAL;
+    for (int L = 0; L <= levels; L++) {
+        int rc = orc_build_graph(S);
+        if (rc != ORC_OK) return rc;
+        rc = orc_prune(S, NULL);
+        if (rc != ORC_OK) return rc;
+        if (L < levels) {
+            rc = orc_subdivide(S, NULL);
+            if (rc != ORC_OK) return rc;
+        }
+    }
+    return ORC_OK;
+}
+
+/* ---- getters ---------------------------------------------------------- */
+int64_t orc_num_live(const orc_solver *S) { return S ? S->n_live : -1; }
+int64_t orc_num_edges(const orc_solver *S) { return (S && S->have_graph) ? S->off[S->n_live * S->n_u] : -1; }
+int64_t orc_num_nodes(const orc_solver *S) { return S ? S->n_nodes : -1; }
+int32_t orc_max_level(const orc_solver *S) { return S ? S->max_level : -1; }
+
+/* live cells in canonical order: level[n_live], idx[n_live x 4] */
+int orc_get_live(const orc_solver *S, int32_t *level, int32_t *idx)
+{
+    if (!S || !S->live) return ORC_ESTATE;
+    for (int64_t s = 0; s < S->n_live; s++) {
+        const orc_node *nd = &S->nodes[S->live[s]];
+        level[s] = nd->level;
+        for (int d = 0; d < ORC_MAXN; d++) idx[s * ORC_MAXN + d] = d < S->P.n ? nd->idx[d] : 0;
+    }
+    return ORC_OK;
+}
+
+int orc_get_graph(const orc_solver *S, int64_t *off, int32_t *tgt, uint8_t *flag, double *bbox)
+{
+    if (!S || !S->have_graph) return ORC_ESTATE;
+    int64_t P = S->n_live * S->n_u;
+    if (off) memcpy(off, S->off, (size_t)(P + 1) * sizeof(int64_t));
+    if (tgt) memcpy(tgt, S->tgt, (size_t)S->off[P] * sizeof(int32_t));
+    if (flag) memcpy(flag, S->flag, (size_t)P);
+    if (bbox) memcpy(bbox, S->bbox, (size_t)P * 2 * S->P.n * sizeof(double));
+    return ORC_OK;
+}
+
+int orc_get_kept(const orc_solver *S, uint8_t *kept)
+{
+    if (!S || !S->have_prune) return ORC_ESTATE;
+    memcpy(kept, S->kept, (size_t)S->n_live);
+    return ORC_OK;
+}
+
+/* all tree nodes: level, state, idx[4], child */
+int orc_get_nodes(const orc_solver *S, int32_t *level, int32_t *state, int32_t *idx, int64_t *child)
+{
+    if (!S) return ORC_EINVAL;
+    for (int64_t i = 0; i < S->n_nodes; i++) {
+        level[i] = S->nodes[i].level;
+        state[i] = S->nodes[i].state;
+        for (int d = 0; d < ORC_MAXN; d++) idx[i * ORC_MAXN + d] = S->nodes[i].idx[d];
+        child[i] = S->nodes[i].child;
+    }
+    return ORC_OK;
+}
