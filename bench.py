@@ -1,0 +1,312 @@
+"""Benchmark of the GIS hot path on GB300.
+
+One step = one whole solve of the dimensionless-CSTR workload (256^2 root
+cells, 4x4 samples, 11 controls, RK4 4 x 0.0125, three levels of boundary
+subdivision, FP32 propagation with FP64 recheck): leaf materialisation,
+propagation, image boxes, recheck, count / scan / fill, transpose, prune,
+boundary classification and subdivision, through the C ABI of libgis.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gis|reference]
+
+Prints one JSON line (rank 0). The metric is graph-construction throughput:
+live cells whose graph was built, summed over the levels of the solve, per
+second of solve time. --impl reference times the FP64 CPU oracle on the same
+workload and metric on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "graph-construction cells/s"
+UNIT = "cells/s"
+FP32_LANES_PER_SM = 128
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gis", choices=["gis", "reference"])
+    ap.add_argument("--workload", default="cstr_256")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _workload(name):
+    from paper_2202_06111_gb300 import workloads as W
+    if name == "cstr_256":
+        p = W.cstr_256()
+        p["band"] = 1e-2
+        return p
+    if name == "cartpole_48":
+        return dict(W.cartpole_48(), band=1e-4)
+    if name == "vdp_64":
+        return W.vdp_64()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def _config(prob, name):
+    return {"workload": name, "system": prob["dyn"], "root_cells": prob["n0"], "samples_per_dim": prob["k"],
+            "controls": len(prob["controls"]), "levels": prob["levels"], "rule": prob.get("rule", "inner"),
+            "precision": "fp32 propagation, fp64 recheck" if prob.get("precision") == "fp32" else "fp64",
+            "band_cells": prob.get("band"), "l2": "flushed (512 MiB write) before every timed step"}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 5 + i and "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(prob, seconds_cap=30.0):
+    """The oracle as it stands, all host threads, on the full workload (one solve)."""
+    import oracle
+    oracle.build()
+    threads = oracle.set_threads(0)
+    t = time.perf_counter()
+    s = oracle.Solver(prob)
+    cells = 0
+    for L in range(prob["levels"] + 1):
+        s.build_graph()
+        cells += s.num_live()
+        s.prune()
+        if L < prob["levels"]:
+            s.subdivide()
+    dt = time.perf_counter() - t
+    return {"value": cells / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"one full FP64 oracle solve of the workload ({cells} cells built, {dt:.2f} s)"}, dt
+
+
+def run_reference(a, prob):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    threads = oracle.set_threads(0)
+    times, cells = [], 0
+    for i in range(a.warmup + a.steps):
+        t = time.perf_counter()
+        s = oracle.Solver(prob)
+        c = 0
+        for L in range(prob["levels"] + 1):
+            s.build_graph()
+            c += s.num_live()
+            s.prune()
+            if L < prob["levels"]:
+                s.subdivide()
+        dt = time.perf_counter() - t
+        if i >= a.warmup:
+            times.append(dt)
+            cells = c
+    ms = 1e3 * sum(times) / len(times)
+    value = cells / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": _config(prob, a.workload),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "one full FP64 oracle solve of the workload per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gis(a, prob):
+    import torch
+    from paper_2202_06111_gb300 import build, gis
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    build.build()
+    gis.load()
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def solve_once(timing=1):
+        ctx = gis.Context(prob, stream=stream.cuda_stream, timing=timing)
+        return ctx
+
+    # warm-up (also builds the memory pool and any cached shapes)
+    for _ in range(a.warmup):
+        with torch.cuda.stream(stream):
+            c = solve_once()
+            c.solve()
+            c.close()
+    torch.cuda.synchronize()
+
+    # timed: device time of gis_solve, CUDA events on the library's stream
+    ctxs = []
+    with torch.cuda.stream(stream):
+        for _ in range(a.steps):
+            ctxs.append(solve_once())
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = Clocks(dev) if rank == 0 else None
+    per_step, stats = [], []
+    torch.cuda.synchronize()
+    for c in ctxs:
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c.solve()
+        e1.record(stream)
+        e1.synchronize()
+        per_step.append(e0.elapsed_time(e1))
+        stats.append(c.stats())
+    torch.cuda.synchronize()
+    clocks = clk.stop() if clk else None
+    total_ms = sum(per_step)
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    for c in ctxs:
+        c.close()
+    cells = sum(s["cum_cells_built"] for s in stats)
+    edges = sum(s["cum_edges"] for s in stats)
+    launches = sum(s["cum_launches"] for s in stats)
+    value = cells * ws / (total_ms / 1e3)
+
+    # end to end through the C ABI: create from host arrays, solve, read the kept cells
+    e2e_times, d2h = [], 0
+    h2d = len(prob["controls"]) * 8 * prob.get("m", 1) + 8 * (32 + 4) + 8 * 8 + 4 * 5
+    for i in range(max(3, a.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        with torch.cuda.stream(stream):
+            c = gis.Context(prob, stream=stream.cuda_stream)
+            c.solve()
+            lv, fl, idx = c.cells()
+        dt = time.perf_counter() - t
+        d2h = lv.size * 24
+        c.close()
+        e2e_times.append(dt)
+    e2e_value = (cells / len(stats)) / statistics.mean(e2e_times)
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.barrier()
+        return
+    peaks, src = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    agg = {k: sum(s[k] for s in stats) for k in stats[0] if isinstance(stats[0][k], (int, float))}
+    phases = {"prop": ("ms_prop", "prop_flops", "alu"), "count": ("ms_count", "count_bytes", "hbm"),
+              "fill": ("ms_fill", "fill_bytes", "hbm"), "transpose": ("ms_transpose", "transpose_bytes", "hbm"),
+              "prune": ("ms_prune", "prune_bytes", "hbm")}
+    dom = max(phases, key=lambda k: agg[phases[k][0]])
+    ms_k, work_k, bound = phases[dom]
+    sec = agg[ms_k] / 1e3
+    if bound == "alu":
+        achieved = agg[work_k] / sec / 1e12
+        peak, unit = fp32_peak, "TFLOP/s"
+    else:
+        achieved = agg[work_k] / sec / 1e9
+        peak, unit = float(peaks["hbm_gbs"]), "GB/s"
+    by_phase = {}
+    for k, (m, w, b) in phases.items():
+        s_ = agg[m] / 1e3
+        if s_ > 0:
+            ach = agg[w] / s_ / (1e12 if b == "alu" else 1e9)
+            pk = fp32_peak if b == "alu" else float(peaks["hbm_gbs"])
+            by_phase[k] = {"ms_per_step": agg[m] / len(stats), "achieved": ach, "frac": ach / pk, "bound": b}
+    for k in ("ms_bin", "ms_recheck", "ms_scan", "ms_classify", "ms_split", "ms_other"):
+        by_phase[k[3:]] = {"ms_per_step": agg[k] / len(stats)}
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{src} ({'FP32 FMA: SMs x 128 lanes x 2 x max SM clock' if bound == 'alu' else 'HBM copy'})",
+                "phases": by_phase}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": total_ms / len(per_step), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(prob, a.workload),
+            "edges_per_s": edges * ws / (total_ms / 1e3), "solve_ms": {"mean": statistics.mean(per_step),
+                                                                       "p50": statistics.median(per_step),
+                                                                       "p99": max(per_step)},
+            "cells_per_step": cells / len(stats), "edges_per_step": edges / len(stats),
+            "recheck_pairs_per_step": agg["cum_recheck"] / len(stats),
+            "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": 1e3 * statistics.mean(e2e_times)}}
+    if ws == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"], _ = cpu_baseline(prob)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+
+
+def main():
+    a = _args()
+    prob = _workload(a.workload)
+    if a.impl == "reference":
+        run_reference(a, prob)
+    else:
+        run_gis(a, prob)
+
+
+if __name__ == "__main__":
+    main()

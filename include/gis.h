@@ -1,0 +1,243 @@
+/*
+ * gis.h -- C ABI of libgis: the graph-construction hot path of the
+ * graph-based invariant set (GIS) algorithm on one GB300 (sm_103a).
+ *
+ * The method (Decardi-Nelson & Liu, "An efficient implementation of
+ * graph-based invariant set algorithm for constrained nonlinear dynamical
+ * systems") approximates the largest control invariant set of x+ = f(x,u)
+ * with x in the box X and u in a finite set of control values (Eq. 1, Eq. 2-3):
+ *   1. cover X with closed cells (Sec. 2.1);
+ *   2. for every (cell, control) pair propagate a k^n lattice of samples
+ *      through f (an RK4 period of a continuous model, or a discrete map),
+ *      take the image bounding box, and join the cell to every cell the box
+ *      meets: the symbolic image (Def. 1, Sec. 2.2, Sec. 3.2);
+ *   3. prune the graph to its greatest fixed point (Sec. 2.3, Prop. 1);
+ *   4. split the boundary cells of the kept set into 2^n children
+ *      (Sec. 3.1, Alg. 1 in its exact form) and repeat.
+ *
+ * Conventions for every function below:
+ *   - returns a gis_status (GIS_OK = 0); never throws, exits or prints;
+ *   - on error the message is available from gis_last_error(ctx);
+ *   - all pointers named host_* or documented "host" are host memory owned
+ *     by the caller; the library copies what it keeps;
+ *   - device memory is owned by the context and freed by gis_destroy;
+ *   - work is issued on the context's CUDA stream (the one passed to
+ *     gis_create, NULL = the legacy default stream); functions that return
+ *     counts synchronise that stream.
+ * Every computation runs in the library's CUDA kernels; there is no CPU
+ * fallback: without a usable GPU gis_create fails with GIS_ECUDA.
+ */
+#ifndef GIS_H
+#define GIS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t gis_status;
+#define GIS_OK            0
+#define GIS_EINVAL       -1   /* bad argument or problem definition            */
+#define GIS_ENOMEM       -2   /* device or host allocation failed / over limit  */
+#define GIS_ECUDA        -3   /* CUDA runtime error (no device, launch failure) */
+#define GIS_ETIMEOUT     -4   /* a bounded device wait or round limit ran out   */
+#define GIS_EUNSUPPORTED -5   /* valid request this build does not implement    */
+#define GIS_ECANCELLED   -6   /* request cancelled before completion            */
+#define GIS_EBOUNDS      -7   /* caller buffer too small (size returned)        */
+#define GIS_ESTATE       -8   /* call out of order (e.g. prune before build)    */
+
+#define GIS_MAX_DIM      4    /* state dimension n <= 4, control dimension m <= 4 */
+#define GIS_MAX_LEVEL    15   /* subdivision depth                               */
+#define GIS_NPARAM       32
+
+/* Dynamics ids. f(x,u) for the continuous models is one sampling period dt of
+ * `substeps` classic RK4 steps of x' = g(x,u) (h = dt/substeps); substeps = 0
+ * makes GIS_DYN_LINMAP the discrete map itself.                                */
+enum {
+    GIS_DYN_LINMAP = 0,     /* g = A x + B u; params: A (n x n row-major), B (n x m)       */
+    GIS_DYN_VDP = 1,        /* x1' = x2, x2' = -x1 + mu (1 - x1^2) x2 + u; params: mu      */
+    GIS_DYN_CSTR_DL = 2,    /* r = Da (1-x1) exp(x2/(1+x2/gamma)); x1' = -x1 + r,
+                               x2' = -x2 + B r - beta (x2 - u); params: Da, B, beta, gamma */
+    GIS_DYN_CARTPOLE = 3,   /* state (p, v, theta, omega), frictionless, l = half length;
+                               params: m_cart, m_pole, l, g                                */
+    GIS_DYN_CSTR_PAPER = 4  /* Eq. 4 of the paper, state (c_A, T), u = T_c; params (Table 2):
+                               q, V, c_Af, T_f, E/R, k0, -dH, UA, c_p, rho                  */
+};
+
+/* Pruning rules (Sec. 2.3). OUTER: keep a cell iff some edge of some control
+ * leads to a kept cell (non-leaving cells, Def. 3 read as every cell with an
+ * infinite admissible path). INNER: keep a cell iff some control maps its
+ * image box inside X, touching no removed cell, with every image cell kept. */
+enum { GIS_RULE_INNER = 0, GIS_RULE_OUTER = 1 };
+
+/* Precision of the propagation. FP64_PLAIN: every sample in FP64. FP32_RECHECK:
+ * samples in FP32; every image-box extreme within `band` finest-level cell
+ * widths of a grid line is recomputed in FP64 on the GPU, so the edge sets
+ * equal those of the FP64 computation whenever the FP32 error of a sample is
+ * below band/2 cell widths.                                                    */
+enum { GIS_FP64_PLAIN = 0, GIS_FP32_RECHECK = 1 };
+
+typedef struct {
+    int32_t dyn_id;         /* GIS_DYN_*                                          */
+    int32_t n;              /* state dimension 1..4                               */
+    int32_t m;              /* control dimension 1..4                             */
+    int32_t substeps;       /* RK4 substeps per period; 0 = discrete map          */
+    double dt;              /* sampling period                                    */
+    double params[GIS_NPARAM];
+} gis_dynamics;
+
+typedef struct {
+    double lo[GIS_MAX_DIM], hi[GIS_MAX_DIM]; /* X = prod [lo_d, hi_d], hi > lo    */
+    int32_t root_cells[GIS_MAX_DIM];         /* n0_d >= 1 root cells per dimension */
+    int32_t k_samples;      /* samples per dimension: x_j = lo_cell + w j/(k-1),
+                               corners included; k = 1 is the cell centre          */
+} gis_grid;
+
+typedef struct {
+    int32_t n_controls;     /* >= 1                                               */
+    const double *u;        /* host, n_controls x m row-major; copied at create    */
+} gis_controls;
+
+typedef struct {
+    int32_t rule;           /* GIS_RULE_*                                         */
+    int32_t precision;      /* GIS_FP64_PLAIN | GIS_FP32_RECHECK                   */
+    double band;            /* FP32 recheck band, finest-level cell widths (> 0)   */
+    int32_t lanes_per_pair; /* propagation lanes per pair 1,2,4,8,16,32; 0 = auto  */
+    int32_t timing;         /* 1: record per-kernel CUDA-event times into stats    */
+    int64_t max_device_bytes; /* 0 = no limit; else allocations beyond -> ENOMEM   */
+    int64_t round_limit;    /* prune rounds before GIS_ETIMEOUT; 0 = 1<<30         */
+} gis_options;
+
+/* One live cell: box = prod [lo + idx w_level, lo + (idx+1) w_level],
+ * w_level = (hi - lo) / (n0 2^level).                                         */
+typedef struct {
+    int32_t level;
+    int32_t flags;          /* bit 0: kept by the last prune; bit 1: boundary      */
+    int32_t idx[GIS_MAX_DIM];
+} gis_cell;
+
+#define GIS_CELL_KEPT     1
+#define GIS_CELL_BOUNDARY 2
+
+/* Pair flags of the graph (one byte per (cell, control) pair). */
+#define GIS_PAIR_INX        1  /* image box inside X (closed)                      */
+#define GIS_PAIR_TOUCH_DEAD 2  /* image box meets a removed cell                   */
+#define GIS_PAIR_NONFINITE  4  /* some sample's image is not finite                */
+
+typedef struct {
+    int32_t finest_level;   /* finest level present in the subdivision tree       */
+    int32_t level;          /* levels completed (subdivisions done)               */
+    int64_t n_nodes;        /* tree nodes (leaves alive, removed and split)       */
+    int64_t n_live;         /* live cells of the current covering                 */
+    int64_t n_pairs;        /* n_live x n_controls                                */
+    int64_t n_edges;        /* edges of the current graph                         */
+    int64_t n_kept;         /* kept by the last prune                             */
+    int64_t n_split;        /* split by the last subdivision                      */
+    int64_t n_new_pairs;    /* pairs propagated by the last build                 */
+    int64_t n_recheck;      /* pairs with an FP64 recheck at the last build        */
+    int32_t prune_rounds;   /* frontier rounds of the last prune                  */
+    int32_t lanes_per_pair; /* propagation shape in use                           */
+    /* cumulative over the context lifetime */
+    int64_t cum_cells_built, cum_pairs_propagated, cum_edges, cum_recheck;
+    int64_t cum_prop_launches;
+    /* cumulative kernel time (ms, CUDA events on the context stream; timing = 1) */
+    double ms_prop, ms_bin, ms_recheck, ms_count, ms_scan, ms_fill, ms_transpose,
+           ms_prune, ms_classify, ms_split, ms_other;
+    /* cumulative algorithmic work of the propagation kernels */
+    double prop_flops;      /* FP32 (or FP64) arithmetic operations, as counted
+                               from the model expressions                         */
+    double graph_bytes;     /* algorithmic bytes of count + fill + transpose       */
+    double prune_bytes;     /* algorithmic bytes of the prune                      */
+    double count_bytes, fill_bytes, transpose_bytes; /* the parts of graph_bytes   */
+    int64_t cum_launches;   /* kernel launches issued by the library              */
+} gis_stats;
+
+typedef struct gis_ctx gis_ctx;
+
+/* Default options: INNER rule, FP32_RECHECK, band 1e-2, auto lanes, no timing. */
+void gis_default_options(gis_options *out);
+
+/* Create a context on the current CUDA device, with the covering of root
+ * cells. `stream` is a cudaStream_t (NULL: legacy default stream).
+ * Errors: EINVAL (bad sizes / ids / box), ECUDA (no device), ENOMEM.          */
+gis_status gis_create(gis_ctx **out, const gis_dynamics *dyn, const gis_grid *grid,
+                      const gis_controls *controls, const gis_options *opt, void *stream);
+
+/* Steps 1-2 on the current covering: propagate the new cells, bin the image
+ * boxes, recheck near-line extremes in FP64, count / scan / fill the CSR
+ * graph over (cell, control) pairs and its transpose.                        */
+gis_status gis_build_graph(gis_ctx *ctx);
+
+/* Step 3: greatest fixed point of the pruning rule on the current graph.
+ * n_kept / n_rounds may be NULL. ESTATE without a graph; ETIMEOUT if the
+ * round limit is reached.                                                      */
+gis_status gis_prune(gis_ctx *ctx, int64_t *n_kept, int32_t *n_rounds);
+
+/* Step 4: classify the kept cells and split every boundary cell into 2^n
+ * children; removed cells stay removed. ESTATE if the graph is not pruned.   */
+gis_status gis_subdivide(gis_ctx *ctx, int64_t *n_split);
+
+/* The whole loop: `levels` times build / prune / subdivide, then a final
+ * build / prune. Synchronises the stream at the end.                          */
+gis_status gis_solve(gis_ctx *ctx, int32_t levels);
+
+/* The live cells of the current covering (after a prune: with kept flags).
+ * out = NULL or cap too small: *n_total is set and GIS_EBOUNDS returned
+ * (GIS_OK for out = NULL).                                                     */
+gis_status gis_get_cells(gis_ctx *ctx, gis_cell *out, int64_t cap, int64_t *n_total);
+
+/* The current graph in the order of gis_get_cells: pair p = cell * n_controls + u,
+ * off[n_pairs + 1] (int64), tgt[n_edges] (cell index), flag[n_pairs]. Any
+ * output may be NULL; sizes are always returned. EBOUNDS if cap_edges < n_edges. */
+gis_status gis_get_graph(gis_ctx *ctx, int64_t *off, int32_t *tgt, uint8_t *flag,
+                         int64_t cap_edges, int64_t *n_pairs, int64_t *n_edges);
+
+/* Image boxes of the current pairs: box32 [n_pairs x 2n] FP32 extremes
+ * (ymin_0..ymin_{n-1}, ymax_0..), box64 the same in FP64 where `exact` has the
+ * extreme's bit set (bit e for extreme e), else the FP32 value widened.
+ * Any output may be NULL. For testing and calibration.                       */
+gis_status gis_get_boxes(gis_ctx *ctx, float *box32, double *box64, uint8_t *exact, int64_t cap_pairs);
+
+gis_status gis_get_stats(const gis_ctx *ctx, gis_stats *out);
+
+/* Message of the last failing call on ctx (owned by ctx, valid until the next
+ * call); a static string when ctx is NULL.                                    */
+const char *gis_last_error(const gis_ctx *ctx);
+
+void gis_destroy(gis_ctx *ctx);   /* NULL-safe */
+
+/* ---- batched: many independent problems in one set of launches ----------- */
+typedef struct {
+    gis_dynamics dyn;
+    gis_grid grid;
+    gis_controls controls;
+    int32_t levels;         /* subdivision levels of this problem                 */
+    int32_t rule;           /* GIS_RULE_*                                         */
+    int32_t precision;
+    double band;
+} gis_request;
+
+typedef struct {
+    gis_status status;
+    int32_t levels_done;
+    int64_t n_kept;         /* kept cells at the end                              */
+    int64_t n_cells;        /* live cells at the end                              */
+    int64_t n_edges_total;  /* edges built over all levels                        */
+    int64_t cells_built;    /* live cells graph-built over all levels             */
+    gis_cell *cells;        /* caller buffer for the kept cells, or NULL          */
+    int64_t cells_cap;
+} gis_result;
+
+/* Solve `n` requests together: every phase of every level runs as one launch
+ * over the union of all requests' cells (requests at different levels
+ * proceed together; finished ones drop out). res[i].cells (if not NULL)
+ * receives up to cells_cap kept cells of request i. `opt` supplies timing,
+ * lanes and limits (rule / precision / band come from each request).        */
+gis_status gis_batch_solve(const gis_request *reqs, int32_t n, gis_result *res,
+                           const gis_options *opt, void *stream, gis_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GIS_H */

@@ -1,0 +1,110 @@
+// gis_kernels.cuh -- host-side launch interface of the GIS kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gis_device.cuh"
+
+namespace gis {
+
+void note_launch();              // every kernel launch of the library is counted
+long long launches_total();
+
+struct WorkList {                // ranges of one kernel launch, device copy + block count
+    const Range *d_ranges = nullptr;
+    int n_ranges = 0;
+    int64_t n_blocks = 0;
+};
+
+struct RecheckQueue {            // per dynamics: (global pair, inst | mask << 16)
+    int2 *items;
+    int32_t *count;              // device counter
+};
+
+// FP32 propagation with `lanes` per pair (1..32), FP64 propagation (plain).
+cudaError_t launch_prop32(int dyn, int n, int lanes, const InstDesc *D, const WorkList &w, cudaStream_t st);
+cudaError_t launch_prop64(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st);
+int prop_pairs_per_block(int lanes);
+// binning: decisions at the finest level, band check, recheck queue
+cudaError_t launch_bin(int n, const InstDesc *D, const WorkList &w, int32_t *rng, uint8_t *pflag,
+                       int2 *queue_items, int32_t *queue_counts, int64_t queue_cap, cudaStream_t st);
+// FP64 recheck of flagged pairs: phase 0 candidates (per dynamics kind),
+// phase 1 FP64 samples (per dynamics kind), phase 2 finalize (per n).
+struct RecheckArgs {
+    const InstDesc *D;
+    const int2 *items;           // (global pair, inst | mask << 16)
+    const int32_t *count;        // device count of items
+    int64_t qcap;
+    long long *mnk, *mxk;        // [item x n] ordered keys of the FP64 extremes
+    int32_t *bad;                // [item] an FP64 sample was not finite
+    int2 *cand;                  // (item, sample)
+    int32_t *ncand;
+    int64_t ccap;
+    int32_t *rng;
+    uint8_t *pflag;
+};
+cudaError_t launch_recheck(int phase, int dyn, int n, const RecheckArgs &a, cudaStream_t st);
+// count (fill = false) / fill (fill = true) by tree descent
+cudaError_t launch_edges(bool fill, int n, const InstDesc *D, const WorkList &w, const int32_t *rng,
+                         uint8_t *pflag, int32_t *cnt, const int64_t *off, int32_t *tgt,
+                         int32_t *err, cudaStream_t st);
+// exclusive scan of n int32 (or int64) values into int64 out[n + 1]; scratch >= scan_scratch_bytes(n)
+size_t scan_scratch_bytes(int64_t n);
+cudaError_t launch_scan_i32(const int32_t *in, int64_t *out, int64_t n, void *scratch, cudaStream_t st);
+cudaError_t launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, void *scratch, cudaStream_t st);
+cudaError_t launch_scan_u8(const uint8_t *in, int64_t *out, int64_t n, void *scratch, cudaStream_t st);
+cudaError_t launch_inst_totals(const int64_t *pscan, const int64_t *be, int n, int64_t *out, cudaStream_t st);
+cudaError_t launch_init_roots(uint8_t *lvl, uint8_t *state, int32_t *const *idx, int32_t *child, int32_t *live,
+                              int n, const int32_t *n0, int64_t R, cudaStream_t st);
+// slot gather: node -> global slot, pair -> slot
+cudaError_t launch_gather(const InstDesc *D, const WorkList &wslots, int32_t *pair_slot, cudaStream_t st);
+// transpose
+cudaError_t launch_indeg(const int32_t *tgt, int64_t E, int32_t *rcnt, cudaStream_t st);
+cudaError_t launch_rscatter(const int64_t *off, const int32_t *tgt, int64_t P, int64_t *rcur,
+                            int32_t *rsrc, cudaStream_t st);
+// prune
+cudaError_t launch_prune_init(int rule, const InstDesc *D, const WorkList &wslots, const int64_t *off,
+                              const uint8_t *pflag, int32_t *pstate, int32_t *ncnt, uint8_t *alive,
+                              int32_t *frontier0, uint32_t *sizes, cudaStream_t st);
+struct PruneArgs {
+    int rule;
+    const int64_t *roff;
+    const int32_t *rsrc;
+    const int32_t *pair_slot;
+    int32_t *pstate;             // INNER: dead flag; OUTER: live-target count
+    int32_t *ncnt;               // viable pairs per slot
+    uint8_t *alive;
+    int32_t *frontier[2];
+    uint32_t *sizes;             // [3] rotating frontier sizes
+    uint32_t *bar;               // grid barrier counter
+    int32_t *err;                // 0 ok, else GIS_ETIMEOUT
+    int32_t *rounds;             // rounds executed
+    unsigned long long *scanned; // reverse edges walked
+    int64_t round_limit;
+    int64_t spin_limit;
+};
+cudaError_t launch_prune(const PruneArgs &a, int64_t n_slots, cudaStream_t st);
+// mark removed, classify boundary, split
+cudaError_t launch_mark_dead(const InstDesc *D, const WorkList &wslots, const uint8_t *alive, cudaStream_t st);
+cudaError_t launch_classify(int n, const InstDesc *D, const WorkList &wslots, const uint8_t *alive,
+                            uint8_t *bnd, int64_t *packed, int32_t *inst_maxlvl, cudaStream_t st);
+struct SplitInst {               // per instance, for the split kernel
+    int32_t *new_live;
+    int32_t n_nodes;             // first child id
+    int32_t n_keep;              // kept, unsplit cells of this instance
+};
+cudaError_t launch_split(int n, const InstDesc *D, const WorkList &wslots, const uint8_t *alive,
+                         const uint8_t *bnd, const int64_t *packed_scan, const SplitInst *si, cudaStream_t st);
+// per-slot output of cells: level, flags, idx
+cudaError_t launch_export_cells(const InstDesc *D, const WorkList &wslots, const uint8_t *alive,
+                                const uint8_t *bnd, gis_cell *out, int only_kept, const int64_t *kept_scan,
+                                cudaStream_t st);
+cudaError_t launch_count_kept(const WorkList &wslots, const uint8_t *alive, int64_t *per_inst, cudaStream_t st);
+// graph export: tgt (global slot) -> instance-local cell index
+cudaError_t launch_localize(const int32_t *tgt, int64_t E, int32_t base, int32_t *out, cudaStream_t st);
+// boxes export
+cudaError_t launch_export_boxes(int n, const InstDesc *D, const WorkList &wpairs, float *box32, double *box64,
+                                uint8_t *exact, cudaStream_t st);
+
+}  // namespace gis

@@ -1,0 +1,553 @@
+// gis_prop.cu -- propagation kernels: per (cell, control) pair, push the k^n
+// sample lattice of the cell through one sampling period of the model and
+// reduce the image bounding box (Eq. 1-3, the image F(B_i) of Def. 1 and the
+// batched one-step maps of Sec. 3.2).
+//
+//  k_prop32   FP32 samples, `G` lanes per pair, group-shuffle min / max
+//  k_prop64   FP64 samples in the defining operation order (plain FP64 mode)
+//  k_recheck  FP64 recomputation of the extremes that lie within the band of a
+//             grid line: only the samples whose FP32 image lies within the
+//             candidate window of the FP32 extreme can hold the FP64 extreme
+#include <cfloat>
+
+#include "gis_kernels.cuh"
+
+namespace gis {
+
+constexpr int PROP_THREADS = 256;
+
+// FP32 lower corner of the cell, widened from the FP64 definition lo + idx w.
+template <int N>
+__device__ __forceinline__ void cell_base32(const InstDesc &I, int node, int L, float *base, float *w)
+{
+#pragma unroll
+    for (int d = 0; d < N; d++) {
+        double b = I.lo[d] + (double)I.idx[d][node] * I.w64[L][d];
+        base[d] = (float)b;
+        w[d] = I.w32[L][d];
+    }
+}
+
+template <class DY, int G>
+__global__ void __launch_bounds__(PROP_THREADS) k_prop32(const InstDesc *__restrict__ D,
+                                                         const Range *__restrict__ R, int nr)
+{
+    constexpr int N = DY::N;
+    constexpr int PPB = PROP_THREADS / G;
+    __shared__ int s_r;
+    __shared__ float s_p[GIS_NPARAM];
+    __shared__ float s_frac[MAXS * N];
+    if (threadIdx.x == 0) s_r = find_range(R, nr, blockIdx.x);
+    __syncthreads();
+    const Range rg = R[s_r];
+    const InstDesc &I = D[rg.inst];
+    const int S = I.S, k = I.k;
+    if (threadIdx.x < GIS_NPARAM) s_p[threadIdx.x] = I.p32[threadIdx.x];
+    for (int t = threadIdx.x; t < S; t += PROP_THREADS) {
+        int r = t;
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            s_frac[t * N + d] = I.frac32[r % k];
+            r /= k;
+        }
+    }
+    __syncthreads();
+    const M32 M{s_p, I.m, I.substeps, I.h32, I.hh32, I.h6_32};
+    const int64_t local = (int64_t)(blockIdx.x - rg.block_start) * PPB + threadIdx.x / G;
+    const bool valid = local < rg.count;
+    const int lane = threadIdx.x & (G - 1);
+    float mn[N], mx[N];
+#pragma unroll
+    for (int d = 0; d < N; d++) { mn[d] = FLT_MAX; mx[d] = -FLT_MAX; }
+    int bad = 0;
+    int64_t q = 0;
+    if (valid) {
+        const int64_t lp = rg.first + local - I.pair_base;
+        const int ls = (int)(lp / I.nu);
+        const int u = (int)(lp - (int64_t)ls * I.nu);
+        const int node = I.live[ls];
+        const int L = I.lvl[node];
+        float base[N], w[N];
+        cell_base32<N>(I, node, L, base, w);
+        float uu[MAXN];
+        for (int j = 0; j < I.m; j++) uu[j] = I.u32[u * I.m + j];
+        q = (int64_t)node * I.nu + u;
+        for (int s = lane; s < S; s += G) {
+            float x[N], y[N];
+#pragma unroll
+            for (int d = 0; d < N; d++) x[d] = fmaf(w[d], s_frac[s * N + d], base[d]);
+            step32<DY>(M, x, uu, y);
+#pragma unroll
+            for (int d = 0; d < N; d++) {
+                bad |= !(fabsf(y[d]) <= FLT_MAX);
+                mn[d] = fminf(mn[d], y[d]);
+                mx[d] = fmaxf(mx[d], y[d]);
+            }
+        }
+    }
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            mn[d] = fminf(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], off, G));
+            mx[d] = fmaxf(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], off, G));
+        }
+        bad |= __shfl_xor_sync(0xffffffffu, bad, off, G);
+    }
+    if (valid) {
+        for (int e = lane; e < 2 * N; e += G) {
+            float v = 0.0f;
+#pragma unroll
+            for (int d = 0; d < N; d++) {
+                if (e == d) v = mn[d];
+                if (e == N + d) v = mx[d];
+            }
+            I.box32[q * 2 * N + e] = v;
+        }
+        if (lane == 0) I.exact[q] = bad ? EX_NF32 : 0;
+    }
+}
+
+template <class DY>
+__global__ void __launch_bounds__(PROP_THREADS) k_prop64(const InstDesc *__restrict__ D,
+                                                         const Range *__restrict__ R, int nr)
+{
+    constexpr int N = DY::N;
+    __shared__ int s_r;
+    __shared__ double s_p[GIS_NPARAM];
+    if (threadIdx.x == 0) s_r = find_range(R, nr, blockIdx.x);
+    __syncthreads();
+    const Range rg = R[s_r];
+    const InstDesc &I = D[rg.inst];
+    if (threadIdx.x < GIS_NPARAM) s_p[threadIdx.x] = I.p64[threadIdx.x];
+    __syncthreads();
+    const M64 M{s_p, I.m, I.substeps, I.h64, I.hh64, I.h6_64};
+    const int64_t local = (int64_t)(blockIdx.x - rg.block_start) * PROP_THREADS + threadIdx.x;
+    if (local >= rg.count) return;
+    const int64_t lp = rg.first + local - I.pair_base;
+    const int ls = (int)(lp / I.nu);
+    const int u = (int)(lp - (int64_t)ls * I.nu);
+    const int node = I.live[ls];
+    const int L = I.lvl[node];
+    int32_t idx[N];
+#pragma unroll
+    for (int d = 0; d < N; d++) idx[d] = I.idx[d][node];
+    double uu[MAXN];
+    for (int j = 0; j < I.m; j++) uu[j] = I.u64[u * I.m + j];
+    double mn[N], mx[N];
+#pragma unroll
+    for (int d = 0; d < N; d++) { mn[d] = INFINITY; mx[d] = -INFINITY; }
+    int bad = 0;
+    for (int s = 0; s < I.S; s++) {
+        double x[N], y[N];
+        sample64<N>(I, L, idx, s, x);
+        step64<DY>(M, x, uu, y);
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            if (!isfinite(y[d])) { bad = 1; continue; }
+            mn[d] = y[d] < mn[d] ? y[d] : mn[d];
+            mx[d] = y[d] > mx[d] ? y[d] : mx[d];
+        }
+    }
+    const int64_t q = (int64_t)node * I.nu + u;
+#pragma unroll
+    for (int d = 0; d < N; d++) {
+        I.box64[q * 2 * N + d] = mn[d];
+        I.box64[q * 2 * N + N + d] = mx[d];
+        I.box32[q * 2 * N + d] = (float)mn[d];
+        I.box32[q * 2 * N + N + d] = (float)mx[d];
+    }
+    I.exact[q] = (uint16_t)(((1u << (2 * N)) - 1u) | (bad ? EX_NF64 : 0));
+}
+
+// ---------------------------------------------------------------------------
+// Decisions at the finest level Lf: for a lower extreme c = ceil(t), for an
+// upper extreme f = floor(t), t = (y - lo) / w_Lf, clamped to [0, Nf+1] /
+// [-1, Nf]; coarser levels follow by exact integer shifts.
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void decide_exact(const InstDesc &I, int e, double v, int32_t &out, bool &inx)
+{
+    const int d = e % N;
+    const double t = __ddiv_rn(__dsub_rn(v, I.lo[d]), I.w64[I.Lf][d]);
+    const double Nf = (double)((int64_t)I.n0[d] << I.Lf);
+    if (e < N) {
+        out = (int32_t)fmin(fmax(ceil(t), 0.0), Nf + 1.0);
+        inx = inx && (v >= I.lo[d]);
+    } else {
+        out = (int32_t)fmin(fmax(floor(t), -1.0), Nf);
+        inx = inx && (v <= I.hi[d]);
+    }
+}
+
+// FP32 decision; false if the extreme lies within the band of a grid line of
+// X (t in (-1/2, Nf + 1/2)) and must be recomputed in FP64.
+template <int N>
+__device__ __forceinline__ bool decide_approx(const InstDesc &I, int e, float v, int32_t &out, bool &inx)
+{
+    const int d = e % N;
+    const float t = (v - I.lo32[d]) * I.invwf32[d];
+    const float Nf = (float)(I.n0[d] << I.Lf);
+    if (t > -0.5f && t < Nf + 0.5f && fabsf(t - rintf(t)) < I.band_t[d]) return false;
+    if (e < N) {
+        out = (int32_t)fminf(fmaxf(ceilf(t), 0.0f), Nf + 1.0f);
+        inx = inx && (t >= 0.0f);
+    } else {
+        out = (int32_t)fminf(fmaxf(floorf(t), -1.0f), Nf);
+        inx = inx && (t <= Nf);
+    }
+    return true;
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) k_bin(const InstDesc *__restrict__ D, const Range *__restrict__ R, int nr,
+                                             int32_t *__restrict__ rng, uint8_t *__restrict__ pflag,
+                                             int2 *__restrict__ qitems, int32_t *__restrict__ qcount,
+                                             int64_t qcap)
+{
+    __shared__ int s_r;
+    if (threadIdx.x == 0) s_r = find_range(R, nr, blockIdx.x);
+    __syncthreads();
+    const Range rg = R[s_r];
+    const int64_t local = (int64_t)(blockIdx.x - rg.block_start) * 256 + threadIdx.x;
+    if (local >= rg.count) return;
+    const InstDesc &I = D[rg.inst];
+    const int64_t p = rg.first + local;
+    const int64_t lp = p - I.pair_base;
+    const int ls = (int)(lp / I.nu);
+    const int u = (int)(lp - (int64_t)ls * I.nu);
+    const int node = I.live[ls];
+    const int64_t q = (int64_t)node * I.nu + u;
+    const uint16_t ex = I.exact[q];
+    constexpr unsigned FULL = (1u << (2 * N)) - 1u;
+    if (ex & EX_NF64) {
+        pflag[p] = PF_NONFINITE;
+        return;
+    }
+    unsigned mask = 0;
+    int32_t out[2 * N];
+    bool inx = true;
+    if ((ex & EX_NF32) && (ex & FULL) != FULL) {
+        mask = FULL;
+    } else {
+#pragma unroll
+        for (int e = 0; e < 2 * N; e++) {
+            if ((ex >> e) & 1) decide_exact<N>(I, e, I.box64[q * 2 * N + e], out[e], inx);
+            else if (!decide_approx<N>(I, e, I.box32[q * 2 * N + e], out[e], inx)) mask |= 1u << e;
+        }
+    }
+    if (mask) {
+        int pos = atomicAdd(qcount, 1);
+        if (pos < qcap) qitems[pos] = make_int2((int)p, rg.inst | (int)(mask << 16));
+        pflag[p] = PF_RECHECK;
+        return;
+    }
+#pragma unroll
+    for (int e = 0; e < 2 * N; e++) rng[p * 2 * N + e] = out[e];
+    pflag[p] = inx ? PF_INX : 0;
+}
+
+// Order-preserving map of doubles to signed 64-bit keys (for atomic min / max).
+__device__ __forceinline__ long long dkey(double v)
+{
+    const long long b = __double_as_longlong(v);
+    return b >= 0 ? b : b ^ 0x7fffffffffffffffll;
+}
+__device__ __forceinline__ double dkey_inv(long long k)
+{
+    return __longlong_as_double(k >= 0 ? k : k ^ 0x7fffffffffffffffll);
+}
+
+// Recheck, phase A: one warp per flagged pair recomputes its FP32 samples and
+// appends the candidates of the flagged extremes -- the samples whose FP32
+// image lies within the candidate window of the FP32 extreme -- or all samples
+// if some FP32 image was not finite. Also resets the pair's FP64 reductions.
+template <class DY, int DYN>
+__global__ void __launch_bounds__(256) k_rc_cand(const InstDesc *__restrict__ D, const int2 *__restrict__ items,
+                                                 const int32_t *__restrict__ count, int64_t qcap,
+                                                 long long *__restrict__ mnk, long long *__restrict__ mxk,
+                                                 int32_t *__restrict__ bad, int2 *__restrict__ cand,
+                                                 int32_t *__restrict__ ncand)
+{
+    constexpr int N = DY::N;
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x / 32);
+    const int total = (int)min((int64_t)*count, qcap);
+    for (int it = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; it < total; it += nw) {
+        const int2 item = items[it];
+        const int inst = item.y & 0xFFFF;
+        const unsigned mask = (unsigned)item.y >> 16;
+        const InstDesc &I = D[inst];
+        if (I.dyn != DYN || I.n != N) continue;
+        const int64_t lp = (int64_t)item.x - I.pair_base;
+        const int ls = (int)(lp / I.nu);
+        const int u = (int)(lp - (int64_t)ls * I.nu);
+        const int node = I.live[ls];
+        const int L = I.lvl[node];
+        const int64_t q = (int64_t)node * I.nu + u;
+        const bool all64 = (I.exact[q] & EX_NF32) != 0;
+        if (lane < N) {
+            mnk[(int64_t)it * N + lane] = dkey(INFINITY);
+            mxk[(int64_t)it * N + lane] = dkey(-INFINITY);
+        }
+        if (lane == 0) bad[it] = 0;
+        float base[N], w[N];
+        cell_base32<N>(I, node, L, base, w);
+        float u32[MAXN];
+        for (int j = 0; j < I.m; j++) u32[j] = I.u32[u * I.m + j];
+        float v32[2 * N];
+#pragma unroll
+        for (int e = 0; e < 2 * N; e++) v32[e] = I.box32[q * 2 * N + e];
+        const M32 M3{I.p32, I.m, I.substeps, I.h32, I.hh32, I.h6_32};
+        for (int s0 = 0; s0 < I.S; s0 += 32) {
+            const int s = s0 + lane;
+            bool c = false;
+            if (s < I.S) {
+                c = all64;
+                if (!c) {
+                    float x[N], y[N];
+                    int r = s;
+#pragma unroll
+                    for (int d = 0; d < N; d++) {
+                        x[d] = fmaf(w[d], I.frac32[r % I.k], base[d]);
+                        r /= I.k;
+                    }
+                    step32<DY>(M3, x, u32, y);
+#pragma unroll
+                    for (int e = 0; e < 2 * N; e++) {
+                        if (!((mask >> e) & 1)) continue;
+                        const int d = e % N;
+                        if (e < N) c |= !(y[d] > v32[e] + I.cand32[d]);
+                        else c |= !(y[d] < v32[e] - I.cand32[d]);
+                    }
+                }
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, c);
+            int pos = 0;
+            if (lane == 0 && b) pos = atomicAdd(ncand, __popc(b));
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            if (c) cand[pos + __popc(b & ((1u << lane) - 1u))] = make_int2(it, s);
+        }
+    }
+}
+
+// Recheck, phase B: one thread per candidate sample, in FP64 (every lane busy).
+template <class DY, int DYN>
+__global__ void __launch_bounds__(256) k_rc_fp64(const InstDesc *__restrict__ D, const int2 *__restrict__ items,
+                                                 const int2 *__restrict__ cand, const int32_t *__restrict__ ncand,
+                                                 int64_t ccap, long long *__restrict__ mnk,
+                                                 long long *__restrict__ mxk, int32_t *__restrict__ bad)
+{
+    constexpr int N = DY::N;
+    const int total = (int)min((int64_t)*ncand, ccap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int2 c = cand[i];
+        const int2 item = items[c.x];
+        const InstDesc &I = D[item.y & 0xFFFF];
+        if (I.dyn != DYN || I.n != N) continue;
+        const int64_t lp = (int64_t)item.x - I.pair_base;
+        const int ls = (int)(lp / I.nu);
+        const int u = (int)(lp - (int64_t)ls * I.nu);
+        const int node = I.live[ls];
+        const int L = I.lvl[node];
+        int32_t idx[N];
+#pragma unroll
+        for (int d = 0; d < N; d++) idx[d] = I.idx[d][node];
+        double uu[MAXN];
+        for (int j = 0; j < I.m; j++) uu[j] = I.u64[u * I.m + j];
+        const M64 M6{I.p64, I.m, I.substeps, I.h64, I.hh64, I.h6_64};
+        double x[N], y[N];
+        sample64<N>(I, L, idx, c.y, x);
+        step64<DY>(M6, x, uu, y);
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            if (!isfinite(y[d])) {
+                atomicOr(&bad[c.x], 1);
+                continue;
+            }
+            atomicMin(&mnk[(int64_t)c.x * N + d], dkey(y[d]));
+            atomicMax(&mxk[(int64_t)c.x * N + d], dkey(y[d]));
+        }
+    }
+}
+
+// Recheck, phase C: exact extremes into the cache, decisions of the pair.
+template <int N>
+__global__ void __launch_bounds__(256) k_rc_final(const InstDesc *__restrict__ D, const int2 *__restrict__ items,
+                                                  const int32_t *__restrict__ count, int64_t qcap,
+                                                  const long long *__restrict__ mnk,
+                                                  const long long *__restrict__ mxk,
+                                                  const int32_t *__restrict__ bad, int32_t *__restrict__ rng,
+                                                  uint8_t *__restrict__ pflag)
+{
+    constexpr unsigned FULL = (1u << (2 * N)) - 1u;
+    const int total = (int)min((int64_t)*count, qcap);
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+        const int2 item = items[it];
+        const unsigned mask = (unsigned)item.y >> 16;
+        const InstDesc &I = D[item.y & 0xFFFF];
+        if (I.n != N) continue;
+        const int64_t p = item.x;
+        const int64_t lp = p - I.pair_base;
+        const int ls = (int)(lp / I.nu);
+        const int u = (int)(lp - (int64_t)ls * I.nu);
+        const int64_t q = (int64_t)I.live[ls] * I.nu + u;
+        const bool all64 = (I.exact[q] & EX_NF32) != 0;
+        if (bad[it]) {
+            I.exact[q] = (uint16_t)(I.exact[q] | EX_NF64);
+            pflag[p] = PF_NONFINITE;
+            continue;
+        }
+        const unsigned upd = all64 ? FULL : mask;
+        unsigned ex = I.exact[q] & FULL;
+#pragma unroll
+        for (int e = 0; e < 2 * N; e++) {
+            if (!((upd >> e) & 1)) continue;
+            const int d = e % N;
+            I.box64[q * 2 * N + e] = e < N ? dkey_inv(mnk[(int64_t)it * N + d]) : dkey_inv(mxk[(int64_t)it * N + d]);
+            ex |= 1u << e;
+        }
+        I.exact[q] = (uint16_t)ex;
+        bool inx = true;
+        int32_t out[2 * N];
+#pragma unroll
+        for (int e = 0; e < 2 * N; e++) {
+            if ((ex >> e) & 1) decide_exact<N>(I, e, I.box64[q * 2 * N + e], out[e], inx);
+            else decide_approx<N>(I, e, I.box32[q * 2 * N + e], out[e], inx);
+        }
+#pragma unroll
+        for (int e = 0; e < 2 * N; e++) rng[p * 2 * N + e] = out[e];
+        pflag[p] = inx ? PF_INX : 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// dispatch
+// ---------------------------------------------------------------------------
+int prop_pairs_per_block(int lanes) { return PROP_THREADS / lanes; }
+
+template <class DY>
+static cudaError_t prop32_g(int lanes, const InstDesc *D, const WorkList &w, cudaStream_t st)
+{
+    dim3 g((unsigned)w.n_blocks), b(PROP_THREADS);
+    switch (lanes) {
+    case 1: k_prop32<DY, 1><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges); note_launch(); break;
+    case 2: k_prop32<DY, 2><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges); note_launch(); break;
+    case 4: k_prop32<DY, 4><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges); note_launch(); break;
+    case 8: k_prop32<DY, 8><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges); note_launch(); break;
+    case 16: k_prop32<DY, 16><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges); note_launch(); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prop32(int dyn, int n, int lanes, const InstDesc *D, const WorkList &w, cudaStream_t st)
+{
+    if (w.n_blocks == 0) return cudaSuccess;
+    switch (dyn) {
+    case GIS_DYN_VDP: return prop32_g<DynVdp>(lanes, D, w, st);
+    case GIS_DYN_CSTR_DL: return prop32_g<DynCstrDl>(lanes, D, w, st);
+    case GIS_DYN_CARTPOLE: return prop32_g<DynCartpole>(lanes, D, w, st);
+    case GIS_DYN_CSTR_PAPER: return prop32_g<DynCstrPaper>(lanes, D, w, st);
+    case GIS_DYN_LINMAP:
+        switch (n) {
+        case 1: return prop32_g<DynLin<1>>(lanes, D, w, st);
+        case 2: return prop32_g<DynLin<2>>(lanes, D, w, st);
+        case 3: return prop32_g<DynLin<3>>(lanes, D, w, st);
+        case 4: return prop32_g<DynLin<4>>(lanes, D, w, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class DY>
+static cudaError_t prop64_l(const InstDesc *D, const WorkList &w, cudaStream_t st)
+{
+    k_prop64<DY><<<(unsigned)w.n_blocks, PROP_THREADS, 0, st>>>(D, w.d_ranges, w.n_ranges); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prop64(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st)
+{
+    if (w.n_blocks == 0) return cudaSuccess;
+    switch (dyn) {
+    case GIS_DYN_VDP: return prop64_l<DynVdp>(D, w, st);
+    case GIS_DYN_CSTR_DL: return prop64_l<DynCstrDl>(D, w, st);
+    case GIS_DYN_CARTPOLE: return prop64_l<DynCartpole>(D, w, st);
+    case GIS_DYN_CSTR_PAPER: return prop64_l<DynCstrPaper>(D, w, st);
+    case GIS_DYN_LINMAP:
+        switch (n) {
+        case 1: return prop64_l<DynLin<1>>(D, w, st);
+        case 2: return prop64_l<DynLin<2>>(D, w, st);
+        case 3: return prop64_l<DynLin<3>>(D, w, st);
+        case 4: return prop64_l<DynLin<4>>(D, w, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_bin(int n, const InstDesc *D, const WorkList &w, int32_t *rng, uint8_t *pflag,
+                       int2 *qitems, int32_t *qcount, int64_t qcap, cudaStream_t st)
+{
+    if (w.n_blocks == 0) return cudaSuccess;
+    dim3 g((unsigned)w.n_blocks), b(256);
+    switch (n) {
+    case 1: k_bin<1><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges, rng, pflag, qitems, qcount, qcap); note_launch(); break;
+    case 2: k_bin<2><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges, rng, pflag, qitems, qcount, qcap); note_launch(); break;
+    case 3: k_bin<3><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges, rng, pflag, qitems, qcount, qcap); note_launch(); break;
+    case 4: k_bin<4><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges, rng, pflag, qitems, qcount, qcap); note_launch(); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+static int sm_count()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+template <class DY, int DYN>
+static cudaError_t recheck_l(int phase, const RecheckArgs &a, cudaStream_t st)
+{
+    const int g = sm_count() * 8;
+    if (phase == 0) {
+        k_rc_cand<DY, DYN><<<g, 256, 0, st>>>(a.D, a.items, a.count, a.qcap, a.mnk, a.mxk, a.bad, a.cand, a.ncand); note_launch();
+    } else {
+        k_rc_fp64<DY, DYN><<<g, 256, 0, st>>>(a.D, a.items, a.cand, a.ncand, a.ccap, a.mnk, a.mxk, a.bad); note_launch();
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_recheck(int phase, int dyn, int n, const RecheckArgs &a, cudaStream_t st)
+{
+    if (phase == 2) {
+        const int g = sm_count() * 8;
+        switch (n) {
+        case 1: k_rc_final<1><<<g, 256, 0, st>>>(a.D, a.items, a.count, a.qcap, a.mnk, a.mxk, a.bad, a.rng, a.pflag); note_launch(); break;
+        case 2: k_rc_final<2><<<g, 256, 0, st>>>(a.D, a.items, a.count, a.qcap, a.mnk, a.mxk, a.bad, a.rng, a.pflag); note_launch(); break;
+        case 3: k_rc_final<3><<<g, 256, 0, st>>>(a.D, a.items, a.count, a.qcap, a.mnk, a.mxk, a.bad, a.rng, a.pflag); note_launch(); break;
+        case 4: k_rc_final<4><<<g, 256, 0, st>>>(a.D, a.items, a.count, a.qcap, a.mnk, a.mxk, a.bad, a.rng, a.pflag); note_launch(); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
+    switch (dyn) {
+    case GIS_DYN_VDP: return recheck_l<DynVdp, GIS_DYN_VDP>(phase, a, st);
+    case GIS_DYN_CSTR_DL: return recheck_l<DynCstrDl, GIS_DYN_CSTR_DL>(phase, a, st);
+    case GIS_DYN_CARTPOLE: return recheck_l<DynCartpole, GIS_DYN_CARTPOLE>(phase, a, st);
+    case GIS_DYN_CSTR_PAPER: return recheck_l<DynCstrPaper, GIS_DYN_CSTR_PAPER>(phase, a, st);
+    case GIS_DYN_LINMAP:
+        switch (n) {
+        case 1: return recheck_l<DynLin<1>, GIS_DYN_LINMAP>(phase, a, st);
+        case 2: return recheck_l<DynLin<2>, GIS_DYN_LINMAP>(phase, a, st);
+        case 3: return recheck_l<DynLin<3>, GIS_DYN_LINMAP>(phase, a, st);
+        case 4: return recheck_l<DynLin<4>, GIS_DYN_LINMAP>(phase, a, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace gis

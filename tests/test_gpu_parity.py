@@ -1,0 +1,121 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle,
+level by level: live cells, every edge of the symbolic image, the pair flags,
+the kept set of the pruning fixed point and the subdivided covering.
+The bar is bit-exact equality (integer and set outputs)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_06111_gb300 import workloads as W
+
+from gis_compare import compare_graph, first_edge_diff, kept_keys, perm_to_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gis():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2202_06111_gb300 import build, gis as g
+    build.build()
+    g.load()
+    oracle.build()
+    oracle.set_threads(0)
+    return g
+
+
+def run_both(gis, prob, levels, check_graph=True, **opts):
+    """Step the GPU context and the oracle side by side; compare every level."""
+    ctx = gis.Context(prob, **opts)
+    ref = oracle.Solver(prob)
+    nu = len(prob["controls"])
+    out = []
+    for L in range(levels + 1):
+        ctx.build_graph()
+        ref.build_graph()
+        glv, _, gidx = ctx.cells()
+        olv, oidx = ref.live()
+        perm = perm_to_oracle(glv, gidx, olv, oidx)
+        if check_graph:
+            same, bad_flags, sizes = compare_graph(ctx.graph(), ref.graph(), perm, nu)
+            if not same:
+                g, o = first_edge_diff(ctx.graph(), ref.graph(), perm, nu)
+                pytest.fail(f"level {L}: edges differ {sizes}; gpu-only {g} oracle-only {o}")
+            assert len(bad_flags) == 0, f"level {L}: {len(bad_flags)} pair flags differ, e.g. {bad_flags[:5]}"
+        nk, rounds = ctx.prune()
+        onk = ref.prune()
+        assert nk == onk, f"level {L}: kept {nk} on the GPU vs {onk} in the oracle"
+        gk = kept_keys(*ctx.kept_cells())
+        ok = kept_keys(*ref.kept_cells())
+        assert gk == ok, f"level {L}: kept sets differ ({len(gk ^ ok)} cells)"
+        out.append((nk, ctx.stats()))
+        if L < levels:
+            ns = ctx.subdivide()
+            ons = ref.subdivide()
+            assert ns == ons, f"level {L}: split {ns} vs {ons}"
+    ctx.close()
+    return out
+
+
+@pytest.mark.parametrize("rule", ["inner", "outer"])
+def test_vdp_64_fp64_full_size(gis, rule):
+    """Van der Pol workload at its full size (64^2, 3x3 samples, FP64 plain)."""
+    run_both(gis, dict(W.vdp_64(), rule=rule), 0)
+
+
+@pytest.mark.parametrize("rule", ["inner", "outer"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cstr_small_levels(gis, rule, precision):
+    """CSTR, 37^2 root cells (ragged tails), 3 levels of boundary refinement."""
+    run_both(gis, dict(W.cstr_256(levels=3, n0=37), rule=rule, precision=precision), 3)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cartpole_small_levels(gis, precision):
+    """Cart-pole 4-D, 7^4 root cells, 2 levels (OUTER keeps a non-trivial set)."""
+    run_both(gis, dict(W.cartpole_48(levels=2, n0=7), rule="outer", precision=precision), 2)
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16])
+def test_lanes_per_pair_same_result(gis, lanes):
+    """Every propagation shape gives the same graph (min / max are exact)."""
+    run_both(gis, dict(W.cstr_256(levels=1, n0=29), rule="outer"), 1, lanes_per_pair=lanes)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_linear_maps_all_dimensions(gis, n):
+    rng = np.random.default_rng(n)
+    A = (np.eye(n) * 1.05 + rng.uniform(-0.2, 0.2, (n, n))).tolist()
+    B = rng.uniform(-0.5, 0.5, (n, 1)).tolist()
+    prob = W.problem(W.linmap(A, B), [-1.3] * n, [1.7] * n, [9, 7, 5, 3][:n], 3 if n < 4 else 2,
+                     W.controls_grid(-0.4, 0.3, 4), 1.0, 0, rule="outer", precision="fp32")
+    run_both(gis, prob, 2 if n < 4 else 1)
+
+
+@pytest.mark.parametrize("n0", [2, 8, 16, 64])
+@pytest.mark.parametrize("rule", ["inner", "outer"])
+def test_closed_form_doubling_map(gis, n0, rule):
+    """x+ = 2x + u, u in {-1/2, 0, 1/2}: exact ties on grid lines everywhere."""
+    prob = W.problem(W.linmap([[2.0]], [[1.0]]), [-1.0], [1.0], n0, 2, [[-0.5], [0.0], [0.5]], 1.0, 0,
+                     rule=rule, precision="fp32")
+    run_both(gis, prob, 2)
+
+
+def test_everything_leaves(gis):
+    """x+ = 2x + 3: every image leaves X, nothing is kept, no split."""
+    prob = W.problem(W.linmap([[2.0]], [[1.0]]), [-1.0], [1.0], 16, 2, [[3.0]], 1.0, 0, precision="fp32")
+    res = run_both(gis, prob, 1)
+    assert res[0][0] == 0
+
+
+def test_single_root_cell_and_centre_sample(gis):
+    prob = W.problem(W.vdp(1.0), [-3, -3], [3, 3], 1, 1, [[0.0]], 0.1, 2, rule="outer", precision="fp32")
+    run_both(gis, prob, 2)
+
+
+def test_paper_cstr_eq4(gis):
+    """The dimensional CSTR of Eq. 4 / Table 2 on X = [0,1] x [345,355] (FP64:
+    near 350 K an FP32 state carries only 3e-5 K, amplified by the reaction)."""
+    run_both(gis, dict(W.cstr_paper_problem(n0=(24, 24)), rule="outer", precision="fp64"), 2)
