@@ -237,6 +237,37 @@ typedef struct {
 gis_status gis_batch_solve(const gis_request *reqs, int32_t n, gis_result *res,
                            const gis_options *opt, void *stream, gis_stats *stats);
 
+/* ---- pruning without device allocation ---------------------------------- */
+#define GIS_NOALLOC_MAX_CELLS 131072    /* 2^17 cells                          */
+#define GIS_NOALLOC_MAX_PAIRS 1048576   /* 2^20 (cell, control) pairs          */
+#define GIS_NOALLOC_MAX_EDGES 4194304   /* 2^22 edges                          */
+
+/* The paper has no counterpart of this entry point. It exists for callers
+ * that cannot allocate device memory -- code that runs inside a fixed device
+ * memory arena, next to an allocator that owns the whole device, or on paths
+ * that must not call cudaMalloc / cudaFree because those may synchronise the
+ * device. It computes what gis_prune computes, the greatest fixed point of
+ * `rule` (GIS_RULE_INNER / GIS_RULE_OUTER), on a graph the caller supplies,
+ * and allocates nothing: its scratch is one fixed __device__ array of the
+ * library (about 28 MB, reserved on every GPU that loads the library until the
+ * process exits).
+ *   off[n_cells * n_controls + 1]  device, int64 CSR offsets of the pairs
+ *                                  (pair = cell * n_controls + control)
+ *   tgt[n_edges]                   device, int32 target cell of every edge
+ *   flag[n_cells * n_controls]     device, GIS_PAIR_* bits of every pair
+ *   kept[n_cells]                  device output, 1 = kept, 0 = removed
+ *   n_kept                         host output (may be NULL)
+ * This is the layout gis_get_graph returns. Sizes above GIS_NOALLOC_MAX_* are
+ * rejected with GIS_EUNSUPPORTED before any work is queued. The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture. Every
+ * call uses the same array, so calls that overlap on the GPU (from several
+ * streams or threads) race and give wrong results: serialise them. The call
+ * synchronises `stream` before it returns.                                   */
+gis_status gis_prune_graph_noalloc(int64_t n_cells, int32_t n_controls, const int64_t *off, const int32_t *tgt,
+                                   const uint8_t *flag, int64_t n_edges, int32_t rule, uint8_t *kept,
+                                   int64_t *n_kept, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

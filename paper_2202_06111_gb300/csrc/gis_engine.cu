@@ -974,6 +974,10 @@ struct gis_ctx {
 
 static thread_local std::string g_err;
 
+namespace gis {
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace gis
+
 #define API_BEGIN try {
 #define API_END(ctx)                                                                   \
     }                                                                                  \

@@ -105,6 +105,8 @@ SIGNATURES = {
     "gis_destroy": (None, [C.c_void_p]),
     "gis_batch_solve": (C.c_int32, [C.POINTER(gis_request), C.c_int32, C.POINTER(gis_result),
                                     C.POINTER(gis_options), C.c_void_p, C.POINTER(gis_stats)]),
+    "gis_prune_graph_noalloc": (C.c_int32, [C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                            C.c_int32, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p]),
 }
 
 _lib = None
