@@ -72,10 +72,12 @@ enum {
 enum { GIS_RULE_INNER = 0, GIS_RULE_OUTER = 1 };
 
 /* Precision of the propagation. FP64_PLAIN: every sample in FP64. FP32_RECHECK:
- * samples in FP32; every image-box extreme within `band` finest-level cell
- * widths of a grid line is recomputed in FP64 on the GPU, so the edge sets
- * equal those of the FP64 computation whenever the FP32 error of a sample is
- * below band/2 cell widths.                                                    */
+ * samples in certified FP32 -- midpoint-radius arithmetic whose radii bound
+ * every rounding (and the documented error of expf / sinf / cosf), so each
+ * image-box extreme is known to lie in an interval; when that interval may
+ * hold a grid line of the finest level (the faces of X included) the extreme
+ * is recomputed in FP64 on the GPU over the samples that can attain it. The
+ * decisions then equal those of the FP64 computation of Sec. 2.2's image box. */
 enum { GIS_FP64_PLAIN = 0, GIS_FP32_RECHECK = 1 };
 
 typedef struct {
@@ -102,7 +104,7 @@ typedef struct {
 typedef struct {
     int32_t rule;           /* GIS_RULE_*                                         */
     int32_t precision;      /* GIS_FP64_PLAIN | GIS_FP32_RECHECK                   */
-    double band;            /* FP32 recheck band, finest-level cell widths (> 0)   */
+    double band;            /* extra recheck margin, finest-level cell widths (>= 0) */
     int32_t lanes_per_pair; /* propagation lanes per pair 1,2,4,8,16,32; 0 = auto  */
     int32_t timing;         /* 1: record per-kernel CUDA-event times into stats    */
     int64_t max_device_bytes; /* 0 = no limit; else allocations beyond -> ENOMEM   */
@@ -151,11 +153,12 @@ typedef struct {
     double prune_bytes;     /* algorithmic bytes of the prune                      */
     double count_bytes, fill_bytes, transpose_bytes; /* the parts of graph_bytes   */
     int64_t cum_launches;   /* kernel launches issued by the library              */
+    int64_t cum_recheck_samples; /* samples recomputed in FP64 by the recheck      */
 } gis_stats;
 
 typedef struct gis_ctx gis_ctx;
 
-/* Default options: INNER rule, FP32_RECHECK, band 1e-2, auto lanes, no timing. */
+/* Default options: INNER rule, FP32_RECHECK, band 0, auto lanes, no timing. */
 void gis_default_options(gis_options *out);
 
 /* Create a context on the current CUDA device, with the covering of root
@@ -194,8 +197,9 @@ gis_status gis_get_graph(gis_ctx *ctx, int64_t *off, int32_t *tgt, uint8_t *flag
                          int64_t cap_edges, int64_t *n_pairs, int64_t *n_edges);
 
 /* Image boxes of the current pairs: box32 [n_pairs x 2n] FP32 extremes
- * (ymin_0..ymin_{n-1}, ymax_0..), box64 the same in FP64 where `exact` has the
- * extreme's bit set (bit e for extreme e), else the FP32 value widened.
+ * (ymin_0..ymin_{n-1}, ymax_0..; the midpoint of each certified interval),
+ * box64 the same in FP64 where `exact` has the extreme's bit set (bit e for
+ * extreme e), else the FP32 value widened.
  * Any output may be NULL. For testing and calibration.                       */
 gis_status gis_get_boxes(gis_ctx *ctx, float *box32, double *box64, uint8_t *exact, int64_t cap_pairs);
 

@@ -16,21 +16,6 @@
 
 #include "gis.h"
 
-// FP32 transcendentals of the propagation: hardware approximations (default)
-// or the accurate CUDA library versions.
-#ifndef GIS_FAST_MATH
-#define GIS_FAST_MATH 1
-#endif
-#if GIS_FAST_MATH
-#define GIS_EXPF(x) __expf(x)
-#define GIS_SINCOSF(x, s, c) __sincosf(x, s, c)
-#define GIS_FDIV(a, b) __fdividef(a, b)
-#else
-#define GIS_EXPF(x) expf(x)
-#define GIS_SINCOSF(x, s, c) sincosf(x, s, c)
-#define GIS_FDIV(a, b) ((a) / (b))
-#endif
-
 namespace gis {
 
 constexpr int MAXN = GIS_MAX_DIM;
@@ -61,20 +46,26 @@ struct InstDesc {
     int32_t dyn, n, m, nu, k, S, substeps, rule, precision, Lf;
     int64_t slot_base, pair_base, n_live;
     float p32[GIS_NPARAM];      // derived constants for the FP32 model
+    float pr32[GIS_NPARAM];     // their radii: |p32 - exact value|, rounded up
     double p64[GIS_NPARAM];     // derived constants for the FP64 model (same ops as the definition)
+    double p64_exact[GIS_NPARAM]; // the values p32 stands for (host bookkeeping)
     float h32, hh32, h6_32;
+    float hr32, hhr32, h6r32;   // radii of h, h/2, h/6
     double h64, hh64, h6_64;
     double lo[MAXN], hi[MAXN];
     float lo32[MAXN];
+    float lor32[MAXN];          // radius of lo32
     int32_t n0[MAXN];
     double w64[MAXL + 1][MAXN]; // (hi - lo) / (n0 2^L)
     float w32[MAXL + 1][MAXN];
+    float wr32[MAXL + 1][MAXN]; // radius of w32
     float invwf32[MAXN];        // 1 / w at Lf
-    float band_t[MAXN];         // recheck threshold, in Lf cell widths
-    float cand32[MAXN];         // recheck candidate window, absolute
+    float tmargin[MAXN];        // FP32 t-computation error bound plus the optional band, Lf cells
     float frac32[MAXK];
+    float fracr32[MAXK];        // radius of frac32
     double frac64[MAXK];        // j / (k - 1)
     const float *u32;           // nu x m controls
+    const float *ur32;          // their radii
     const double *u64;
     // ---- subdivision tree ----
     uint8_t *lvl, *state;
@@ -83,7 +74,8 @@ struct InstDesc {
     int32_t *slot;              // global slot of a live node at this level
     const int32_t *live;        // live nodes in slot order
     // ---- image-box cache, indexed node * nu + u ----
-    float *box32;               // [.. x 2n] : ymin[0..n-1], ymax[0..n-1]
+    float *box32;               // [.. x 2n x 2]: per extreme e (ymin_0..ymin_{n-1}, ymax_0..)
+                                // a certified interval [lo, hi] that holds its exact value
     double *box64;
     uint16_t *exact;
 };
@@ -104,11 +96,107 @@ __device__ __forceinline__ int find_range(const Range *__restrict__ R, int nr, i
 // contraction), transcendentals from the CUDA math library.
 // p32 / p64 layouts are filled by the host (derive_params).
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Certified FP32: midpoint-radius ("ball") arithmetic. A Ball {m, r} stands
+// for every real value in [m - r, m + r]; each operation returns a ball that
+// holds every exact result of its operands' values. Midpoints are computed
+// with round-to-nearest, radii with upward rounding: the rounding error of a
+// midpoint is at most 2^-24 |m| (bounded here by 2^-23 |m| + 1e-37 to cover
+// underflow); expf / sinf / cosf are within 2 ulp (CUDA's documented bounds,
+// bounded here by 2^-21 |m|); FP32 division rounds correctly.
+// ---------------------------------------------------------------------------
+struct Ball {
+    float m, r;
+};
+
+constexpr float B_U = 1.1920929e-07f;    // 2^-23
+constexpr float B_ETA = 1.0e-37f;
+constexpr float B_F = 4.7683716e-07f;    // 2^-21, library function error
+
+__device__ __forceinline__ float b_rerr(float m) { return __fmaf_ru(fabsf(m), B_U, B_ETA); }
+__device__ __forceinline__ Ball bexact(float v) { return {v, 0.0f}; }
+__device__ __forceinline__ Ball badd(Ball a, Ball b)
+{
+    const float m = a.m + b.m;
+    return {m, __fadd_ru(__fadd_ru(a.r, b.r), b_rerr(m))};
+}
+__device__ __forceinline__ Ball bsub(Ball a, Ball b)
+{
+    const float m = a.m - b.m;
+    return {m, __fadd_ru(__fadd_ru(a.r, b.r), b_rerr(m))};
+}
+__device__ __forceinline__ Ball bneg(Ball a) { return {-a.m, a.r}; }
+__device__ __forceinline__ Ball bmul(Ball a, Ball b)
+{
+    const float m = a.m * b.m;
+    const float r = __fmaf_ru(fabsf(a.m), b.r, __fmaf_ru(fabsf(b.m), a.r, __fmul_ru(a.r, b.r)));
+    return {m, __fadd_ru(r, b_rerr(m))};
+}
+// a * b + c with one rounding of the midpoint
+__device__ __forceinline__ Ball bfma(Ball a, Ball b, Ball c)
+{
+    const float m = fmaf(a.m, b.m, c.m);
+    const float r = __fmaf_ru(fabsf(a.m), b.r, __fmaf_ru(fabsf(b.m), a.r, __fmaf_ru(a.r, b.r, c.r)));
+    return {m, __fadd_ru(r, b_rerr(m))};
+}
+// |a/b - am/bm| <= (|am| rb + |bm| ra) / (|bm| (|bm| - rb)) when |bm| > rb
+__device__ __forceinline__ Ball bdiv(Ball a, Ball b)
+{
+    const float ab = fabsf(b.m);
+    if (!(ab > b.r)) return {NAN, INFINITY};
+    const float m = a.m / b.m;
+    const float num = __fmaf_ru(fabsf(a.m), b.r, __fmul_ru(ab, a.r));
+    const float den = __fmul_rd(ab, __fsub_rd(ab, b.r));
+    return {m, __fadd_ru(__fdiv_ru(num, den), b_rerr(m))};
+}
+// exp is increasing: the ball of exp over [m - r, m + r] spans
+// [expf(m - r) (1 - 2^-21), expf(m + r) (1 + 2^-21)] (library error bound);
+// for small r the midpoint is expf(m) and the radius e^m (r + r^2) + error.
+__device__ __forceinline__ Ball bexp(Ball a)
+{
+    if (a.r <= 0.25f) {
+        const float e = expf(a.m);
+        const float eup = __fmaf_ru(e, B_F, e);
+        const float grow = __fmaf_ru(a.r, a.r, a.r);
+        return {e, __fmaf_ru(eup, grow, __fmaf_ru(e, B_F, B_ETA))};
+    }
+    const float lo = __fmul_rd(expf(__fsub_rd(a.m, a.r)), 1.0f - B_F);
+    const float hi = __fmul_ru(expf(__fadd_ru(a.m, a.r)), 1.0f + B_F);
+    const float m = 0.5f * lo + 0.5f * hi;
+    return {m, __fadd_ru(fmaxf(__fsub_ru(hi, m), __fsub_ru(m, lo)), b_rerr(m))};
+}
+
+// sin and cos are 1-Lipschitz
+__device__ __forceinline__ void bsincos(Ball a, Ball *s, Ball *c)
+{
+    float sm, cm;
+    sincosf(a.m, &sm, &cm);
+    s->m = sm;
+    s->r = __fadd_ru(a.r, __fmaf_ru(fabsf(sm), B_F, B_ETA));
+    c->m = cm;
+    c->r = __fadd_ru(a.r, __fmaf_ru(fabsf(cm), B_F, B_ETA));
+}
+
+// Model constants of one instance as the ball propagation sees them.
+struct MB {
+    const float *p, *pr;        // may point to shared memory
+    int m, substeps;
+    Ball h, hh, h6;
+    __device__ __forceinline__ Ball P(int i) const { return {p[i], pr[i]}; }
+};
+
+// ---------------------------------------------------------------------------
+// Models. Ball (certified FP32) right-hand sides, written for few operations;
+// FP64 right-hand sides in the defining operation order, every operation
+// rounded on its own (_rn intrinsics, no contraction), transcendentals from
+// the CUDA math library. p32 / p64 layouts are filled by the host.
+// ---------------------------------------------------------------------------
 struct DynVdp {       // p: mu
     static constexpr int N = 2;
-    __device__ static __forceinline__ void rhs32(const float *p, const float *x, const float *u, float *dx) {
+    __device__ static __forceinline__ void rhsB(const MB &M, const Ball *x, const Ball *u, Ball *dx) {
         dx[0] = x[1];
-        dx[1] = fmaf(p[0] * fmaf(-x[0], x[0], 1.0f), x[1], u[0] - x[0]);
+        const Ball a = bfma(bneg(x[0]), x[0], bexact(1.0f));
+        dx[1] = bfma(bmul(M.P(0), a), x[1], bsub(u[0], x[0]));
     }
     __device__ static __forceinline__ void rhs64(const double *p, const double *x, const double *u, double *dx) {
         dx[0] = x[1];
@@ -121,11 +209,11 @@ struct DynVdp {       // p: mu
 
 struct DynCstrDl {    // p32: Da, B, beta, 1/gamma   p64: Da, B, beta, gamma
     static constexpr int N = 2;
-    __device__ static __forceinline__ void rhs32(const float *p, const float *x, const float *u, float *dx) {
-        float e = GIS_EXPF(GIS_FDIV(x[1], fmaf(x[1], p[3], 1.0f)));
-        float r = p[0] * (1.0f - x[0]) * e;
-        dx[0] = r - x[0];
-        dx[1] = fmaf(p[1], r, -x[1]) - p[2] * (x[1] - u[0]);
+    __device__ static __forceinline__ void rhsB(const MB &M, const Ball *x, const Ball *u, Ball *dx) {
+        const Ball e = bexp(bdiv(x[1], bfma(x[1], M.P(3), bexact(1.0f))));
+        const Ball r = bmul(bmul(M.P(0), bsub(bexact(1.0f), x[0])), e);
+        dx[0] = bsub(r, x[0]);
+        dx[1] = bsub(bfma(M.P(1), r, bneg(x[1])), bmul(M.P(2), bsub(x[1], u[0])));
     }
     __device__ static __forceinline__ void rhs64(const double *p, const double *x, const double *u, double *dx) {
         double e = exp(__ddiv_rn(x[1], __dadd_rn(1.0, __ddiv_rn(x[1], p[3]))));
@@ -138,14 +226,14 @@ struct DynCstrDl {    // p32: Da, B, beta, 1/gamma   p64: Da, B, beta, gamma
 
 struct DynCartpole {  // p32: g, 1/tot, pml, l, mp, 4/3    p64: mc, mp, l, g, tot, pml, 4/3
     static constexpr int N = 4;
-    __device__ static __forceinline__ void rhs32(const float *p, const float *x, const float *u, float *dx) {
-        float s, c;
-        GIS_SINCOSF(x[2], &s, &c);
-        float temp = fmaf(p[2] * x[3] * x[3], s, u[0]) * p[1];
-        float den = p[3] * fmaf(-p[4] * c * c, p[1], p[5]);
-        float thacc = GIS_FDIV(fmaf(p[0], s, -c * temp), den);
+    __device__ static __forceinline__ void rhsB(const MB &M, const Ball *x, const Ball *u, Ball *dx) {
+        Ball s, c;
+        bsincos(x[2], &s, &c);
+        const Ball temp = bmul(bfma(bmul(bmul(M.P(2), x[3]), x[3]), s, u[0]), M.P(1));
+        const Ball den = bmul(M.P(3), bfma(bmul(bmul(bneg(M.P(4)), c), c), M.P(1), M.P(5)));
+        const Ball thacc = bdiv(bfma(M.P(0), s, bneg(bmul(c, temp))), den);
         dx[0] = x[1];
-        dx[1] = fmaf(-p[2] * thacc * c, p[1], temp);
+        dx[1] = bfma(bmul(bmul(bneg(M.P(2)), thacc), c), M.P(1), temp);
         dx[2] = x[3];
         dx[3] = thacc;
     }
@@ -167,10 +255,10 @@ struct DynCartpole {  // p32: g, 1/tot, pml, l, mp, 4/3    p64: mc, mp, l, g, to
 
 struct DynCstrPaper { // p32: qV, cAf, Tf, ER, a1, a2, ln k0   p64: qV, cAf, Tf, ER, k0, a1, a2
     static constexpr int N = 2;
-    __device__ static __forceinline__ void rhs32(const float *p, const float *x, const float *u, float *dx) {
-        float rate = GIS_EXPF(p[6] - GIS_FDIV(p[3], x[1])) * x[0];
-        dx[0] = fmaf(p[0], p[1] - x[0], -rate);
-        dx[1] = fmaf(p[0], p[2] - x[1], fmaf(p[4], rate, p[5] * (u[0] - x[1])));
+    __device__ static __forceinline__ void rhsB(const MB &M, const Ball *x, const Ball *u, Ball *dx) {
+        const Ball rate = bmul(bexp(bsub(M.P(6), bdiv(M.P(3), x[1]))), x[0]);
+        dx[0] = bfma(M.P(0), bsub(M.P(1), x[0]), bneg(rate));
+        dx[1] = bfma(M.P(0), bsub(M.P(2), x[1]), bfma(M.P(4), rate, bmul(M.P(5), bsub(u[0], x[1]))));
     }
     __device__ static __forceinline__ void rhs64(const double *p, const double *x, const double *u, double *dx) {
         double rate = __dmul_rn(__dmul_rn(p[4], exp(__ddiv_rn(-p[3], x[1]))), x[0]);
@@ -185,13 +273,13 @@ struct DynCstrPaper { // p32: qV, cAf, Tf, ER, a1, a2, ln k0   p64: qV, cAf, Tf,
 template <int NN>
 struct DynLin {
     static constexpr int N = NN;
-    __device__ static __forceinline__ void rhs32_m(const float *p, int m, const float *x, const float *u, float *dx) {
+    __device__ static __forceinline__ void rhsB(const MB &M, const Ball *x, const Ball *u, Ball *dx) {
 #pragma unroll
         for (int i = 0; i < NN; i++) {
-            float acc = 0.0f;
+            Ball acc = bexact(0.0f);
 #pragma unroll
-            for (int j = 0; j < NN; j++) acc = fmaf(p[i * NN + j], x[j], acc);
-            for (int j = 0; j < m; j++) acc = fmaf(p[NN * NN + i * m + j], u[j], acc);
+            for (int j = 0; j < NN; j++) acc = bfma(M.P(i * NN + j), x[j], acc);
+            for (int j = 0; j < M.m; j++) acc = bfma(M.P(NN * NN + i * M.m + j), u[j], acc);
             dx[i] = acc;
         }
     }
@@ -210,17 +298,7 @@ struct DynLin {
 template <class DY> struct IsLin { static constexpr bool value = false; };
 template <int NN> struct IsLin<DynLin<NN>> { static constexpr bool value = true; };
 
-// Model constants of one instance as the propagation loops see them (p may
-// point to shared memory).
-struct M32 { const float *p; int m, substeps; float h, hh, h6; };
 struct M64 { const double *p; int m, substeps; double h, hh, h6; };
-
-template <class DY>
-__device__ __forceinline__ void rhs32(const M32 &M, const float *x, const float *u, float *dx)
-{
-    if constexpr (IsLin<DY>::value) DY::rhs32_m(M.p, M.m, x, u, dx);
-    else DY::rhs32(M.p, x, u, dx);
-}
 
 template <class DY>
 __device__ __forceinline__ void rhs64(const M64 &M, const double *x, const double *u, double *dx)
@@ -229,33 +307,34 @@ __device__ __forceinline__ void rhs64(const M64 &M, const double *x, const doubl
     else DY::rhs64(M.p, x, u, dx);
 }
 
-// One sampling period in FP32: `substeps` classic RK4 steps, or the discrete map.
+// One sampling period in certified FP32: `substeps` classic RK4 steps (or the
+// discrete map); the returned balls hold the exact results.
 template <class DY>
-__device__ __forceinline__ void step32(const M32 &M, const float *x0, const float *u, float *y)
+__device__ __forceinline__ void stepB(const MB &M, const Ball *x0, const Ball *u, Ball *y)
 {
     constexpr int N = DY::N;
-    float x[N];
+    Ball x[N];
 #pragma unroll
     for (int d = 0; d < N; d++) x[d] = x0[d];
     if (M.substeps == 0) {
-        rhs32<DY>(M, x, u, y);
+        DY::rhsB(M, x, u, y);
         return;
     }
-    const float h = M.h, hh = M.hh, h6 = M.h6;
     for (int s = 0; s < M.substeps; s++) {
-        float k1[N], k2[N], k3[N], k4[N], xt[N];
-        rhs32<DY>(M, x, u, k1);
+        Ball k1[N], k2[N], k3[N], k4[N], xt[N];
+        DY::rhsB(M, x, u, k1);
 #pragma unroll
-        for (int d = 0; d < N; d++) xt[d] = fmaf(hh, k1[d], x[d]);
-        rhs32<DY>(M, xt, u, k2);
+        for (int d = 0; d < N; d++) xt[d] = bfma(M.hh, k1[d], x[d]);
+        DY::rhsB(M, xt, u, k2);
 #pragma unroll
-        for (int d = 0; d < N; d++) xt[d] = fmaf(hh, k2[d], x[d]);
-        rhs32<DY>(M, xt, u, k3);
+        for (int d = 0; d < N; d++) xt[d] = bfma(M.hh, k2[d], x[d]);
+        DY::rhsB(M, xt, u, k3);
 #pragma unroll
-        for (int d = 0; d < N; d++) xt[d] = fmaf(h, k3[d], x[d]);
-        rhs32<DY>(M, xt, u, k4);
+        for (int d = 0; d < N; d++) xt[d] = bfma(M.h, k3[d], x[d]);
+        DY::rhsB(M, xt, u, k4);
 #pragma unroll
-        for (int d = 0; d < N; d++) x[d] = fmaf(h6, fmaf(2.0f, k2[d] + k3[d], k1[d] + k4[d]), x[d]);
+        for (int d = 0; d < N; d++)
+            x[d] = bfma(M.h6, bfma(bexact(2.0f), badd(k2[d], k3[d]), badd(k1[d], k4[d])), x[d]);
     }
 #pragma unroll
     for (int d = 0; d < N; d++) y[d] = x[d];
@@ -297,6 +376,11 @@ __device__ __forceinline__ void step64(const M64 &M, const double *x0, const dou
 #pragma unroll
     for (int d = 0; d < N; d++) y[d] = x[d];
 }
+
+// Final widening: the FP64 evaluation of the same expressions differs from the
+// exact result by at most its own rounding terms, 2^-29 of the FP32 ones the
+// radius already counts; 2^-20 r covers them with room to spare.
+__device__ __forceinline__ Ball bfinal(Ball y) { return {y.m, __fmaf_ru(y.r, 9.5367432e-07f, __fadd_ru(y.r, B_ETA))}; }
 
 // FP64 sample s of cell (L, idx): x_d = (lo_d + idx_d w_d) + w_d frac(j_d), j_d = digit d of s base k.
 template <int N>

@@ -194,7 +194,7 @@ struct Inst {
     float *box32 = nullptr;
     double *box64 = nullptr;
     uint16_t *exact = nullptr;
-    float *u32 = nullptr;
+    float *u32 = nullptr, *ur32 = nullptr;
     double *u64 = nullptr;
     InstDesc desc{};
 };
@@ -270,7 +270,7 @@ static void setup_inst(Inst &I, const gis_dynamics &dyn, const gis_grid &grid, c
     if (ctl.n_controls < 1 || !ctl.u) throw Error{GIS_EINVAL, "need >= 1 control value"};
     if (rule != GIS_RULE_INNER && rule != GIS_RULE_OUTER) throw Error{GIS_EINVAL, "bad rule"};
     if (precision != GIS_FP64_PLAIN && precision != GIS_FP32_RECHECK) throw Error{GIS_EINVAL, "bad precision"};
-    if (precision == GIS_FP32_RECHECK && !(band > 0 && band < 0.25)) throw Error{GIS_EINVAL, "band must be in (0, 1/4)"};
+    if (precision == GIS_FP32_RECHECK && !(band >= 0 && band < 0.25)) throw Error{GIS_EINVAL, "band must be in [0, 1/4)"};
     I.dyn = dyn;
     I.grid = grid;
     I.nu = ctl.n_controls;
@@ -289,17 +289,19 @@ static void setup_inst(Inst &I, const gis_dynamics &dyn, const gis_grid &grid, c
 static void derive_params(const Inst &I, InstDesc &D)
 {
     const double *p = I.dyn.params;
-    for (int i = 0; i < GIS_NPARAM; i++) { D.p64[i] = p[i]; D.p32[i] = (float)p[i]; }
+    for (int i = 0; i < GIS_NPARAM; i++) { D.p64[i] = p[i]; D.p32[i] = (float)p[i]; D.p64_exact[i] = p[i]; }
     switch (I.dyn.dyn_id) {
     case GIS_DYN_CSTR_DL:
-        D.p32[3] = (float)(1.0 / p[3]);
+        D.p64_exact[3] = 1.0 / p[3];
+        D.p32[3] = (float)D.p64_exact[3];
         break;
     case GIS_DYN_CARTPOLE: {
         const double mc = p[0], mp = p[1], l = p[2], g = p[3];
         const double tot = mc + mp, pml = mp * l, ft = 4.0 / 3.0;
         D.p64[4] = tot; D.p64[5] = pml; D.p64[6] = ft;
-        D.p32[0] = (float)g; D.p32[1] = (float)(1.0 / tot); D.p32[2] = (float)pml;
-        D.p32[3] = (float)l; D.p32[4] = (float)mp; D.p32[5] = (float)ft;
+        const double ex[6] = {g, 1.0 / tot, pml, l, mp, ft};
+        for (int i = 0; i < 6; i++) { D.p64_exact[i] = ex[i]; D.p32[i] = (float)ex[i]; }
+        for (int i = 6; i < GIS_NPARAM; i++) { D.p64_exact[i] = 0; D.p32[i] = 0; }
         break;
     }
     case GIS_DYN_CSTR_PAPER: {
@@ -307,12 +309,22 @@ static void derive_params(const Inst &I, InstDesc &D)
         const double mdH = p[6], UA = p[7], cp = p[8], rho = p[9];
         const double qV = q / V, a1 = mdH / (rho * cp), a2 = UA / (V * rho * cp);
         D.p64[0] = qV; D.p64[1] = cAf; D.p64[2] = Tf; D.p64[3] = ER; D.p64[4] = k0; D.p64[5] = a1; D.p64[6] = a2;
-        D.p32[0] = (float)qV; D.p32[1] = (float)cAf; D.p32[2] = (float)Tf; D.p32[3] = (float)ER;
-        D.p32[4] = (float)a1; D.p32[5] = (float)a2; D.p32[6] = (float)std::log(k0);
+        const double ex[7] = {qV, cAf, Tf, ER, a1, a2, std::log(k0)};
+        for (int i = 0; i < 7; i++) { D.p64_exact[i] = ex[i]; D.p32[i] = (float)ex[i]; }
         break;
     }
     default: break;
     }
+}
+
+// Radius (rounded up to a float) of the FP32 stand-in f of the exact value v:
+// |v - f| plus 2^-50 |v| for the FP64 computation of v itself.
+static float radius_of(double v, float f)
+{
+    const double r = std::fabs(v - (double)f) + std::ldexp(std::fabs(v), -50);
+    float rf = (float)r;
+    if ((double)rf < r) rf = std::nextafter(rf, INFINITY);
+    return rf;
 }
 
 static void fill_desc(Inst &I)
@@ -333,6 +345,7 @@ static void fill_desc(Inst &I)
     D.pair_base = I.pair_base;
     D.n_live = I.n_live;
     derive_params(I, D);
+    for (int i = 0; i < GIS_NPARAM; i++) D.pr32[i] = radius_of(D.p64_exact[i], D.p32[i]);
     if (I.dyn.substeps > 0) {
         const double h = I.dyn.dt / (double)I.dyn.substeps;
         D.h64 = h;
@@ -341,34 +354,41 @@ static void fill_desc(Inst &I)
         D.h32 = (float)h;
         D.hh32 = (float)(h * 0.5);
         D.h6_32 = (float)(h / 6.0);
+        D.hr32 = radius_of(h, D.h32);
+        D.hhr32 = radius_of(h * 0.5, D.hh32);
+        D.h6r32 = radius_of(h / 6.0, D.h6_32);
     }
     for (int d = 0; d < MAXN; d++) {
         D.lo[d] = d < n ? I.grid.lo[d] : 0;
         D.hi[d] = d < n ? I.grid.hi[d] : 1;
         D.lo32[d] = (float)D.lo[d];
+        D.lor32[d] = radius_of(D.lo[d], D.lo32[d]);
         D.n0[d] = d < n ? I.grid.root_cells[d] : 1;
         for (int L = 0; L <= MAXL; L++) {
             D.w64[L][d] = (D.hi[d] - D.lo[d]) / (double)((int64_t)D.n0[d] << L);
             D.w32[L][d] = (float)D.w64[L][d];
+            D.wr32[L][d] = radius_of(D.w64[L][d], D.w32[L][d]);
         }
         const double wf = D.w64[I.Lf][d];
         D.invwf32[d] = (float)(1.0 / wf);
-        // FP32 t = (y - lo32) * invw: rounding of lo, of the difference, of the
-        // product and of 1/w, for |t| <= Nf + 1, bounded in Lf cell widths.
+        // FP32 t = (y - lo32) * invw for |y| within the box of X widened by its
+        // size: rounding of lo, of the difference, of the product and of 1/w,
+        // bounded in Lf cell widths (x2 margin), plus the optional band.
         const double Nf = (double)((int64_t)D.n0[d] << I.Lf);
         const double lo_err = std::fabs((double)D.lo32[d] - D.lo[d]) / wf;
-        const double scale = std::max(std::fabs(D.lo[d]), std::fabs(D.hi[d])) / wf + Nf + 2.0;
+        const double scale = 2.0 * std::max(std::fabs(D.lo[d]), std::fabs(D.hi[d])) / wf + Nf + 2.0;
         const double tb = 2.0 * (lo_err + scale * 4.0 * 5.96e-8);
-        D.band_t[d] = (float)(I.band + tb);
-        D.cand32[d] = (float)(2.0 * I.band * wf);
+        D.tmargin[d] = (float)(I.band + tb);
     }
     const int k = I.grid.k_samples;
     for (int j = 0; j < MAXK; j++) {
         const double f = (k == 1) ? 0.5 : (j < k ? (double)j / (double)(k - 1) : 0.0);
         D.frac64[j] = f;
         D.frac32[j] = (float)f;
+        D.fracr32[j] = radius_of(f, D.frac32[j]);
     }
     D.u32 = I.u32;
+    D.ur32 = I.ur32;
     D.u64 = I.u64;
     D.lvl = I.lvl;
     D.state = I.state;
@@ -487,15 +507,18 @@ struct Engine {
             I->n_fresh = R;
             alloc_nodes(*I, R);
             mem.grow(I->live[0], I->cap_live[0], R, 0);
-            mem.grow(I->box32, I->cap_pairs, (size_t)R * I->nu * 2 * dyn.n, 0);
+            mem.grow(I->box32, I->cap_pairs, (size_t)R * I->nu * 4 * dyn.n, 0);
             size_t c64 = 0, cex = 0;
             mem.grow(I->box64, c64, (size_t)R * I->nu * 2 * dyn.n, 0);
             mem.grow(I->exact, cex, (size_t)R * I->nu, 0);
             I->cap_pairs = (size_t)R * I->nu;
-            std::vector<float> u32(I->u.begin(), I->u.end());
+            std::vector<float> u32(I->u.begin(), I->u.end()), ur32(I->u.size());
+            for (size_t j = 0; j < I->u.size(); j++) ur32[j] = radius_of(I->u[j], u32[j]);
             I->u32 = (float *)mem.alloc(u32.size() * sizeof(float));
+            I->ur32 = (float *)mem.alloc(ur32.size() * sizeof(float));
             I->u64 = (double *)mem.alloc(I->u.size() * sizeof(double));
             CK(cudaMemcpyAsync(I->u32, u32.data(), u32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(I->ur32, ur32.data(), ur32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
             CK(cudaMemcpyAsync(I->u64, I->u.data(), I->u.size() * sizeof(double), cudaMemcpyHostToDevice, st));
             CK(launch_init_roots(I->lvl, I->state, I->idx, I->child, I->live[0], dyn.n, grid.root_cells, R, st));
         } catch (...) {
@@ -531,8 +554,8 @@ struct Engine {
             alloc_nodes(I, target);
             const size_t n2 = (size_t)2 * I.dyn.n;
             const size_t keep = (size_t)I.n_nodes * I.nu;
-            size_t c32 = I.cap_pairs * n2, c64 = I.cap_pairs * n2, cex = I.cap_pairs;
-            mem.grow(I.box32, c32, I.cap_nodes * I.nu * n2, keep * n2);
+            size_t c32 = I.cap_pairs * 2 * n2, c64 = I.cap_pairs * n2, cex = I.cap_pairs;
+            mem.grow(I.box32, c32, I.cap_nodes * I.nu * 2 * n2, keep * 2 * n2);
             mem.grow(I.box64, c64, I.cap_nodes * I.nu * n2, keep * n2);
             mem.grow(I.exact, cex, I.cap_nodes * I.nu, keep);
             I.cap_pairs = I.cap_nodes * I.nu;
@@ -731,10 +754,11 @@ struct Engine {
         CK(launch_scan_i32(cnt, off, P, scratch, st));
         timer.end();
         int64_t hE = 0;
-        int32_t hq[2] = {0, 0};
+        int32_t hq[5] = {0, 0, 0, 0, 0};
         CK(cudaMemcpyAsync(&hE, off + P, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(hq, ctl + 6, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hq, ctl + 6, 5 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         sync();
+        if (last_recheck > 0) cum.cum_recheck_samples += hq[4];
         if (hq[1] != 0) throw Error{GIS_EBOUNDS, "subdivision tree descent overflow"};
         E = hE;
         mem.ensure(tgt, c_tgt, (size_t)std::max<int64_t>(E, 1));
@@ -1001,7 +1025,7 @@ void gis_default_options(gis_options *o)
     std::memset(o, 0, sizeof(*o));
     o->rule = GIS_RULE_INNER;
     o->precision = GIS_FP32_RECHECK;
-    o->band = 1e-2;
+    o->band = 0.0;
     o->lanes_per_pair = 0;
     o->timing = 0;
     o->max_device_bytes = 0;

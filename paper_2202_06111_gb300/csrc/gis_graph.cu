@@ -689,7 +689,8 @@ __global__ void __launch_bounds__(256) k_export_boxes(const InstDesc *__restrict
     const int64_t q = (int64_t)I.live[ls] * I.nu + u;
     const uint16_t x = I.exact[q];
     for (int e = 0; e < 2 * N; e++) {
-        const float f = I.box32[q * 2 * N + e];
+        const float lo = I.box32[q * 4 * N + 2 * e], hi = I.box32[q * 4 * N + 2 * e + 1];
+        const float f = 0.5f * lo + 0.5f * hi;
         if (b32) b32[lp * 2 * N + e] = f;
         if (b64) b64[lp * 2 * N + e] = ((x >> e) & 1) ? I.box64[q * 2 * N + e] : (double)f;
     }

@@ -3,11 +3,13 @@
 // reduce the image bounding box (Eq. 1-3, the image F(B_i) of Def. 1 and the
 // batched one-step maps of Sec. 3.2).
 //
-//  k_prop32   FP32 samples, `G` lanes per pair, group-shuffle min / max
+//  k_prop32   certified FP32 samples (ball arithmetic), `G` lanes per pair,
+//             group-shuffle reduction to an interval around each extreme
 //  k_prop64   FP64 samples in the defining operation order (plain FP64 mode)
-//  k_recheck  FP64 recomputation of the extremes that lie within the band of a
-//             grid line: only the samples whose FP32 image lies within the
-//             candidate window of the FP32 extreme can hold the FP64 extreme
+//  k_bin      decisions at the finest level; an extreme whose interval may
+//             straddle a grid line goes to the recheck queue
+//  k_rc_*     FP64 recomputation of those extremes over the samples whose
+//             ball can reach the extreme (dense: one FP64 sample per lane)
 #include <cfloat>
 
 #include "gis_kernels.cuh"
@@ -16,15 +18,16 @@ namespace gis {
 
 constexpr int PROP_THREADS = 256;
 
-// FP32 lower corner of the cell, widened from the FP64 definition lo + idx w.
+// Ball of sample s of a cell: lo + w (idx + j/(k-1)) per dimension (the exact
+// lattice point), from the FP32 roundings of lo, w and j/(k-1) and their radii.
 template <int N>
-__device__ __forceinline__ void cell_base32(const InstDesc &I, int node, int L, float *base, float *w)
+__device__ __forceinline__ void sampleB(const InstDesc &I, int L, const int32_t *idx, const float *fr,
+                                        const float *frr, Ball *x)
 {
 #pragma unroll
     for (int d = 0; d < N; d++) {
-        double b = I.lo[d] + (double)I.idx[d][node] * I.w64[L][d];
-        base[d] = (float)b;
-        w[d] = I.w32[L][d];
+        const Ball t = badd(bexact((float)idx[d]), Ball{fr[d], frr[d]});
+        x[d] = bfma(Ball{I.w32[L][d], I.wr32[L][d]}, t, Ball{I.lo32[d], I.lor32[d]});
     }
 }
 
@@ -35,30 +38,38 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop32(const InstDesc *__restr
     constexpr int N = DY::N;
     constexpr int PPB = PROP_THREADS / G;
     __shared__ int s_r;
-    __shared__ float s_p[GIS_NPARAM];
-    __shared__ float s_frac[MAXS * N];
+    __shared__ float s_p[GIS_NPARAM], s_pr[GIS_NPARAM];
+    __shared__ float s_fr[MAXS * N], s_frr[MAXS * N];
     if (threadIdx.x == 0) s_r = find_range(R, nr, blockIdx.x);
     __syncthreads();
     const Range rg = R[s_r];
     const InstDesc &I = D[rg.inst];
     const int S = I.S, k = I.k;
-    if (threadIdx.x < GIS_NPARAM) s_p[threadIdx.x] = I.p32[threadIdx.x];
+    if (threadIdx.x < GIS_NPARAM) {
+        s_p[threadIdx.x] = I.p32[threadIdx.x];
+        s_pr[threadIdx.x] = I.pr32[threadIdx.x];
+    }
     for (int t = threadIdx.x; t < S; t += PROP_THREADS) {
         int r = t;
 #pragma unroll
         for (int d = 0; d < N; d++) {
-            s_frac[t * N + d] = I.frac32[r % k];
+            s_fr[t * N + d] = I.frac32[r % k];
+            s_frr[t * N + d] = I.fracr32[r % k];
             r /= k;
         }
     }
     __syncthreads();
-    const M32 M{s_p, I.m, I.substeps, I.h32, I.hh32, I.h6_32};
+    const MB M{s_p, s_pr, I.m, I.substeps, {I.h32, I.hr32}, {I.hh32, I.hhr32}, {I.h6_32, I.h6r32}};
     const int64_t local = (int64_t)(blockIdx.x - rg.block_start) * PPB + threadIdx.x / G;
     const bool valid = local < rg.count;
     const int lane = threadIdx.x & (G - 1);
-    float mn[N], mx[N];
+    // per dimension: min and max of (m - r) and of (m + r) over the samples
+    float lomin[N], himin[N], lomax[N], himax[N];
 #pragma unroll
-    for (int d = 0; d < N; d++) { mn[d] = FLT_MAX; mx[d] = -FLT_MAX; }
+    for (int d = 0; d < N; d++) {
+        lomin[d] = himin[d] = INFINITY;
+        lomax[d] = himax[d] = -INFINITY;
+    }
     int bad = 0;
     int64_t q = 0;
     if (valid) {
@@ -67,21 +78,25 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop32(const InstDesc *__restr
         const int u = (int)(lp - (int64_t)ls * I.nu);
         const int node = I.live[ls];
         const int L = I.lvl[node];
-        float base[N], w[N];
-        cell_base32<N>(I, node, L, base, w);
-        float uu[MAXN];
-        for (int j = 0; j < I.m; j++) uu[j] = I.u32[u * I.m + j];
+        int32_t idx[N];
+#pragma unroll
+        for (int d = 0; d < N; d++) idx[d] = I.idx[d][node];
+        Ball uu[MAXN];
+        for (int j = 0; j < I.m; j++) uu[j] = Ball{I.u32[u * I.m + j], I.ur32[u * I.m + j]};
         q = (int64_t)node * I.nu + u;
         for (int s = lane; s < S; s += G) {
-            float x[N], y[N];
-#pragma unroll
-            for (int d = 0; d < N; d++) x[d] = fmaf(w[d], s_frac[s * N + d], base[d]);
-            step32<DY>(M, x, uu, y);
+            Ball x[N], y[N];
+            sampleB<N>(I, L, idx, s_fr + s * N, s_frr + s * N, x);
+            stepB<DY>(M, x, uu, y);
 #pragma unroll
             for (int d = 0; d < N; d++) {
-                bad |= !(fabsf(y[d]) <= FLT_MAX);
-                mn[d] = fminf(mn[d], y[d]);
-                mx[d] = fmaxf(mx[d], y[d]);
+                const Ball yb = bfinal(y[d]);
+                const float a = __fsub_rd(yb.m, yb.r), b = __fadd_ru(yb.m, yb.r);
+                bad |= !(fabsf(a) <= FLT_MAX && fabsf(b) <= FLT_MAX);
+                lomin[d] = fminf(lomin[d], a);
+                himin[d] = fminf(himin[d], b);
+                lomax[d] = fmaxf(lomax[d], a);
+                himax[d] = fmaxf(himax[d], b);
             }
         }
     }
@@ -89,20 +104,23 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop32(const InstDesc *__restr
     for (int off = G / 2; off > 0; off >>= 1) {
 #pragma unroll
         for (int d = 0; d < N; d++) {
-            mn[d] = fminf(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], off, G));
-            mx[d] = fmaxf(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], off, G));
+            lomin[d] = fminf(lomin[d], __shfl_xor_sync(0xffffffffu, lomin[d], off, G));
+            himin[d] = fminf(himin[d], __shfl_xor_sync(0xffffffffu, himin[d], off, G));
+            lomax[d] = fmaxf(lomax[d], __shfl_xor_sync(0xffffffffu, lomax[d], off, G));
+            himax[d] = fmaxf(himax[d], __shfl_xor_sync(0xffffffffu, himax[d], off, G));
         }
         bad |= __shfl_xor_sync(0xffffffffu, bad, off, G);
     }
     if (valid) {
         for (int e = lane; e < 2 * N; e += G) {
-            float v = 0.0f;
+            float a = 0.0f, b = 0.0f;
 #pragma unroll
             for (int d = 0; d < N; d++) {
-                if (e == d) v = mn[d];
-                if (e == N + d) v = mx[d];
+                if (e == d) { a = lomin[d]; b = himin[d]; }
+                if (e == N + d) { a = lomax[d]; b = himax[d]; }
             }
-            I.box32[q * 2 * N + e] = v;
+            I.box32[q * 4 * N + 2 * e] = a;
+            I.box32[q * 4 * N + 2 * e + 1] = b;
         }
         if (lane == 0) I.exact[q] = bad ? EX_NF32 : 0;
     }
@@ -154,8 +172,10 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop64(const InstDesc *__restr
     for (int d = 0; d < N; d++) {
         I.box64[q * 2 * N + d] = mn[d];
         I.box64[q * 2 * N + N + d] = mx[d];
-        I.box32[q * 2 * N + d] = (float)mn[d];
-        I.box32[q * 2 * N + N + d] = (float)mx[d];
+        I.box32[q * 4 * N + 2 * d] = __double2float_rd(mn[d]);
+        I.box32[q * 4 * N + 2 * d + 1] = __double2float_ru(mn[d]);
+        I.box32[q * 4 * N + 2 * (N + d)] = __double2float_rd(mx[d]);
+        I.box32[q * 4 * N + 2 * (N + d) + 1] = __double2float_ru(mx[d]);
     }
     I.exact[q] = (uint16_t)(((1u << (2 * N)) - 1u) | (bad ? EX_NF64 : 0));
 }
@@ -180,21 +200,26 @@ __device__ __forceinline__ void decide_exact(const InstDesc &I, int e, double v,
     }
 }
 
-// FP32 decision; false if the extreme lies within the band of a grid line of
-// X (t in (-1/2, Nf + 1/2)) and must be recomputed in FP64.
+// FP32 decision from the certified interval [a, b] of an extreme; false if its
+// t-range (widened by the FP32 t-computation bound) may hold a grid line of X
+// (an integer in [0, Nf]): then the extreme must be recomputed in FP64.
 template <int N>
-__device__ __forceinline__ bool decide_approx(const InstDesc &I, int e, float v, int32_t &out, bool &inx)
+__device__ __forceinline__ bool decide_approx(const InstDesc &I, int e, float a, float b, int32_t &out, bool &inx)
 {
     const int d = e % N;
-    const float t = (v - I.lo32[d]) * I.invwf32[d];
+    const float tA = (a - I.lo32[d]) * I.invwf32[d];
+    const float tB = (b - I.lo32[d]) * I.invwf32[d];
     const float Nf = (float)(I.n0[d] << I.Lf);
-    if (t > -0.5f && t < Nf + 0.5f && fabsf(t - rintf(t)) < I.band_t[d]) return false;
+    float k0 = ceilf(tA - I.tmargin[d]), k1 = floorf(tB + I.tmargin[d]);
+    k0 = fmaxf(k0, 0.0f);
+    k1 = fminf(k1, Nf);
+    if (!(k0 > k1)) return false;       // also catches NaN
     if (e < N) {
-        out = (int32_t)fminf(fmaxf(ceilf(t), 0.0f), Nf + 1.0f);
-        inx = inx && (t >= 0.0f);
+        out = (int32_t)fminf(fmaxf(ceilf(tB), 0.0f), Nf + 1.0f);
+        inx = inx && (tB > 0.0f);
     } else {
-        out = (int32_t)fminf(fmaxf(floorf(t), -1.0f), Nf);
-        inx = inx && (t <= Nf);
+        out = (int32_t)fminf(fmaxf(floorf(tA), -1.0f), Nf);
+        inx = inx && (tA < Nf);
     }
     return true;
 }
@@ -233,7 +258,8 @@ __global__ void __launch_bounds__(256) k_bin(const InstDesc *__restrict__ D, con
 #pragma unroll
         for (int e = 0; e < 2 * N; e++) {
             if ((ex >> e) & 1) decide_exact<N>(I, e, I.box64[q * 2 * N + e], out[e], inx);
-            else if (!decide_approx<N>(I, e, I.box32[q * 2 * N + e], out[e], inx)) mask |= 1u << e;
+            else if (!decide_approx<N>(I, e, I.box32[q * 4 * N + 2 * e], I.box32[q * 4 * N + 2 * e + 1], out[e], inx))
+                mask |= 1u << e;
         }
     }
     if (mask) {
@@ -291,34 +317,39 @@ __global__ void __launch_bounds__(256) k_rc_cand(const InstDesc *__restrict__ D,
             mxk[(int64_t)it * N + lane] = dkey(-INFINITY);
         }
         if (lane == 0) bad[it] = 0;
-        float base[N], w[N];
-        cell_base32<N>(I, node, L, base, w);
-        float u32[MAXN];
-        for (int j = 0; j < I.m; j++) u32[j] = I.u32[u * I.m + j];
-        float v32[2 * N];
+        int32_t idx[N];
 #pragma unroll
-        for (int e = 0; e < 2 * N; e++) v32[e] = I.box32[q * 2 * N + e];
-        const M32 M3{I.p32, I.m, I.substeps, I.h32, I.hh32, I.h6_32};
+        for (int d = 0; d < N; d++) idx[d] = I.idx[d][node];
+        Ball uu[MAXN];
+        for (int j = 0; j < I.m; j++) uu[j] = Ball{I.u32[u * I.m + j], I.ur32[u * I.m + j]};
+        float lim[2 * N];                  // hi end of a min extreme, lo end of a max extreme
+#pragma unroll
+        for (int e = 0; e < 2 * N; e++) lim[e] = I.box32[q * 4 * N + 2 * e + (e < N ? 1 : 0)];
+        const MB M{I.p32, I.pr32, I.m, I.substeps, {I.h32, I.hr32}, {I.hh32, I.hhr32}, {I.h6_32, I.h6r32}};
         for (int s0 = 0; s0 < I.S; s0 += 32) {
             const int s = s0 + lane;
             bool c = false;
             if (s < I.S) {
                 c = all64;
                 if (!c) {
-                    float x[N], y[N];
+                    float fr[N], frr[N];
                     int r = s;
 #pragma unroll
                     for (int d = 0; d < N; d++) {
-                        x[d] = fmaf(w[d], I.frac32[r % I.k], base[d]);
+                        fr[d] = I.frac32[r % I.k];
+                        frr[d] = I.fracr32[r % I.k];
                         r /= I.k;
                     }
-                    step32<DY>(M3, x, u32, y);
+                    Ball x[N], y[N];
+                    sampleB<N>(I, L, idx, fr, frr, x);
+                    stepB<DY>(M, x, uu, y);
 #pragma unroll
                     for (int e = 0; e < 2 * N; e++) {
                         if (!((mask >> e) & 1)) continue;
-                        const int d = e % N;
-                        if (e < N) c |= !(y[d] > v32[e] + I.cand32[d]);
-                        else c |= !(y[d] < v32[e] - I.cand32[d]);
+                        const Ball yb = bfinal(y[e % N]);
+                        // the sample can hold the extreme unless its ball lies beyond the limit
+                        if (e < N) c |= !(__fsub_rd(yb.m, yb.r) > lim[e]);
+                        else c |= !(__fadd_ru(yb.m, yb.r) < lim[e]);
                     }
                 }
             }
@@ -413,7 +444,7 @@ __global__ void __launch_bounds__(256) k_rc_final(const InstDesc *__restrict__ D
 #pragma unroll
         for (int e = 0; e < 2 * N; e++) {
             if ((ex >> e) & 1) decide_exact<N>(I, e, I.box64[q * 2 * N + e], out[e], inx);
-            else decide_approx<N>(I, e, I.box32[q * 2 * N + e], out[e], inx);
+            else decide_approx<N>(I, e, I.box32[q * 4 * N + 2 * e], I.box32[q * 4 * N + 2 * e + 1], out[e], inx);
         }
 #pragma unroll
         for (int e = 0; e < 2 * N; e++) rng[p * 2 * N + e] = out[e];

@@ -69,7 +69,8 @@ _STAT_FIELDS = [("finest_level", C.c_int32), ("level", C.c_int32), ("n_nodes", C
                 ("ms_transpose", C.c_double), ("ms_prune", C.c_double), ("ms_classify", C.c_double),
                 ("ms_split", C.c_double), ("ms_other", C.c_double), ("prop_flops", C.c_double),
                 ("graph_bytes", C.c_double), ("prune_bytes", C.c_double), ("count_bytes", C.c_double),
-                ("fill_bytes", C.c_double), ("transpose_bytes", C.c_double), ("cum_launches", C.c_int64)]
+                ("fill_bytes", C.c_double), ("transpose_bytes", C.c_double), ("cum_launches", C.c_int64),
+                ("cum_recheck_samples", C.c_int64)]
 
 
 class gis_stats(C.Structure):
@@ -301,7 +302,7 @@ def batch_solve(problems: list[dict], stream: int | None = None, want_cells: boo
         r.levels = p.get("levels", 0)
         r.rule = RULES[p.get("rule", "inner")]
         r.precision = PRECISIONS[p.get("precision", "fp32")]
-        r.band = p.get("band", 1e-2)
+        r.band = p.get("band", 0.0)
         if want_cells:
             cap = p.get("cells_cap", 2 * int(np.prod(p["n0"])) * (1 + r.levels))
             buf = (gis_cell * cap)()

@@ -56,7 +56,7 @@ def test_struct_layouts_match_header(tmp_path):
 
 def test_default_options(lib):
     o = gis.options()
-    assert o.rule == 0 and o.precision == 1 and o.band == pytest.approx(1e-2) and o.lanes_per_pair == 0
+    assert o.rule == 0 and o.precision == 1 and o.band == 0.0 and o.lanes_per_pair == 0
 
 
 def test_null_arguments_rejected_without_touching_a_gpu(lib):
