@@ -154,6 +154,10 @@ typedef struct {
     double count_bytes, fill_bytes, transpose_bytes; /* the parts of graph_bytes   */
     int64_t cum_launches;   /* kernel launches issued by the library              */
     int64_t cum_recheck_samples; /* samples recomputed in FP64 by the recheck      */
+    int64_t n_cell_edges;   /* edges B_i -> B_j of the current symbolic image (Def. 1:
+                               the union over the controls); n_edges counts the
+                               (cell, control) -> cell edges                       */
+    int64_t cum_cell_edges;
 } gis_stats;
 
 typedef struct gis_ctx gis_ctx;
@@ -227,7 +231,7 @@ typedef struct {
     int32_t levels_done;
     int64_t n_kept;         /* kept cells at the end                              */
     int64_t n_cells;        /* live cells at the end                              */
-    int64_t n_edges_total;  /* edges built over all levels                        */
+    int64_t n_edges_total;  /* cell -> cell edges (Def. 1) built over all levels   */
     int64_t cells_built;    /* live cells graph-built over all levels             */
     gis_cell *cells;        /* caller buffer for the kept cells, or NULL          */
     int64_t cells_cap;

@@ -397,4 +397,43 @@ __device__ __forceinline__ void sample64(const InstDesc &I, int L, const int32_t
     }
 }
 
+// Level-L index range of the leaves meeting [c - 1, f] at the finest level Lf
+// (c = ceil(t_min), f = floor(t_max) at Lf): ceil and floor commute with the
+// exact division by 2^(Lf - L).
+__device__ __forceinline__ void level_range(int c, int f, int sh, int NL, int &a, int &b)
+{
+    a = ((c + (1 << sh) - 1) >> sh) - 1;
+    b = f >> sh;
+    a = a < 0 ? 0 : a;
+    b = b > NL - 1 ? NL - 1 : b;
+}
+
+// Grid-wide barrier for a cooperative launch: a monotone arrival counter, a
+// bounded wait (sets *err = GIS_ETIMEOUT and gives up after spin_limit
+// polls); returns whether the grid may go on.
+__device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t target, int32_t *err, int64_t spin_limit)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        int64_t it = 0;
+        for (;;) {
+            const uint32_t v = *(volatile uint32_t *)bar;
+            if (v >= target) break;
+            if (*(volatile int32_t *)err != 0) break;
+            if (++it > spin_limit) {
+                atomicCAS(err, 0, GIS_ETIMEOUT);
+                break;
+            }
+            __nanosleep(40);
+        }
+        __threadfence();
+        s_ok = *(volatile int32_t *)err == 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 }  // namespace gis

@@ -425,6 +425,16 @@ struct Engine {
     // per-level arrays over the union
     int64_t NL = 0, P = 0, E = 0;
     int32_t *pair_slot = nullptr; size_t c_pair_slot = 0;
+    int64_t Ecell = 0;
+    int32_t *cps = nullptr; size_t c_cps = 0;
+    uint8_t *cinfo = nullptr; size_t c_cinfo = 0;
+    int32_t *pcnt = nullptr; size_t c_pcnt = 0;
+    int32_t *ccnt = nullptr; size_t c_ccnt = 0;
+    int64_t *coff = nullptr; size_t c_coff = 0;
+    int32_t *cent = nullptr; size_t c_cent = 0;
+    uint32_t *cmask = nullptr; size_t c_cmask = 0;
+    uint32_t *rmask = nullptr; size_t c_rmask = 0;
+    uint32_t *vmask = nullptr; size_t c_vmask = 0;
     int32_t *rng = nullptr; size_t c_rng = 0;
     uint8_t *pflag = nullptr; size_t c_pflag = 0;
     int32_t *cnt = nullptr; size_t c_cnt = 0;
@@ -662,17 +672,16 @@ struct Engine {
         number(ids);
         have_graph = have_prune = have_bnd = false;
         const size_t Ps = (size_t)std::max<int64_t>(P, 1), NLs = (size_t)std::max<int64_t>(NL, 1);
-        mem.ensure(pair_slot, c_pair_slot, Ps);
         mem.ensure(rng, c_rng, Ps * 2 * MAXN);
         mem.ensure(pflag, c_pflag, Ps);
-        mem.ensure(cnt, c_cnt, Ps);
-        mem.ensure(off, c_off, Ps + 1);
         mem.ensure(rq, c_rq, Ps);
         mem.ensure(scratch, c_scratch, scan_scratch_bytes(std::max<int64_t>(P, NL) + 1));
 
         timer.begin(PH_OTHER);
         WorkList ws = make_work(slot_ranges(ids), 256);
-        CK(launch_gather(d_desc, ws, pair_slot, st));
+        mem.ensure(cps, c_cps, NLs);
+        mem.ensure(cinfo, c_cinfo, NLs);
+        CK(launch_cgather(d_desc, ws, cps, cinfo, st));
         timer.end();
 
         // propagation of new cells, grouped by (dynamics, n, precision, lanes)
@@ -741,70 +750,80 @@ struct Engine {
             timer.end();
         }
 
-        // count, scan, fill
-        timer.begin(PH_COUNT);
-        for (int n = 1; n <= MAXN; n++) {
-            auto sub = with_n(ids, n);
-            if (sub.empty()) continue;
-            CK(launch_edges(false, n, d_desc, make_work(pair_ranges(sub), 256), rng, pflag, cnt, nullptr, nullptr,
-                            ctl + 7, st));
-        }
-        timer.end();
-        timer.begin(PH_SCAN);
-        CK(launch_scan_i32(cnt, off, P, scratch, st));
-        timer.end();
-        int64_t hE = 0;
-        int32_t hq[5] = {0, 0, 0, 0, 0};
-        CK(cudaMemcpyAsync(&hE, off + P, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(hq, ctl + 6, 5 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        sync();
-        if (last_recheck > 0) cum.cum_recheck_samples += hq[4];
-        if (hq[1] != 0) throw Error{GIS_EBOUNDS, "subdivision tree descent overflow"};
-        E = hE;
-        mem.ensure(tgt, c_tgt, (size_t)std::max<int64_t>(E, 1));
-        mem.ensure(rsrc, c_rsrc, (size_t)std::max<int64_t>(E, 1));
-        timer.begin(PH_FILL);
-        for (int n = 1; n <= MAXN; n++) {
-            auto sub = with_n(ids, n);
-            if (sub.empty()) continue;
-            CK(launch_edges(true, n, d_desc, make_work(pair_ranges(sub), 256), rng, pflag, cnt, off, tgt, ctl + 7,
-                            st));
-        }
-        timer.end();
-
-        // transpose
-        timer.begin(PH_TRANSPOSE);
+        // count the cell graph, scan edges and in-degrees, fill edges and
+        // reverse edges (the transpose is fused into the fill)
+        mem.ensure(pcnt, c_pcnt, Ps);
+        mem.ensure(ccnt, c_ccnt, NLs);
+        mem.ensure(coff, c_coff, NLs + 1);
         mem.ensure(rcnt, c_rcnt, NLs);
         mem.ensure(roff, c_roff, NLs + 1);
         mem.ensure(rcur, c_rcur, NLs);
         CK(cudaMemsetAsync(rcnt, 0, NLs * sizeof(int32_t), st));
-        CK(launch_indeg(tgt, E, rcnt, st));
+        CK(cudaMemsetAsync(ctl + 12, 0, 2 * sizeof(int32_t), st));
+        CellGraph g{rng, pflag, pcnt, ccnt, rcnt, coff, nullptr, nullptr, (unsigned long long *)rcur, nullptr,
+                    nullptr, (unsigned long long *)(ctl + 12), ctl + 7};
+        timer.begin(PH_COUNT);
+        for (int n = 1; n <= MAXN; n++) {
+            auto sub = with_n(ids, n);
+            if (sub.empty()) continue;
+            CK(launch_cedges(false, n, d_desc, make_work(slot_ranges(sub), cedges_cells_per_block()), g, st));
+        }
+        timer.end();
+        timer.begin(PH_SCAN);
+        CK(launch_scan_i32(ccnt, coff, NL, scratch, st));
         CK(launch_scan_i32(rcnt, roff, NL, scratch, st));
+        timer.end();
+        int64_t hEc = 0;
+        int32_t hq[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        CK(cudaMemcpyAsync(&hEc, coff + NL, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hq, ctl + 6, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        sync();
+        if (last_recheck > 0) cum.cum_recheck_samples += hq[4];
+        if (hq[1] != 0) throw Error{GIS_EBOUNDS, "subdivision tree descent overflow"};
+        unsigned long long hpe = 0;
+        std::memcpy(&hpe, hq + 6, sizeof(hpe));
+        E = (int64_t)hpe;
+        Ecell = hEc;
+        mem.ensure(cent, c_cent, (size_t)std::max<int64_t>(Ecell, 1));
+        mem.ensure(cmask, c_cmask, (size_t)std::max<int64_t>(Ecell, 1));
+        mem.ensure(rsrc, c_rsrc, (size_t)std::max<int64_t>(Ecell, 1));
+        mem.ensure(rmask, c_rmask, (size_t)std::max<int64_t>(Ecell, 1));
+        g.cent = cent;
+        g.cmask = cmask;
+        g.rsrc = rsrc;
+        g.rmask = rmask;
+        timer.begin(PH_FILL);
         CK(cudaMemcpyAsync(rcur, roff, NLs * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
-        CK(launch_rscatter(off, tgt, P, rcur, rsrc, st));
+        for (int n = 1; n <= MAXN; n++) {
+            auto sub = with_n(ids, n);
+            if (sub.empty()) continue;
+            CK(launch_cedges(true, n, d_desc, make_work(slot_ranges(sub), cedges_cells_per_block()), g, st));
+        }
         timer.end();
 
         for (int i : ids) inst[i]->cells_built += inst[i]->n_live;
         cum.cum_cells_built += NL;
         cum.cum_pairs_propagated += last_new_pairs;
         cum.cum_edges += E;
+        cum.cum_cell_edges += Ecell;
         cum.cum_recheck += last_recheck;
-        // algorithmic bytes per pair: count reads the decisions (8n) and the flag,
-        // writes cnt and the flag; fill reads decisions, flag and offset, writes
-        // 4 per edge; transpose reads every target twice, writes rsrc, reads offsets.
+        // algorithmic bytes. count: per pair the decisions (8n), the flag (read and
+        // write) and the target count; per cell the edge count; per cell edge the
+        // in-degree update (8). fill: per pair decisions and flag, per cell the
+        // offset; per cell edge the edge (8), the reverse cursor update (16) and
+        // the reverse edge (8).
         double cb = 0, fb = 0;
         for (int i : ids) {
             const Inst &I = *inst[i];
             const double pairs = (double)I.n_live * I.nu;
-            cb += pairs * (8.0 * I.dyn.n + 1 + 4 + 1);
-            fb += pairs * (8.0 * I.dyn.n + 1 + 8);
+            cb += pairs * (8.0 * I.dyn.n + 1 + 4 + 1) + 4.0 * (double)I.n_live;
+            fb += pairs * (8.0 * I.dyn.n + 1) + 8.0 * (double)I.n_live;
         }
-        fb += 4.0 * E;
-        const double tb = 4.0 * E + 4.0 * E + 4.0 * E + 8.0 * P + 16.0 * NL;
+        cb += 8.0 * (double)Ecell;
+        fb += 32.0 * (double)Ecell;
         cum.count_bytes += cb;
         cum.fill_bytes += fb;
-        cum.transpose_bytes += tb;
-        cum.graph_bytes += cb + fb + tb;
+        cum.graph_bytes += cb + fb;
         have_graph = true;
     }
 
@@ -814,7 +833,7 @@ struct Engine {
         if (!have_graph) throw Error{GIS_ESTATE, "prune needs a graph"};
         const size_t NLs = (size_t)std::max<int64_t>(NL, 1), Ps = (size_t)std::max<int64_t>(P, 1);
         mem.ensure(pstate, c_pstate, Ps);
-        mem.ensure(ncnt, c_ncnt, NLs);
+        mem.ensure(vmask, c_vmask, NLs);
         mem.ensure(alive, c_alive, NLs);
         mem.ensure(front[0], c_front[0], NLs);
         mem.ensure(front[1], c_front[1], NLs);
@@ -822,13 +841,15 @@ struct Engine {
         CK(cudaMemsetAsync(ctl, 0, 6 * sizeof(int32_t), st));
         CK(cudaMemsetAsync(ctl + 8, 0, 2 * sizeof(int32_t), st));
         WorkList ws = make_work(slot_ranges(step), 256);
-        CK(launch_prune_init(0, d_desc, ws, off, pflag, pstate, ncnt, alive, front[0], (uint32_t *)ctl, st));
-        PruneArgs a{};
+        CK(launch_cprune_init(d_desc, ws, pflag, pcnt, pstate, vmask, alive, front[0], (uint32_t *)ctl, st));
+        CPruneArgs a{};
         a.roff = roff;
         a.rsrc = rsrc;
-        a.pair_slot = pair_slot;
-        a.pstate = pstate;
-        a.ncnt = ncnt;
+        a.rmask = rmask;
+        a.cps = cps;
+        a.cinfo = cinfo;
+        a.pc = pstate;
+        a.vmask = vmask;
         a.alive = alive;
         a.frontier[0] = front[0];
         a.frontier[1] = front[1];
@@ -839,7 +860,7 @@ struct Engine {
         a.scanned = (unsigned long long *)(ctl + 8);
         a.round_limit = opt.round_limit > 0 ? opt.round_limit : ((int64_t)1 << 30);
         a.spin_limit = (int64_t)1 << 25;
-        if (NL > 0) CK(launch_prune(a, NL, st));
+        if (NL > 0) CK(launch_cprune(a, NL, st));
         timer.end();
         mem.ensure(inst_i64, c_inst_i64, inst.size() + 1);
         CK(cudaMemsetAsync(inst_i64, 0, inst.size() * sizeof(int64_t), st));
@@ -859,7 +880,10 @@ struct Engine {
             last_kept += kept[i];
         }
         const double dead = (double)(NL - last_kept);
-        cum.prune_bytes += (double)P * (8 + 1 + 4) + (double)NL * (4 + 1) + 24.0 * dead + 12.0 * (double)scanned;
+        // init: per pair flag, target count and counter (9), per cell mask and flag (5);
+        // per removed cell its reverse offsets and frontier slots (24); per reverse
+        // edge walked its source, mask, info byte and the mask update (17)
+        cum.prune_bytes += (double)P * 9 + (double)NL * 5 + 24.0 * dead + 17.0 * (double)scanned;
         have_prune = true;
     }
 
@@ -967,6 +991,7 @@ struct Engine {
             s->n_pairs = I.n_live * I.nu;
         }
         s->n_edges = have_graph ? E : 0;
+        s->n_cell_edges = have_graph ? Ecell : 0;
         s->n_kept = last_kept;
         s->n_split = last_split;
         s->n_new_pairs = last_new_pairs;
@@ -1138,12 +1163,19 @@ gis_status gis_get_graph(gis_ctx *ctx, int64_t *off, int32_t *tgt, uint8_t *flag
     if (n_pairs) *n_pairs = E.P;
     if (n_edges) *n_edges = E.E;
     if (tgt && cap_edges < E.E) return GIS_EBOUNDS;
-    if (off) CK(cudaMemcpyAsync(off, E.off, (E.P + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, E.st));
-    if (tgt && E.E) CK(cudaMemcpyAsync(tgt, E.tgt, E.E * sizeof(int32_t), cudaMemcpyDeviceToHost, E.st));
-    if (flag && E.P) {
-        CK(cudaMemcpyAsync(flag, E.pflag, E.P, cudaMemcpyDeviceToHost, E.st));
-    }
+    // per-(cell, control) CSR expanded from the cell graph
+    int64_t *poff = (int64_t *)E.mem.alloc((E.P + 1) * sizeof(int64_t));
+    int32_t *dt = (int32_t *)E.mem.alloc(std::max<int64_t>(E.E, 1) * sizeof(int32_t));
+    E.mem.ensure(E.scratch, E.c_scratch, scan_scratch_bytes(E.P + 1));
+    CK(launch_scan_i32(E.pcnt, poff, E.P, E.scratch, E.st));
+    WorkList w8 = E.make_work(E.slot_ranges({0}), 8);
+    CK(launch_cexport(E.d_desc, w8, E.coff, E.cent, E.cmask, poff, dt, E.st));
+    if (off) CK(cudaMemcpyAsync(off, poff, (E.P + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, E.st));
+    if (tgt && E.E) CK(cudaMemcpyAsync(tgt, dt, E.E * sizeof(int32_t), cudaMemcpyDeviceToHost, E.st));
+    if (flag && E.P) CK(cudaMemcpyAsync(flag, E.pflag, E.P, cudaMemcpyDeviceToHost, E.st));
     E.sync();
+    E.mem.free(poff);
+    E.mem.free(dt);
     if (flag)
         for (int64_t p = 0; p < E.P; p++) flag[p] &= (GIS_PAIR_INX | GIS_PAIR_TOUCH_DEAD | GIS_PAIR_NONFINITE);
     API_END(ctx)
@@ -1212,19 +1244,21 @@ gis_status gis_batch_solve(const gis_request *reqs, int32_t n, gis_result *res, 
         while (!act.empty()) {
             E->build_graph(act);
             E->prune();
-            for (int i : act) E->inst[i]->edges_total += 0;
-            // per-instance edges of this level
-            std::vector<int64_t> offs(2 * act.size());
+            // per-instance cell edges of this level, one gather kernel
             {
-                std::vector<int64_t> h(act.size() * 2);
+                std::vector<int64_t> be(2 * act.size()), h(act.size());
                 for (size_t j = 0; j < act.size(); j++) {
-                    Inst &I = *E->inst[act[j]];
-                    CK(cudaMemcpyAsync(&h[2 * j], E->off + I.pair_base, sizeof(int64_t), cudaMemcpyDeviceToHost, E->st));
-                    CK(cudaMemcpyAsync(&h[2 * j + 1], E->off + I.pair_base + I.n_live * I.nu, sizeof(int64_t),
-                                       cudaMemcpyDeviceToHost, E->st));
+                    be[2 * j] = E->inst[act[j]]->slot_base;
+                    be[2 * j + 1] = E->inst[act[j]]->slot_base + E->inst[act[j]]->n_live;
                 }
+                E->mem.ensure(E->inst_i64, E->c_inst_i64, 3 * act.size() + 2);
+                CK(cudaMemcpyAsync(E->inst_i64, be.data(), be.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                   E->st));
+                CK(launch_inst_totals(E->coff, E->inst_i64, (int)act.size(), E->inst_i64 + 2 * act.size(), E->st));
+                CK(cudaMemcpyAsync(h.data(), E->inst_i64 + 2 * act.size(), h.size() * sizeof(int64_t),
+                                   cudaMemcpyDeviceToHost, E->st));
                 E->sync();
-                for (size_t j = 0; j < act.size(); j++) E->inst[act[j]]->edges_total += h[2 * j + 1] - h[2 * j];
+                for (size_t j = 0; j < act.size(); j++) E->inst[act[j]]->edges_total += h[j];
             }
             std::vector<int> cont, fin;
             for (int i : act) (E->inst[i]->level < E->inst[i]->levels ? cont : fin).push_back(i);

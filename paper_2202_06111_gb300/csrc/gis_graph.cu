@@ -29,17 +29,6 @@ long long launches_total() { return t_launches; }
     if (local >= rg.count) return;                                            \
     const InstDesc &I = D[rg.inst];
 
-// Level-L index range of the leaves meeting [c - 1, f] at the finest level Lf
-// (c = ceil(t_min), f = floor(t_max) at Lf): ceil and floor commute with the
-// exact division by 2^(Lf - L).
-__device__ __forceinline__ void level_range(int c, int f, int sh, int NL, int &a, int &b)
-{
-    a = ((c + (1 << sh) - 1) >> sh) - 1;
-    b = f >> sh;
-    a = a < 0 ? 0 : a;
-    b = b > NL - 1 ? NL - 1 : b;
-}
-
 // Visit every leaf of the tree whose level-L index lies in the per-level
 // ranges given by RF(L, d, a, b). Visitor V(node, state) returns false to stop.
 template <int N, class RF, class V>
@@ -313,14 +302,6 @@ __global__ void k_rscatter(const int64_t *__restrict__ off, const int32_t *__res
     }
 }
 
-static int grid_for(int64_t n, int per_block, int cap_blocks)
-{
-    int64_t b = (n + per_block - 1) / per_block;
-    if (b < 1) b = 1;
-    if (b > cap_blocks) b = cap_blocks;
-    return (int)b;
-}
-
 cudaError_t launch_indeg(const int32_t *tgt, int64_t E, int32_t *rcnt, cudaStream_t st)
 {
     if (E == 0) return cudaSuccess;
@@ -379,34 +360,6 @@ cudaError_t launch_prune_init(int rule, const InstDesc *D, const WorkList &w, co
     k_prune_init<<<(unsigned)w.n_blocks, 256, 0, st>>>(D, w.d_ranges, w.n_ranges, off, pflag, pstate, ncnt, alive,
                                                        frontier0, sizes); note_launch();
     return cudaGetLastError();
-}
-
-// Grid-wide barrier for a cooperative launch: a monotone arrival counter, a
-// bounded wait (sets *err = GIS_ETIMEOUT and gives up after spin_limit
-// polls); returns whether the grid may go on.
-__device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t target, int32_t *err, int64_t spin_limit)
-{
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(bar, 1u);
-        int64_t it = 0;
-        for (;;) {
-            const uint32_t v = *(volatile uint32_t *)bar;
-            if (v >= target) break;
-            if (*(volatile int32_t *)err != 0) break;
-            if (++it > spin_limit) {
-                atomicCAS(err, 0, GIS_ETIMEOUT);
-                break;
-            }
-            __nanosleep(40);
-        }
-        __threadfence();
-        s_ok = *(volatile int32_t *)err == 0;
-    }
-    __syncthreads();
-    return s_ok != 0;
 }
 
 __global__ void __launch_bounds__(256) k_prune(PruneArgs a)

@@ -11,6 +11,14 @@ namespace gis {
 void note_launch();              // every kernel launch of the library is counted
 long long launches_total();
 
+inline int grid_for(int64_t n, int per_block, int cap_blocks)
+{
+    int64_t b = (n + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > cap_blocks) b = cap_blocks;
+    return (int)b;
+}
+
 struct WorkList {                // ranges of one kernel launch, device copy + block count
     const Range *d_ranges = nullptr;
     int n_ranges = 0;
@@ -85,6 +93,49 @@ struct PruneArgs {
     int64_t spin_limit;
 };
 cudaError_t launch_prune(const PruneArgs &a, int64_t n_slots, cudaStream_t st);
+// ---- the cell graph (edges cell -> cell with a control mask) ----
+struct CellGraph {
+    const int32_t *rng;
+    uint8_t *pflag;
+    int32_t *pcnt;               // targets per pair
+    int32_t *ccnt;               // edges per cell
+    int32_t *rcnt;               // in-degree per cell
+    const int64_t *coff;         // edge offsets per cell (fill pass)
+    int32_t *cent;               // edge target (global slot)
+    uint32_t *cmask;             // edge control mask
+    unsigned long long *rcur;    // reverse cursor per cell (fill pass)
+    int32_t *rsrc;               // reverse edge source
+    uint32_t *rmask;             // reverse edge control mask
+    unsigned long long *pair_edges;  // total (cell, control) -> cell edges
+    int32_t *err;
+};
+cudaError_t launch_cgather(const InstDesc *D, const WorkList &wslots, int32_t *cps, uint8_t *cinfo, cudaStream_t st);
+cudaError_t launch_cedges(bool fill, int n, const InstDesc *D, const WorkList &w, const CellGraph &g, cudaStream_t st);
+int cedges_cells_per_block();
+cudaError_t launch_cprune_init(const InstDesc *D, const WorkList &wslots, const uint8_t *pflag, const int32_t *pcnt,
+                               int32_t *pc, uint32_t *vmask, uint8_t *alive, int32_t *frontier0, uint32_t *sizes,
+                               cudaStream_t st);
+struct CPruneArgs {
+    const int64_t *roff;
+    const int32_t *rsrc;
+    const uint32_t *rmask;
+    const int32_t *cps;          // first pair of each cell
+    const uint8_t *cinfo;        // n_controls | rule << 6
+    int32_t *pc;                 // OUTER: kept targets per pair
+    uint32_t *vmask;             // viable controls per cell
+    uint8_t *alive;
+    int32_t *frontier[2];
+    uint32_t *sizes;
+    uint32_t *bar;
+    int32_t *err;
+    int32_t *rounds;
+    unsigned long long *scanned;
+    int64_t round_limit;
+    int64_t spin_limit;
+};
+cudaError_t launch_cprune(const CPruneArgs &a, int64_t n_slots, cudaStream_t st);
+cudaError_t launch_cexport(const InstDesc *D, const WorkList &w8, const int64_t *coff, const int32_t *cent,
+                           const uint32_t *cmask, const int64_t *poff, int32_t *tgt, cudaStream_t st);
 // mark removed, classify boundary, split
 cudaError_t launch_mark_dead(const InstDesc *D, const WorkList &wslots, const uint8_t *alive, cudaStream_t st);
 cudaError_t launch_classify(int n, const InstDesc *D, const WorkList &wslots, const uint8_t *alive,
