@@ -51,6 +51,8 @@ def _workload(name):
         return dict(W.cartpole_48(), rule="outer")
     if name == "vdp_64":
         return W.vdp_64()
+    if name == "serving_2000":
+        return {"serving": W.serving_2000()}
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -245,6 +247,27 @@ def run_gis(a, prob):
         e2e_times.append(dt)
     e2e_value = (cells / len(stats)) / statistics.mean(e2e_times)
 
+    # the same workload with every sample in FP64 (the plain FP64 GPU form)
+    p64 = dict(prob, precision="fp64")
+    with torch.cuda.stream(stream):
+        c = gis.Context(p64, stream=stream.cuda_stream)
+        c.solve()
+        c.close()
+    fp64_ms = []
+    for _ in range(2):
+        flush.zero_()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            c = gis.Context(p64, stream=stream.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c.solve()
+        e1.record(stream)
+        e1.synchronize()
+        fp64_ms.append(e0.elapsed_time(e1))
+        same = c.stats()["cum_cells_built"] == stats[0]["cum_cells_built"]
+        c.close()
+
     if rank != 0:
         if ws > 1:
             torch.distributed.barrier()
@@ -288,6 +311,9 @@ def run_gis(a, prob):
             "cells_per_step": cells / len(stats), "edges_per_step": edges / len(stats),
             "recheck_pairs_per_step": agg["cum_recheck"] / len(stats),
             "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
+            "fp64_plain": {"ms_per_step": statistics.mean(fp64_ms),
+                           "speedup_of_fp32_recheck": statistics.mean(fp64_ms) / (total_ms / len(per_step)),
+                           "same_cells_built": same},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": 1e3 * statistics.mean(e2e_times)}}
     if ws == 1 and not a.no_cpu_baseline:
@@ -297,9 +323,75 @@ def run_gis(a, prob):
         torch.distributed.barrier()
 
 
+def run_serving(a, reqs):
+    """Real-time replay of Poisson arrivals through the continuous-batching server."""
+    import threading
+
+    import torch
+    from paper_2202_06111_gb300 import build, gis, workloads as W
+
+    build.build()
+    gis.load()
+    dev = torch.cuda.current_device()
+    srv = gis.Server(device=dev)
+    for r in W.serving_2000(count=8, seed=1, max_2d_cells=64.0 ** 2, max_4d_n0=8.0):   # warm-up
+        srv.poll(srv.submit(r), wait=True, want_cells=False)
+    base = srv.stats()
+    lat, done_at = {}, {}
+    submitted = {}
+    lock = threading.Lock()
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, r in enumerate(reqs):
+            wait = t0 + r["arrival_s"] - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            t = srv.submit(r)
+            with lock:
+                submitted[t] = (i, time.perf_counter())
+
+    th = threading.Thread(target=submitter)
+    clk = Clocks(dev)
+    th.start()
+    while len(done_at) < len(reqs):
+        with lock:
+            outstanding = [(t, v) for t, v in submitted.items() if t not in done_at]
+        for t, (i, ts) in outstanding:
+            res = srv.poll(t, wait=False, want_cells=True)
+            if res is not None:
+                now = time.perf_counter()
+                done_at[t] = now
+                lat[i] = (now - ts) * 1e3
+                assert res["status"] == 0, res
+        time.sleep(0.0005)
+    th.join()
+    clocks = clk.stop()
+    wall = max(done_at.values()) - t0
+    st = srv.stats()
+    srv.close()
+    lats = sorted(lat.values())
+    cells = st["cells_built"] - base["cells_built"]
+    line = {"metric": "serving requests/s", "value": len(reqs) / wall, "unit": "requests/s", "n_gpus": 1,
+            "steps": len(reqs), "warmup": 8, "ms_per_step": 1e3 * wall / len(reqs), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving_2000", "requests": len(reqs), "arrivals": "Poisson, mean 200/s",
+                       "systems": "Van der Pol, CSTR, cart-pole", "grids": "32^2-1024^2, 16^4-48^4",
+                       "levels": "0-3", "rule": "inner"},
+            "latency_ms": {"p50": lats[len(lats) // 2], "p99": lats[min(len(lats) - 1, int(0.99 * len(lats)))],
+                           "max": lats[-1]},
+            "cells_per_s": cells / wall, "engine_steps": st["steps"] - base["steps"], "clocks": clocks,
+            "offered_load_s": reqs[-1]["arrival_s"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = _args()
     prob = _workload(a.workload)
+    if "serving" in prob:
+        if a.impl == "gis":
+            run_serving(a, prob["serving"][: a.steps] if a.steps < len(prob["serving"]) else prob["serving"])
+        return
     if a.impl == "reference":
         run_reference(a, prob)
     else:

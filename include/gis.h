@@ -97,7 +97,7 @@ typedef struct {
 } gis_grid;
 
 typedef struct {
-    int32_t n_controls;     /* >= 1                                               */
+    int32_t n_controls;     /* 1..32                                              */
     const double *u;        /* host, n_controls x m row-major; copied at create    */
 } gis_controls;
 
@@ -244,6 +244,50 @@ typedef struct {
  * lanes and limits (rule / precision / band come from each request).        */
 gis_status gis_batch_solve(const gis_request *reqs, int32_t n, gis_result *res,
                            const gis_options *opt, void *stream, gis_stats *stats);
+
+/* ---- serving: continuous batching of requests ------------------------------
+ * A server owns a worker thread, a CUDA stream on `device` and a batch engine.
+ * Each engine step advances every admitted request by one level (build the
+ * graph, prune, and split its boundary cells unless it is done); requests
+ * that arrive meanwhile are admitted at the next step while their estimated
+ * device memory fits the budget, so requests at different levels share every
+ * launch. Results are the same as solving each request alone (the requests'
+ * graphs are disjoint).                                                        */
+typedef struct {
+    int32_t max_active;        /* requests advanced together (0: 1024)                 */
+    int64_t max_device_bytes;  /* admission budget of estimated device memory
+                                  (0: half the free device memory at create)           */
+    int32_t lanes_per_pair;    /* as in gis_options (0: auto)                          */
+    int32_t timing;
+} gis_server_opts;
+
+typedef struct {
+    int64_t submitted, completed, failed, active, queued;
+    int64_t steps;             /* engine steps                                          */
+    int64_t cells_built;       /* live cells graph-built, all requests                 */
+    int64_t cell_edges;        /* cell -> cell edges built, all requests               */
+    int64_t budget_bytes, admitted_bytes; /* admission budget, estimate in use         */
+} gis_server_stats;
+
+typedef struct gis_server gis_server;
+
+/* Start a server on CUDA device `device`. Errors: ECUDA (no device), ENOMEM. */
+gis_status gis_server_create(gis_server **out, const gis_server_opts *opt, int32_t device);
+
+/* Queue a request (copied, controls included); returns its ticket.
+ * EINVAL for a malformed request (checked before queueing).                  */
+gis_status gis_server_submit(gis_server *srv, const gis_request *req, uint64_t *ticket);
+
+/* *done = 0 while the request runs. Once done, fills res (status, counts and
+ * the kept cells into res->cells if not NULL) and forgets the ticket (EINVAL
+ * afterwards). If res->cells_cap is below the kept count, returns EBOUNDS with
+ * res->n_kept set and keeps the ticket. When wait != 0 blocks until done.    */
+gis_status gis_server_poll(gis_server *srv, uint64_t ticket, gis_result *res, int32_t *done, int32_t wait);
+
+gis_status gis_server_get_stats(gis_server *srv, gis_server_stats *out);
+
+/* Stops the worker after the current step; pending requests are dropped. */
+void gis_server_destroy(gis_server *srv);
 
 /* ---- pruning without device allocation ---------------------------------- */
 #define GIS_NOALLOC_MAX_CELLS 131072    /* 2^17 cells                          */

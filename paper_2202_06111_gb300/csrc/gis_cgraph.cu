@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cedges(const InstDesc *__rest
         if (live_box) {
 #pragma unroll
             for (int d = 0; d < N; d++) {
-                const int c = rng[p * 2 * N + d], f = rng[p * 2 * N + N + d];
+                const int c = rng[p * 2 * MAXN + d], f = rng[p * 2 * MAXN + N + d];
                 sc[lane][d] = c;
                 sf[lane][d] = f;
                 int a, b;

@@ -101,15 +101,16 @@ __device__ __forceinline__ int find_range(const Range *__restrict__ R, int nr, i
 // for every real value in [m - r, m + r]; each operation returns a ball that
 // holds every exact result of its operands' values. Midpoints are computed
 // with round-to-nearest, radii with upward rounding: the rounding error of a
-// midpoint is at most 2^-24 |m| (bounded here by 2^-23 |m| + 1e-37 to cover
-// underflow); expf / sinf / cosf are within 2 ulp (CUDA's documented bounds,
-// bounded here by 2^-21 |m|); FP32 division rounds correctly.
+// midpoint is at most 2^-24 |x| <= 2^-24 (1 + 2^-24) |m| (bounded here by
+// 2^-24 (1 + 2^-23) |m| + 1e-37 to cover underflow); expf / sinf / cosf are
+// within 2 ulp (CUDA's documented bounds, bounded here by 2^-21 |m|); FP32
+// division rounds correctly.
 // ---------------------------------------------------------------------------
 struct Ball {
     float m, r;
 };
 
-constexpr float B_U = 1.1920929e-07f;    // 2^-23
+constexpr float B_U = 5.9604652e-08f;    // 2^-24 (1 + 2^-23): round-to-nearest error over |fl(x)|
 constexpr float B_ETA = 1.0e-37f;
 constexpr float B_F = 4.7683716e-07f;    // 2^-21, library function error
 

@@ -1,0 +1,1076 @@
+// gis_engine.cuh -- host side of libgis: a batch engine over a disjoint union
+// of GIS problems, shared by the context / batch entry points (gis_engine.cu)
+// and the serving loop (gis_server.cu).
+//
+// One level of the loop of Sec. 2 / Sec. 3 for every active instance:
+//   numbering   global slots / pairs, descriptor upload, slot gather
+//   build       prop (new cells only; unsplit cells keep their cached image
+//               boxes) -> bin -> FP64 recheck -> count -> scan -> fill ->
+//               (cell graph, reverse edges with the fill)    (Def. 1, Sec. 3.2)
+//   prune       frontier rounds to the greatest fixed point (Sec. 2.3)
+//   subdivide   mark removed -> classify -> scan -> grow -> split (Sec. 3.1)
+// Everything is issued on one CUDA stream; the host waits only for the sizes
+// it must allocate (edge count after the scan, split counts after classify).
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gis.h"
+#include "gis_kernels.cuh"
+
+namespace gis {
+
+inline const char *status_name(gis_status s)
+{
+    switch (s) {
+    case GIS_OK: return "ok";
+    case GIS_EINVAL: return "invalid argument";
+    case GIS_ENOMEM: return "out of memory";
+    case GIS_ECUDA: return "CUDA error";
+    case GIS_ETIMEOUT: return "timeout";
+    case GIS_EUNSUPPORTED: return "unsupported";
+    case GIS_ECANCELLED: return "cancelled";
+    case GIS_EBOUNDS: return "buffer too small";
+    case GIS_ESTATE: return "call out of order";
+    }
+    return "unknown";
+}
+
+struct Error {
+    gis_status st;
+    std::string msg;
+};
+
+#define CK(expr)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (expr);                                                                  \
+        if (e_ != cudaSuccess) throw Error{GIS_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+
+// ------------------------------------------------------------------ memory --
+struct Mem {
+    cudaStream_t st = nullptr;
+    int64_t limit = 0, used = 0;
+    std::map<void *, size_t> sizes;
+
+    void *alloc(size_t bytes)
+    {
+        if (bytes == 0) bytes = 16;
+        if (limit > 0 && used + (int64_t)bytes > limit)
+            throw Error{GIS_ENOMEM, "device memory limit reached (" + std::to_string(used + bytes) + " bytes)"};
+        void *p = nullptr;
+        cudaError_t e = cudaMallocAsync(&p, bytes, st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw Error{GIS_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e)};
+        }
+        sizes[p] = bytes;
+        used += (int64_t)bytes;
+        return p;
+    }
+    void free(void *p)
+    {
+        if (!p) return;
+        auto it = sizes.find(p);
+        if (it != sizes.end()) {
+            used -= (int64_t)it->second;
+            sizes.erase(it);
+        }
+        cudaFreeAsync(p, st);
+    }
+    // grow a scratch buffer (contents not kept)
+    template <class T>
+    void ensure(T *&p, size_t &cap, size_t need)
+    {
+        if (need <= cap && p) return;
+        free(p);
+        size_t c = std::max(need, cap + cap / 2);
+        p = (T *)alloc(c * sizeof(T));
+        cap = c;
+    }
+    // grow keeping the first `keep` elements
+    template <class T>
+    void grow(T *&p, size_t &cap, size_t need, size_t keep)
+    {
+        if (need <= cap && p) return;
+        size_t c = std::max(need, cap + cap / 2);
+        T *q = (T *)alloc(c * sizeof(T));
+        if (p && keep) CK(cudaMemcpyAsync(q, p, keep * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        free(p);
+        p = q;
+        cap = c;
+    }
+    void free_all()
+    {
+        for (auto &kv : sizes) cudaFreeAsync(kv.first, st);
+        sizes.clear();
+        used = 0;
+    }
+};
+
+// ------------------------------------------------------- kernel timing ------
+enum Phase { PH_PROP, PH_BIN, PH_RECHECK, PH_COUNT, PH_SCAN, PH_FILL, PH_TRANSPOSE, PH_PRUNE, PH_CLASSIFY,
+             PH_SPLIT, PH_OTHER, PH_N };
+
+struct Timer {
+    bool on = false;
+    cudaStream_t st = nullptr;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+    double ms[PH_N] = {};
+    cudaEvent_t cur_a = nullptr;
+    int cur_ph = -1;
+
+    cudaEvent_t ev()
+    {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        return e;
+    }
+    void begin(int ph)
+    {
+        if (!on) return;
+        cur_ph = ph;
+        cur_a = ev();
+        CK(cudaEventRecord(cur_a, st));
+    }
+    void end()
+    {
+        if (!on || cur_ph < 0) return;
+        cudaEvent_t b = ev();
+        CK(cudaEventRecord(b, st));
+        pending.push_back({cur_ph, {cur_a, b}});
+        cur_ph = -1;
+    }
+    void resolve()   // after a stream sync
+    {
+        for (auto &p : pending) {
+            float t = 0;
+            cudaEventElapsedTime(&t, p.second.first, p.second.second);
+            ms[p.first] += t;
+            pool.push_back(p.second.first);
+            pool.push_back(p.second.second);
+        }
+        pending.clear();
+    }
+    ~Timer()
+    {
+        for (auto e : pool) cudaEventDestroy(e);
+        for (auto &p : pending) { cudaEventDestroy(p.second.first); cudaEventDestroy(p.second.second); }
+    }
+};
+
+// ------------------------------------------------------------- instance ----
+struct Inst {
+    gis_dynamics dyn{};
+    gis_grid grid{};
+    std::vector<double> u;
+    int nu = 0, rule = 0, precision = 0, levels = 0;
+    double band = 1e-2;
+    int S = 1;
+    // host view of device state
+    int level = 0, Lf = 0;
+    int64_t n_nodes = 0, n_live = 0, n_fresh = 0;
+    int64_t slot_base = 0, pair_base = 0;
+    bool active = true;
+    int tix = -1;               // index in the descriptor table of the current level
+    gis_status status = GIS_OK;
+    int64_t n_kept = 0, cells_built = 0, edges_total = 0, pairs_prop = 0;
+    // device arrays
+    uint8_t *lvl = nullptr, *state = nullptr;
+    int32_t *idx[MAXN] = {};
+    int32_t *child = nullptr, *slot = nullptr;
+    int32_t *live[2] = {};
+    int cur = 0;
+    size_t cap_nodes = 0, cap_live[2] = {0, 0}, cap_pairs = 0;
+    float *box32 = nullptr;
+    double *box64 = nullptr;
+    uint16_t *exact = nullptr;
+    float *u32 = nullptr, *ur32 = nullptr;
+    double *u64 = nullptr;
+    InstDesc desc{};
+};
+
+inline double model_flops_rhs(const Inst &I)
+{
+    const int n = I.dyn.n, m = I.dyn.m;
+    switch (I.dyn.dyn_id) {
+    case GIS_DYN_VDP: return DynVdp::flops_rhs;
+    case GIS_DYN_CSTR_DL: return DynCstrDl::flops_rhs;
+    case GIS_DYN_CARTPOLE: return DynCartpole::flops_rhs;
+    case GIS_DYN_CSTR_PAPER: return DynCstrPaper::flops_rhs;
+    case GIS_DYN_LINMAP: return 2.0 * n * (n + m);
+    }
+    return 0;
+}
+
+// Algorithmic floating-point operations of one (cell, control) pair: per sample
+// 2n for the lattice point, then per RK4 substep 4 right-hand sides plus 13n
+// for the stage states and the weighted update (or one map application).
+inline double pair_flops(const Inst &I)
+{
+    const int n = I.dyn.n;
+    double per = 2.0 * n;
+    if (I.dyn.substeps == 0) per += model_flops_rhs(I);
+    else per += I.dyn.substeps * (4.0 * model_flops_rhs(I) + 13.0 * n);
+    return per * I.S;
+}
+
+inline int ipow(int b, int e)
+{
+    int r = 1;
+    while (e-- > 0) r *= b;
+    return r;
+}
+
+// Validate a problem; fills I (host part).
+inline void setup_inst(Inst &I, const gis_dynamics &dyn, const gis_grid &grid, const gis_controls &ctl, int rule,
+                       int precision, double band, int levels)
+{
+    if (dyn.n < 1 || dyn.n > MAXN || dyn.m < 1 || dyn.m > MAXN) throw Error{GIS_EINVAL, "n and m must be in 1..4"};
+    if (dyn.substeps < 0) throw Error{GIS_EINVAL, "substeps must be >= 0"};
+    if (!(dyn.dt > 0) && dyn.substeps > 0) throw Error{GIS_EINVAL, "dt must be > 0"};
+    switch (dyn.dyn_id) {
+    case GIS_DYN_VDP: case GIS_DYN_CSTR_DL: case GIS_DYN_CSTR_PAPER:
+        if (dyn.n != 2) throw Error{GIS_EINVAL, "this model has n = 2"};
+        if (dyn.substeps == 0) throw Error{GIS_EINVAL, "continuous model needs substeps >= 1"};
+        break;
+    case GIS_DYN_CARTPOLE:
+        if (dyn.n != 4) throw Error{GIS_EINVAL, "cart-pole has n = 4"};
+        if (dyn.substeps == 0) throw Error{GIS_EINVAL, "continuous model needs substeps >= 1"};
+        break;
+    case GIS_DYN_LINMAP: break;
+    default: throw Error{GIS_EINVAL, "unknown dynamics id"};
+    }
+    if (grid.k_samples < 1 || grid.k_samples > MAXK) throw Error{GIS_EINVAL, "k_samples must be in 1..16"};
+    const int S = ipow(grid.k_samples, dyn.n);
+    if (S > MAXS) throw Error{GIS_EINVAL, "k^n must be <= 256"};
+    int64_t R = 1;
+    for (int d = 0; d < dyn.n; d++) {
+        if (grid.root_cells[d] < 1) throw Error{GIS_EINVAL, "root_cells must be >= 1"};
+        if (!(grid.hi[d] > grid.lo[d]) || !std::isfinite(grid.lo[d]) || !std::isfinite(grid.hi[d]))
+            throw Error{GIS_EINVAL, "X must have finite lo < hi"};
+        R *= grid.root_cells[d];
+    }
+    if (R > (int64_t)1 << 30) throw Error{GIS_EINVAL, "too many root cells"};
+    if (levels < 0 || levels > MAXL) throw Error{GIS_EINVAL, "levels must be in 0..15"};
+    if ((int64_t)((1 << dyn.n) - 1) * levels + 1 > STACK)
+        throw Error{GIS_EUNSUPPORTED, "subdivision depth too large for this dimension"};
+    for (int d = 0; d < dyn.n; d++)
+        if (((int64_t)grid.root_cells[d] << levels) > (int64_t)1 << 24)
+            throw Error{GIS_EUNSUPPORTED, "finest grid above 2^24 cells per dimension"};
+    if (ctl.n_controls < 1 || !ctl.u) throw Error{GIS_EINVAL, "need >= 1 control value"};
+    if (ctl.n_controls > 32) throw Error{GIS_EUNSUPPORTED, "at most 32 control values per problem"};
+    if (rule != GIS_RULE_INNER && rule != GIS_RULE_OUTER) throw Error{GIS_EINVAL, "bad rule"};
+    if (precision != GIS_FP64_PLAIN && precision != GIS_FP32_RECHECK) throw Error{GIS_EINVAL, "bad precision"};
+    if (precision == GIS_FP32_RECHECK && !(band >= 0 && band < 0.25)) throw Error{GIS_EINVAL, "band must be in [0, 1/4)"};
+    I.dyn = dyn;
+    I.grid = grid;
+    I.nu = ctl.n_controls;
+    I.u.assign(ctl.u, ctl.u + (size_t)ctl.n_controls * dyn.m);
+    for (double v : I.u)
+        if (!std::isfinite(v)) throw Error{GIS_EINVAL, "control values must be finite"};
+    I.rule = rule;
+    I.precision = precision;
+    I.band = band;
+    I.levels = levels;
+    I.S = S;
+}
+
+// Model constants. FP64: the exact values the defining expressions use
+// (parameter-only subexpressions evaluated once, by the same operations).
+inline void derive_params(const Inst &I, InstDesc &D)
+{
+    const double *p = I.dyn.params;
+    for (int i = 0; i < GIS_NPARAM; i++) { D.p64[i] = p[i]; D.p32[i] = (float)p[i]; D.p64_exact[i] = p[i]; }
+    switch (I.dyn.dyn_id) {
+    case GIS_DYN_CSTR_DL:
+        D.p64_exact[3] = 1.0 / p[3];
+        D.p32[3] = (float)D.p64_exact[3];
+        break;
+    case GIS_DYN_CARTPOLE: {
+        const double mc = p[0], mp = p[1], l = p[2], g = p[3];
+        const double tot = mc + mp, pml = mp * l, ft = 4.0 / 3.0;
+        D.p64[4] = tot; D.p64[5] = pml; D.p64[6] = ft;
+        const double ex[6] = {g, 1.0 / tot, pml, l, mp, ft};
+        for (int i = 0; i < 6; i++) { D.p64_exact[i] = ex[i]; D.p32[i] = (float)ex[i]; }
+        for (int i = 6; i < GIS_NPARAM; i++) { D.p64_exact[i] = 0; D.p32[i] = 0; }
+        break;
+    }
+    case GIS_DYN_CSTR_PAPER: {
+        const double q = p[0], V = p[1], cAf = p[2], Tf = p[3], ER = p[4], k0 = p[5];
+        const double mdH = p[6], UA = p[7], cp = p[8], rho = p[9];
+        const double qV = q / V, a1 = mdH / (rho * cp), a2 = UA / (V * rho * cp);
+        D.p64[0] = qV; D.p64[1] = cAf; D.p64[2] = Tf; D.p64[3] = ER; D.p64[4] = k0; D.p64[5] = a1; D.p64[6] = a2;
+        const double ex[7] = {qV, cAf, Tf, ER, a1, a2, std::log(k0)};
+        for (int i = 0; i < 7; i++) { D.p64_exact[i] = ex[i]; D.p32[i] = (float)ex[i]; }
+        break;
+    }
+    default: break;
+    }
+}
+
+// Radius (rounded up to a float) of the FP32 stand-in f of the exact value v:
+// |v - f| plus 2^-50 |v| for the FP64 computation of v itself.
+inline float radius_of(double v, float f)
+{
+    const double r = std::fabs(v - (double)f) + std::ldexp(std::fabs(v), -50);
+    float rf = (float)r;
+    if ((double)rf < r) rf = std::nextafter(rf, INFINITY);
+    return rf;
+}
+
+inline void fill_desc(Inst &I)
+{
+    InstDesc &D = I.desc;
+    const int n = I.dyn.n;
+    D.dyn = I.dyn.dyn_id;
+    D.n = n;
+    D.m = I.dyn.m;
+    D.nu = I.nu;
+    D.k = I.grid.k_samples;
+    D.S = I.S;
+    D.substeps = I.dyn.substeps;
+    D.rule = I.rule;
+    D.precision = I.precision;
+    D.Lf = I.Lf;
+    D.slot_base = I.slot_base;
+    D.pair_base = I.pair_base;
+    D.n_live = I.n_live;
+    derive_params(I, D);
+    for (int i = 0; i < GIS_NPARAM; i++) D.pr32[i] = radius_of(D.p64_exact[i], D.p32[i]);
+    if (I.dyn.substeps > 0) {
+        const double h = I.dyn.dt / (double)I.dyn.substeps;
+        D.h64 = h;
+        D.hh64 = h * 0.5;
+        D.h6_64 = h / 6.0;
+        D.h32 = (float)h;
+        D.hh32 = (float)(h * 0.5);
+        D.h6_32 = (float)(h / 6.0);
+        D.hr32 = radius_of(h, D.h32);
+        D.hhr32 = radius_of(h * 0.5, D.hh32);
+        D.h6r32 = radius_of(h / 6.0, D.h6_32);
+    }
+    for (int d = 0; d < MAXN; d++) {
+        D.lo[d] = d < n ? I.grid.lo[d] : 0;
+        D.hi[d] = d < n ? I.grid.hi[d] : 1;
+        D.lo32[d] = (float)D.lo[d];
+        D.lor32[d] = radius_of(D.lo[d], D.lo32[d]);
+        D.n0[d] = d < n ? I.grid.root_cells[d] : 1;
+        for (int L = 0; L <= MAXL; L++) {
+            D.w64[L][d] = (D.hi[d] - D.lo[d]) / (double)((int64_t)D.n0[d] << L);
+            D.w32[L][d] = (float)D.w64[L][d];
+            D.wr32[L][d] = radius_of(D.w64[L][d], D.w32[L][d]);
+        }
+        const double wf = D.w64[I.Lf][d];
+        D.invwf32[d] = (float)(1.0 / wf);
+        // FP32 t = (y - lo32) * invw for |y| within the box of X widened by its
+        // size: rounding of lo, of the difference, of the product and of 1/w,
+        // bounded in Lf cell widths (x2 margin), plus the optional band.
+        const double Nf = (double)((int64_t)D.n0[d] << I.Lf);
+        const double lo_err = std::fabs((double)D.lo32[d] - D.lo[d]) / wf;
+        const double scale = 2.0 * std::max(std::fabs(D.lo[d]), std::fabs(D.hi[d])) / wf + Nf + 2.0;
+        const double tb = 2.0 * (lo_err + scale * 4.0 * 5.96e-8);
+        D.tmargin[d] = (float)(I.band + tb);
+    }
+    const int k = I.grid.k_samples;
+    for (int j = 0; j < MAXK; j++) {
+        const double f = (k == 1) ? 0.5 : (j < k ? (double)j / (double)(k - 1) : 0.0);
+        D.frac64[j] = f;
+        D.frac32[j] = (float)f;
+        D.fracr32[j] = radius_of(f, D.frac32[j]);
+    }
+    D.u32 = I.u32;
+    D.ur32 = I.ur32;
+    D.u64 = I.u64;
+    D.lvl = I.lvl;
+    D.state = I.state;
+    for (int d = 0; d < MAXN; d++) D.idx[d] = I.idx[d];
+    D.child = I.child;
+    D.slot = I.slot;
+    D.live = I.live[I.cur];
+    D.box32 = I.box32;
+    D.box64 = I.box64;
+    D.exact = I.exact;
+}
+
+// ---------------------------------------------------------------- engine ---
+struct RangeSpec {
+    int inst;
+    int64_t first, count;
+};
+
+struct Engine {
+    cudaStream_t st = nullptr;
+    gis_options opt{};
+    Mem mem;
+    Timer timer;
+    std::vector<Inst *> inst;
+    int dev = 0, sms = 0;
+
+    // descriptor table and work ranges
+    InstDesc *d_desc = nullptr;
+    size_t cap_desc = 0;
+    Range *d_rng_buf = nullptr;
+    size_t cap_rng_buf = 0, rng_used = 0;
+    std::vector<Range> h_rng;
+
+    // per-level arrays over the union
+    int64_t NL = 0, P = 0, E = 0;
+    int32_t *pair_slot = nullptr; size_t c_pair_slot = 0;
+    int64_t Ecell = 0;
+    int32_t *cps = nullptr; size_t c_cps = 0;
+    uint8_t *cinfo = nullptr; size_t c_cinfo = 0;
+    int32_t *pcnt = nullptr; size_t c_pcnt = 0;
+    int32_t *ccnt = nullptr; size_t c_ccnt = 0;
+    int64_t *coff = nullptr; size_t c_coff = 0;
+    int32_t *cent = nullptr; size_t c_cent = 0;
+    uint32_t *cmask = nullptr; size_t c_cmask = 0;
+    uint32_t *rmask = nullptr; size_t c_rmask = 0;
+    uint32_t *vmask = nullptr; size_t c_vmask = 0;
+    int32_t *rng = nullptr; size_t c_rng = 0;
+    uint8_t *pflag = nullptr; size_t c_pflag = 0;
+    int32_t *cnt = nullptr; size_t c_cnt = 0;
+    int64_t *off = nullptr; size_t c_off = 0;
+    int32_t *tgt = nullptr; size_t c_tgt = 0;
+    int2 *rq = nullptr; size_t c_rq = 0;
+    long long *rc_mnk = nullptr, *rc_mxk = nullptr; size_t c_rc_mnk = 0, c_rc_mxk = 0;
+    int32_t *rc_bad = nullptr; size_t c_rc_bad = 0;
+    int2 *rc_cand = nullptr; size_t c_rc_cand = 0;
+    int32_t *rcnt = nullptr; size_t c_rcnt = 0;
+    int64_t *roff = nullptr; size_t c_roff = 0;
+    int64_t *rcur = nullptr; size_t c_rcur = 0;
+    int32_t *rsrc = nullptr; size_t c_rsrc = 0;
+    int32_t *pstate = nullptr; size_t c_pstate = 0;
+    int32_t *ncnt = nullptr; size_t c_ncnt = 0;
+    uint8_t *alive = nullptr; size_t c_alive = 0;
+    int32_t *front[2] = {}; size_t c_front[2] = {0, 0};
+    uint8_t *bnd = nullptr; size_t c_bnd = 0;
+    int64_t *packed = nullptr; size_t c_packed = 0;
+    int64_t *pscan = nullptr; size_t c_pscan = 0;
+    uint8_t *scratch = nullptr; size_t c_scratch = 0;
+    int64_t *inst_i64 = nullptr; size_t c_inst_i64 = 0;
+    int32_t *inst_i32 = nullptr; size_t c_inst_i32 = 0;
+    SplitInst *d_split = nullptr; size_t c_split = 0;
+    // small control block: [0..2] sizes, [3] bar, [4] err, [5] rounds, [6] rq count, [7] edge err, [8..9] scanned
+    int32_t *ctl = nullptr;
+
+    bool have_graph = false, have_prune = false, have_bnd = false;
+    int last_rounds = 0;
+    int64_t last_recheck = 0, last_new_pairs = 0, last_split = 0, last_kept = 0;
+    gis_stats cum{};
+    std::string last_error;
+    std::vector<int> step;     // instances taking part in the current level
+
+    void init(const gis_options *o, void *stream)
+    {
+        if (o) opt = *o;
+        else gis_default_options(&opt);
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+            cudaGetLastError();
+            throw Error{GIS_ECUDA, "no CUDA device"};
+        }
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        st = (cudaStream_t)stream;
+        mem.st = st;
+        mem.limit = opt.max_device_bytes;
+        timer.on = opt.timing != 0;
+        timer.st = st;
+        ctl = (int32_t *)mem.alloc(64 * sizeof(int32_t));
+        CK(cudaMemsetAsync(ctl, 0, 64 * sizeof(int32_t), st));
+    }
+
+    ~Engine()
+    {
+        for (Inst *I : inst) delete I;
+        mem.free_all();
+        if (st) cudaStreamSynchronize(st);
+        else cudaDeviceSynchronize();
+    }
+
+    void sync()
+    {
+        CK(cudaStreamSynchronize(st));
+        timer.resolve();
+    }
+
+    // ---- instances --------------------------------------------------------
+    int add(const gis_dynamics &dyn, const gis_grid &grid, const gis_controls &ctl_, int rule, int precision,
+            double band, int levels)
+    {
+        Inst *I = new Inst();
+        try {
+            setup_inst(*I, dyn, grid, ctl_, rule, precision, band, levels);
+            int64_t R = 1;
+            for (int d = 0; d < dyn.n; d++) R *= grid.root_cells[d];
+            I->n_nodes = R;
+            I->n_live = R;
+            I->n_fresh = R;
+            alloc_nodes(*I, R);
+            mem.grow(I->live[0], I->cap_live[0], R, 0);
+            mem.grow(I->box32, I->cap_pairs, (size_t)R * I->nu * 4 * dyn.n, 0);
+            size_t c64 = 0, cex = 0;
+            mem.grow(I->box64, c64, (size_t)R * I->nu * 2 * dyn.n, 0);
+            mem.grow(I->exact, cex, (size_t)R * I->nu, 0);
+            I->cap_pairs = (size_t)R * I->nu;
+            std::vector<float> u32(I->u.begin(), I->u.end()), ur32(I->u.size());
+            for (size_t j = 0; j < I->u.size(); j++) ur32[j] = radius_of(I->u[j], u32[j]);
+            I->u32 = (float *)mem.alloc(u32.size() * sizeof(float));
+            I->ur32 = (float *)mem.alloc(ur32.size() * sizeof(float));
+            I->u64 = (double *)mem.alloc(I->u.size() * sizeof(double));
+            CK(cudaMemcpyAsync(I->u32, u32.data(), u32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(I->ur32, ur32.data(), ur32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(I->u64, I->u.data(), I->u.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+            CK(launch_init_roots(I->lvl, I->state, I->idx, I->child, I->live[0], dyn.n, grid.root_cells, R, st));
+        } catch (...) {
+            delete I;
+            throw;
+        }
+        inst.push_back(I);
+        return (int)inst.size() - 1;
+    }
+
+    void alloc_nodes(Inst &I, size_t need)
+    {
+        const size_t keep = (size_t)I.n_nodes;
+        size_t c = I.cap_nodes;
+        size_t c1 = c, c2 = c, c3 = c, c4 = c;
+        const bool first = I.lvl == nullptr;
+        const size_t k = first ? 0 : std::min(keep, c);
+        mem.grow(I.lvl, c1, need, k);
+        mem.grow(I.state, c2, need, k);
+        mem.grow(I.child, c3, need, k);
+        mem.grow(I.slot, c4, need, 0);
+        for (int d = 0; d < I.dyn.n; d++) {
+            size_t cd = c;
+            mem.grow(I.idx[d], cd, need, k);
+        }
+        I.cap_nodes = c1;
+    }
+
+    void grow_inst(Inst &I, int64_t nodes_needed, int64_t live_needed)
+    {
+        if ((size_t)nodes_needed > I.cap_nodes) {
+            const size_t target = std::max((size_t)nodes_needed, I.cap_nodes + I.cap_nodes / 2);
+            alloc_nodes(I, target);
+            const size_t n2 = (size_t)2 * I.dyn.n;
+            const size_t keep = (size_t)I.n_nodes * I.nu;
+            size_t c32 = I.cap_pairs * 2 * n2, c64 = I.cap_pairs * n2, cex = I.cap_pairs;
+            mem.grow(I.box32, c32, I.cap_nodes * I.nu * 2 * n2, keep * 2 * n2);
+            mem.grow(I.box64, c64, I.cap_nodes * I.nu * n2, keep * n2);
+            mem.grow(I.exact, cex, I.cap_nodes * I.nu, keep);
+            I.cap_pairs = I.cap_nodes * I.nu;
+        }
+        const int nx = 1 - I.cur;
+        mem.grow(I.live[nx], I.cap_live[nx], (size_t)std::max<int64_t>(live_needed, 1), 0);
+    }
+
+    // free the device state of a finished instance (stream-ordered)
+    void release(int i)
+    {
+        Inst &I = *inst[i];
+        mem.free(I.lvl); mem.free(I.state); mem.free(I.child); mem.free(I.slot);
+        for (int d = 0; d < MAXN; d++) { mem.free(I.idx[d]); I.idx[d] = nullptr; }
+        mem.free(I.live[0]); mem.free(I.live[1]);
+        mem.free(I.box32); mem.free(I.box64); mem.free(I.exact);
+        mem.free(I.u32); mem.free(I.ur32); mem.free(I.u64);
+        I.lvl = I.state = nullptr;
+        I.child = I.slot = I.live[0] = I.live[1] = nullptr;
+        I.box32 = nullptr; I.box64 = nullptr; I.exact = nullptr;
+        I.u32 = I.ur32 = nullptr; I.u64 = nullptr;
+        I.cap_nodes = I.cap_live[0] = I.cap_live[1] = I.cap_pairs = 0;
+        I.active = false;
+    }
+
+    // cell edges built this level per instance (ids must be numbered this level)
+    std::vector<int64_t> cell_edges_of(const std::vector<int> &ids)
+    {
+        std::vector<int64_t> be(2 * ids.size()), h(ids.size());
+        if (ids.empty()) return h;
+        for (size_t j = 0; j < ids.size(); j++) {
+            be[2 * j] = inst[ids[j]]->slot_base;
+            be[2 * j + 1] = inst[ids[j]]->slot_base + inst[ids[j]]->n_live;
+        }
+        mem.ensure(inst_i64, c_inst_i64, 3 * ids.size() + 2);
+        CK(cudaMemcpyAsync(inst_i64, be.data(), be.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        CK(launch_inst_totals(coff, inst_i64, (int)ids.size(), inst_i64 + 2 * ids.size(), st));
+        CK(cudaMemcpyAsync(h.data(), inst_i64 + 2 * ids.size(), h.size() * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                           st));
+        sync();
+        return h;
+    }
+
+    // kept cells of pruned instances (ids numbered this level), at most `cap[j]` each
+    std::vector<std::vector<gis_cell>> export_kept(const std::vector<int> &ids, const std::vector<int64_t> &cap)
+    {
+        std::vector<std::vector<gis_cell>> out(ids.size());
+        if (ids.empty()) return out;
+        const size_t NLs = (size_t)std::max<int64_t>(NL, 1);
+        int64_t *kscan = (int64_t *)mem.alloc((NLs + 1) * sizeof(int64_t));
+        mem.ensure(scratch, c_scratch, scan_scratch_bytes(NL + 1));
+        CK(launch_scan_u8(alive, kscan, NL, scratch, st));
+        std::vector<gis_cell *> bufs(ids.size(), nullptr);
+        for (size_t j = 0; j < ids.size(); j++) {
+            Inst &I = *inst[ids[j]];
+            const int64_t m = std::min<int64_t>(cap[j], I.n_kept);
+            if (m <= 0) continue;
+            gis_cell *d = (gis_cell *)mem.alloc(I.n_kept * sizeof(gis_cell));
+            bufs[j] = d;
+            WorkList w = make_work({{I.tix, I.slot_base, I.n_live}}, 256);
+            CK(launch_export_cells(d_desc, w, alive, nullptr, d, 1, kscan, st));
+            out[j].resize(m);
+            CK(cudaMemcpyAsync(out[j].data(), d, m * sizeof(gis_cell), cudaMemcpyDeviceToHost, st));
+        }
+        sync();
+        for (gis_cell *d : bufs) mem.free(d);
+        mem.free(kscan);
+        return out;
+    }
+
+    // ---- work ranges ------------------------------------------------------
+    WorkList make_work(const std::vector<RangeSpec> &spec, int per_block)
+    {
+        WorkList w;
+        std::vector<Range> r;
+        int64_t b = 0;
+        for (const RangeSpec &s : spec) {
+            if (s.count <= 0) continue;
+            Range x{};
+            x.inst = s.inst;
+            x.first = s.first;
+            x.count = s.count;
+            x.block_start = b;
+            b += (s.count + per_block - 1) / per_block;
+            r.push_back(x);
+        }
+        if (r.empty()) return w;
+        if (rng_used + r.size() > cap_rng_buf) {
+            // a new buffer; the old one stays valid for kernels already queued
+            size_t c = std::max<size_t>(4096, 2 * (rng_used + r.size()));
+            if (d_rng_buf) mem.free(d_rng_buf);
+            d_rng_buf = (Range *)mem.alloc(c * sizeof(Range));
+            cap_rng_buf = c;
+            rng_used = 0;
+        }
+        Range *dst = d_rng_buf + rng_used;
+        rng_used += r.size();
+        CK(cudaMemcpyAsync(dst, r.data(), r.size() * sizeof(Range), cudaMemcpyHostToDevice, st));
+        w.d_ranges = dst;
+        w.n_ranges = (int)r.size();
+        w.n_blocks = b;
+        return w;
+    }
+
+    // descriptors of the instances of the current level, in table order
+    void upload_desc()
+    {
+        mem.ensure(d_desc, cap_desc, std::max<size_t>(step.size(), 1));
+        std::vector<InstDesc> h(step.size());
+        for (size_t j = 0; j < step.size(); j++) {
+            fill_desc(*inst[step[j]]);
+            h[j] = inst[step[j]]->desc;
+        }
+        if (!h.empty())
+            CK(cudaMemcpyAsync(d_desc, h.data(), h.size() * sizeof(InstDesc), cudaMemcpyHostToDevice, st));
+    }
+
+    std::vector<RangeSpec> slot_ranges(const std::vector<int> &ids) const
+    {
+        std::vector<RangeSpec> r;
+        for (int i : ids) r.push_back({inst[i]->tix, inst[i]->slot_base, inst[i]->n_live});
+        return r;
+    }
+    std::vector<RangeSpec> pair_ranges(const std::vector<int> &ids) const
+    {
+        std::vector<RangeSpec> r;
+        for (int i : ids) r.push_back({inst[i]->tix, inst[i]->pair_base, inst[i]->n_live * inst[i]->nu});
+        return r;
+    }
+    std::vector<int> with_n(const std::vector<int> &ids, int n) const
+    {
+        std::vector<int> r;
+        for (int i : ids)
+            if (inst[i]->dyn.n == n) r.push_back(i);
+        return r;
+    }
+
+    int lanes_for(const Inst &I)
+    {
+        if (opt.lanes_per_pair > 0) return opt.lanes_per_pair;
+        int g = 4;
+        while (g > 1 && g > I.S) g >>= 1;
+        return g;
+    }
+
+    // ---- one level --------------------------------------------------------
+    void number(const std::vector<int> &ids)
+    {
+        step = ids;
+        rng_used = 0;
+        NL = 0;
+        P = 0;
+        for (size_t j = 0; j < ids.size(); j++) inst[ids[j]]->tix = (int)j;
+        for (int i : ids) {
+            Inst &I = *inst[i];
+            I.slot_base = NL;
+            I.pair_base = P;
+            NL += I.n_live;
+            P += I.n_live * I.nu;
+        }
+        if (ids.size() > 65535) throw Error{GIS_EUNSUPPORTED, "at most 65535 problems in one level"};
+        if (NL >= ((int64_t)1 << 31) - 1 || P >= ((int64_t)1 << 31) - 1)
+            throw Error{GIS_EUNSUPPORTED, "more than 2^31 cells or pairs in one level"};
+        upload_desc();
+    }
+
+    void build_graph(const std::vector<int> &ids)
+    {
+        LaunchScope ls_(cum);
+        number(ids);
+        have_graph = have_prune = have_bnd = false;
+        const size_t Ps = (size_t)std::max<int64_t>(P, 1), NLs = (size_t)std::max<int64_t>(NL, 1);
+        mem.ensure(rng, c_rng, Ps * 2 * MAXN);
+        mem.ensure(pflag, c_pflag, Ps);
+        mem.ensure(rq, c_rq, Ps);
+        mem.ensure(scratch, c_scratch, scan_scratch_bytes(std::max<int64_t>(P, NL) + 1));
+
+        timer.begin(PH_OTHER);
+        WorkList ws = make_work(slot_ranges(ids), 256);
+        mem.ensure(cps, c_cps, NLs);
+        mem.ensure(cinfo, c_cinfo, NLs);
+        CK(launch_cgather(d_desc, ws, cps, cinfo, st));
+        timer.end();
+
+        // propagation of new cells, grouped by (dynamics, n, precision, lanes)
+        timer.begin(PH_PROP);
+        last_new_pairs = 0;
+        std::map<std::tuple<int, int, int, int>, std::vector<RangeSpec>> groups;
+        for (int i : ids) {
+            Inst &I = *inst[i];
+            if (I.n_fresh == 0) continue;
+            const int64_t first = I.pair_base + (I.n_live - I.n_fresh) * I.nu;
+            const int lanes = I.precision == GIS_FP64_PLAIN ? 1 : lanes_for(I);
+            groups[{I.dyn.dyn_id, I.dyn.n, I.precision, lanes}].push_back({I.tix, first, I.n_fresh * I.nu});
+            last_new_pairs += I.n_fresh * I.nu;
+            I.pairs_prop += I.n_fresh * I.nu;
+            cum.prop_flops += pair_flops(I) * (double)(I.n_fresh * I.nu);
+            cum.cum_prop_launches += 0;
+        }
+        for (auto &g : groups) {
+            const int dyn = std::get<0>(g.first), n = std::get<1>(g.first), prec = std::get<2>(g.first);
+            const int lanes = std::get<3>(g.first);
+            if (prec == GIS_FP64_PLAIN) {
+                CK(launch_prop64(dyn, n, d_desc, make_work(g.second, 256), st));
+            } else {
+                CK(launch_prop32(dyn, n, lanes, d_desc, make_work(g.second, prop_pairs_per_block(lanes)), st));
+            }
+            cum.cum_prop_launches++;
+        }
+        timer.end();
+        for (int i : ids) inst[i]->n_fresh = 0;
+
+        // binning and recheck
+        timer.begin(PH_BIN);
+        CK(cudaMemsetAsync(ctl + 6, 0, 2 * sizeof(int32_t), st));
+        for (int n = 1; n <= MAXN; n++) {
+            auto sub = with_n(ids, n);
+            if (sub.empty()) continue;
+            CK(launch_bin(n, d_desc, make_work(pair_ranges(sub), 256), rng, pflag, rq, ctl + 6, (int64_t)Ps, st));
+        }
+        timer.end();
+        // the FP64 recheck needs the number of flagged pairs for its buffers
+        int32_t hq0 = 0;
+        CK(cudaMemcpyAsync(&hq0, ctl + 6, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        sync();
+        last_recheck = hq0;
+        if (hq0 > 0) {
+            timer.begin(PH_RECHECK);
+            int Smax = 1;
+            std::map<std::pair<int, int>, int> kinds;
+            std::map<int, int> dims;
+            for (int i : ids)
+                if (inst[i]->precision == GIS_FP32_RECHECK) {
+                    kinds[{inst[i]->dyn.dyn_id, inst[i]->dyn.n}] = 1;
+                    dims[inst[i]->dyn.n] = 1;
+                    Smax = std::max(Smax, inst[i]->S);
+                }
+            mem.ensure(rc_mnk, c_rc_mnk, (size_t)hq0 * MAXN);
+            mem.ensure(rc_mxk, c_rc_mxk, (size_t)hq0 * MAXN);
+            mem.ensure(rc_bad, c_rc_bad, (size_t)hq0);
+            mem.ensure(rc_cand, c_rc_cand, (size_t)hq0 * Smax);
+            CK(cudaMemsetAsync(ctl + 10, 0, sizeof(int32_t), st));
+            RecheckArgs ra{d_desc, rq, ctl + 6, (int64_t)Ps, rc_mnk, rc_mxk, rc_bad, rc_cand, ctl + 10,
+                           (int64_t)hq0 * Smax, rng, pflag};
+            for (auto &k : kinds) CK(launch_recheck(0, k.first.first, k.first.second, ra, st));
+            for (auto &k : kinds) CK(launch_recheck(1, k.first.first, k.first.second, ra, st));
+            for (auto &d : dims) CK(launch_recheck(2, 0, d.first, ra, st));
+            timer.end();
+        }
+
+        // count the cell graph, scan edges and in-degrees, fill edges and
+        // reverse edges (the transpose is fused into the fill)
+        mem.ensure(pcnt, c_pcnt, Ps);
+        mem.ensure(ccnt, c_ccnt, NLs);
+        mem.ensure(coff, c_coff, NLs + 1);
+        mem.ensure(rcnt, c_rcnt, NLs);
+        mem.ensure(roff, c_roff, NLs + 1);
+        mem.ensure(rcur, c_rcur, NLs);
+        CK(cudaMemsetAsync(rcnt, 0, NLs * sizeof(int32_t), st));
+        CK(cudaMemsetAsync(ctl + 12, 0, 2 * sizeof(int32_t), st));
+        CellGraph g{rng, pflag, pcnt, ccnt, rcnt, coff, nullptr, nullptr, (unsigned long long *)rcur, nullptr,
+                    nullptr, (unsigned long long *)(ctl + 12), ctl + 7};
+        timer.begin(PH_COUNT);
+        for (int n = 1; n <= MAXN; n++) {
+            auto sub = with_n(ids, n);
+            if (sub.empty()) continue;
+            CK(launch_cedges(false, n, d_desc, make_work(slot_ranges(sub), cedges_cells_per_block()), g, st));
+        }
+        timer.end();
+        timer.begin(PH_SCAN);
+        CK(launch_scan_i32(ccnt, coff, NL, scratch, st));
+        CK(launch_scan_i32(rcnt, roff, NL, scratch, st));
+        timer.end();
+        int64_t hEc = 0;
+        int32_t hq[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        CK(cudaMemcpyAsync(&hEc, coff + NL, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hq, ctl + 6, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        sync();
+        if (last_recheck > 0) cum.cum_recheck_samples += hq[4];
+        if (hq[1] != 0) throw Error{GIS_EBOUNDS, "subdivision tree descent overflow"};
+        unsigned long long hpe = 0;
+        std::memcpy(&hpe, hq + 6, sizeof(hpe));
+        E = (int64_t)hpe;
+        Ecell = hEc;
+        mem.ensure(cent, c_cent, (size_t)std::max<int64_t>(Ecell, 1));
+        mem.ensure(cmask, c_cmask, (size_t)std::max<int64_t>(Ecell, 1));
+        mem.ensure(rsrc, c_rsrc, (size_t)std::max<int64_t>(Ecell, 1));
+        mem.ensure(rmask, c_rmask, (size_t)std::max<int64_t>(Ecell, 1));
+        g.cent = cent;
+        g.cmask = cmask;
+        g.rsrc = rsrc;
+        g.rmask = rmask;
+        timer.begin(PH_FILL);
+        CK(cudaMemcpyAsync(rcur, roff, NLs * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+        for (int n = 1; n <= MAXN; n++) {
+            auto sub = with_n(ids, n);
+            if (sub.empty()) continue;
+            CK(launch_cedges(true, n, d_desc, make_work(slot_ranges(sub), cedges_cells_per_block()), g, st));
+        }
+        timer.end();
+
+        for (int i : ids) inst[i]->cells_built += inst[i]->n_live;
+        cum.cum_cells_built += NL;
+        cum.cum_pairs_propagated += last_new_pairs;
+        cum.cum_edges += E;
+        cum.cum_cell_edges += Ecell;
+        cum.cum_recheck += last_recheck;
+        // algorithmic bytes. count: per pair the decisions (8n), the flag (read and
+        // write) and the target count; per cell the edge count; per cell edge the
+        // in-degree update (8). fill: per pair decisions and flag, per cell the
+        // offset; per cell edge the edge (8), the reverse cursor update (16) and
+        // the reverse edge (8).
+        double cb = 0, fb = 0;
+        for (int i : ids) {
+            const Inst &I = *inst[i];
+            const double pairs = (double)I.n_live * I.nu;
+            cb += pairs * (8.0 * I.dyn.n + 1 + 4 + 1) + 4.0 * (double)I.n_live;
+            fb += pairs * (8.0 * I.dyn.n + 1) + 8.0 * (double)I.n_live;
+        }
+        cb += 8.0 * (double)Ecell;
+        fb += 32.0 * (double)Ecell;
+        cum.count_bytes += cb;
+        cum.fill_bytes += fb;
+        cum.graph_bytes += cb + fb;
+        have_graph = true;
+    }
+
+    void prune()
+    {
+        LaunchScope ls_(cum);
+        if (!have_graph) throw Error{GIS_ESTATE, "prune needs a graph"};
+        const size_t NLs = (size_t)std::max<int64_t>(NL, 1), Ps = (size_t)std::max<int64_t>(P, 1);
+        mem.ensure(pstate, c_pstate, Ps);
+        mem.ensure(vmask, c_vmask, NLs);
+        mem.ensure(alive, c_alive, NLs);
+        mem.ensure(front[0], c_front[0], NLs);
+        mem.ensure(front[1], c_front[1], NLs);
+        timer.begin(PH_PRUNE);
+        CK(cudaMemsetAsync(ctl, 0, 6 * sizeof(int32_t), st));
+        CK(cudaMemsetAsync(ctl + 8, 0, 2 * sizeof(int32_t), st));
+        WorkList ws = make_work(slot_ranges(step), 256);
+        CK(launch_cprune_init(d_desc, ws, pflag, pcnt, pstate, vmask, alive, front[0], (uint32_t *)ctl, st));
+        CPruneArgs a{};
+        a.roff = roff;
+        a.rsrc = rsrc;
+        a.rmask = rmask;
+        a.cps = cps;
+        a.cinfo = cinfo;
+        a.pc = pstate;
+        a.vmask = vmask;
+        a.alive = alive;
+        a.frontier[0] = front[0];
+        a.frontier[1] = front[1];
+        a.sizes = (uint32_t *)ctl;
+        a.bar = (uint32_t *)(ctl + 3);
+        a.err = ctl + 4;
+        a.rounds = ctl + 5;
+        a.scanned = (unsigned long long *)(ctl + 8);
+        a.round_limit = opt.round_limit > 0 ? opt.round_limit : ((int64_t)1 << 30);
+        a.spin_limit = (int64_t)1 << 25;
+        if (NL > 0) CK(launch_cprune(a, NL, st));
+        timer.end();
+        mem.ensure(inst_i64, c_inst_i64, step.size() + 1);
+        CK(cudaMemsetAsync(inst_i64, 0, step.size() * sizeof(int64_t), st));
+        CK(launch_count_kept(ws, alive, inst_i64, st));
+        int32_t hc[10];
+        std::vector<int64_t> kept(step.size());
+        CK(cudaMemcpyAsync(hc, ctl, 10 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(kept.data(), inst_i64, step.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        sync();
+        if (hc[4] != 0) throw Error{(gis_status)hc[4], "prune: round or wait limit reached"};
+        last_rounds = hc[5];
+        unsigned long long scanned = 0;
+        std::memcpy(&scanned, hc + 8, sizeof(scanned));
+        last_kept = 0;
+        for (int i : step) {
+            inst[i]->n_kept = kept[inst[i]->tix];
+            last_kept += kept[inst[i]->tix];
+        }
+        const double dead = (double)(NL - last_kept);
+        // init: per pair flag, target count and counter (9), per cell mask and flag (5);
+        // per removed cell its reverse offsets and frontier slots (24); per reverse
+        // edge walked its source, mask, info byte and the mask update (17)
+        cum.prune_bytes += (double)P * 9 + (double)NL * 5 + 24.0 * dead + 17.0 * (double)scanned;
+        have_prune = true;
+    }
+
+    // classify + split for instances in `cont` (a subset of the current step)
+    void subdivide(const std::vector<int> &cont)
+    {
+        LaunchScope ls_(cum);
+        if (!have_prune) throw Error{GIS_ESTATE, "subdivide needs a pruned graph"};
+        const size_t NLs = (size_t)std::max<int64_t>(NL, 1);
+        mem.ensure(bnd, c_bnd, NLs);
+        mem.ensure(packed, c_packed, NLs);
+        mem.ensure(pscan, c_pscan, NLs + 1);
+        mem.ensure(scratch, c_scratch, scan_scratch_bytes(NL + 1));
+        mem.ensure(inst_i32, c_inst_i32, step.size() + 1);
+        mem.ensure(inst_i64, c_inst_i64, 2 * step.size() + 2);
+        timer.begin(PH_CLASSIFY);
+        WorkList wall = make_work(slot_ranges(step), 256);
+        CK(launch_mark_dead(d_desc, wall, alive, st));
+        CK(cudaMemsetAsync(packed, 0, NLs * sizeof(int64_t), st));
+        CK(cudaMemsetAsync(bnd, 0, NLs, st));
+        CK(cudaMemsetAsync(inst_i32, 0, step.size() * sizeof(int32_t), st));
+        for (int n = 1; n <= MAXN; n++) {
+            auto sub = with_n(cont, n);
+            if (sub.empty()) continue;
+            CK(launch_classify(n, d_desc, make_work(slot_ranges(sub), 256), alive, bnd, packed, inst_i32, st));
+        }
+        CK(launch_scan_i64(packed, pscan, NL, scratch, st));
+        std::vector<int64_t> be(2 * cont.size());
+        for (size_t j = 0; j < cont.size(); j++) {
+            be[2 * j] = inst[cont[j]]->slot_base;
+            be[2 * j + 1] = inst[cont[j]]->slot_base + inst[cont[j]]->n_live;
+        }
+        int64_t *d_be = inst_i64;
+        int64_t *d_tot = inst_i64 + 2 * cont.size();
+        mem.ensure(inst_i64, c_inst_i64, 3 * cont.size() + 2);
+        d_be = inst_i64;
+        d_tot = inst_i64 + 2 * cont.size();
+        CK(cudaMemcpyAsync(d_be, be.data(), be.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        CK(launch_inst_totals(pscan, d_be, (int)cont.size(), d_tot, st));
+        timer.end();
+        std::vector<int64_t> tot(cont.size());
+        std::vector<int32_t> maxl(step.size());
+        if (!cont.empty())
+            CK(cudaMemcpyAsync(tot.data(), d_tot, cont.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(maxl.data(), inst_i32, step.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        sync();
+        // grow, then split
+        std::vector<SplitInst> si(step.size());
+        last_split = 0;
+        for (size_t j = 0; j < cont.size(); j++) {
+            Inst &I = *inst[cont[j]];
+            const int64_t nb = tot[j] & 0xffffffffll, nkeep = tot[j] >> 32;
+            const int64_t kids = nb << I.dyn.n;
+            if (I.n_nodes + kids >= ((int64_t)1 << 31) - 1) throw Error{GIS_EUNSUPPORTED, "more than 2^31 nodes"};
+            grow_inst(I, I.n_nodes + kids, nkeep + kids);
+            si[I.tix].new_live = I.live[1 - I.cur];
+            si[I.tix].n_nodes = (int32_t)I.n_nodes;
+            si[I.tix].n_keep = (int32_t)nkeep;
+            I.desc.live = I.live[I.cur];
+            last_split += nb;
+        }
+        upload_desc();
+        mem.ensure(d_split, c_split, step.size());
+        CK(cudaMemcpyAsync(d_split, si.data(), si.size() * sizeof(SplitInst), cudaMemcpyHostToDevice, st));
+        timer.begin(PH_SPLIT);
+        for (int n = 1; n <= MAXN; n++) {
+            auto sub = with_n(cont, n);
+            if (sub.empty()) continue;
+            CK(launch_split(n, d_desc, make_work(slot_ranges(sub), 256), alive, bnd, pscan, d_split, st));
+        }
+        timer.end();
+        for (size_t j = 0; j < cont.size(); j++) {
+            Inst &I = *inst[cont[j]];
+            const int64_t nb = tot[j] & 0xffffffffll, nkeep = tot[j] >> 32;
+            const int64_t kids = nb << I.dyn.n;
+            I.n_nodes += kids;
+            I.n_live = nkeep + kids;
+            I.n_fresh = kids;
+            I.cur = 1 - I.cur;
+            I.level += 1;
+            I.Lf = std::max(I.Lf, (int)maxl[I.tix]);
+        }
+        have_graph = have_prune = false;
+        have_bnd = true;
+    }
+
+    struct LaunchScope {          // adds the launches of one phase to the stats
+        gis_stats &c;
+        long long l0;
+        explicit LaunchScope(gis_stats &c_) : c(c_), l0(launches_total()) {}
+        ~LaunchScope() { c.cum_launches += launches_total() - l0; }
+    };
+
+    void fill_stats(gis_stats *s) const
+    {
+        *s = cum;
+        double *ms = &s->ms_prop;
+        for (int i = 0; i < PH_N; i++) ms[i] = timer.ms[i];
+        if (!inst.empty()) {
+            const Inst &I = *inst[0];
+            s->finest_level = I.Lf;
+            s->level = I.level;
+            s->n_nodes = I.n_nodes;
+            s->n_live = I.n_live;
+            s->n_pairs = I.n_live * I.nu;
+        }
+        s->n_edges = have_graph ? E : 0;
+        s->n_cell_edges = have_graph ? Ecell : 0;
+        s->n_kept = last_kept;
+        s->n_split = last_split;
+        s->n_new_pairs = last_new_pairs;
+        s->n_recheck = last_recheck;
+        s->prune_rounds = last_rounds;
+        s->lanes_per_pair = inst.empty() ? 0 : const_cast<Engine *>(this)->lanes_for(*inst[0]);
+    }
+};
+
+}  // namespace gis
+

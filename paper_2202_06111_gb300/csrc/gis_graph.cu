@@ -1,13 +1,12 @@
-// gis_graph.cu -- symbolic image, pruning fixed point and subdivision kernels.
+// gis_graph.cu -- scans, the per-(cell, control) prune, boundary classification
+// and subdivision kernels.
 //
-//  k_edges<fill=false>  per pair: descend the subdivision tree over the leaves
-//                       whose closed box meets the image box (Def. 1, closed
-//                       cells of Sec. 2.1), count live targets, flag removed ones
 //  scan                 exclusive prefix sums (CSR offsets)
-//  k_edges<fill=true>   same descent, write targets (global slots)
-//  k_indeg/k_rscatter   transpose: pairs entering each cell
+//  k_indeg/k_rscatter   transpose of a per-(cell, control) graph: the pairs
+//                       entering each cell (used by gis_prune_graph_noalloc)
 //  k_prune              greatest fixed point of the pruning rule (Sec. 2.3,
-//                       Prop. 1) by frontier rounds in one cooperative launch
+//                       Prop. 1) on such a graph, frontier rounds in one
+//                       cooperative launch (gis_prune_graph_noalloc)
 //  k_classify           exact boundary rule (Sec. 3.1.1, Alg. 1, Remark 1)
 //  k_split              2^n children of boundary cells (Sec. 2.1, Sec. 3.1)
 #include "gis_kernels.cuh"
@@ -81,66 +80,6 @@ __device__ __forceinline__ int descend(const InstDesc &I, const RF &rf, V &visit
         cur[d]++;
     }
     return 0;
-}
-
-template <int N, bool FILL>
-__global__ void __launch_bounds__(256) k_edges(const InstDesc *__restrict__ D, const Range *__restrict__ R, int nr,
-                                               const int32_t *__restrict__ rng, uint8_t *__restrict__ pflag,
-                                               int32_t *__restrict__ cnt, const int64_t *__restrict__ off,
-                                               int32_t *__restrict__ tgt, int32_t *__restrict__ err)
-{
-    RANGE_HEAD(256)
-    const int64_t p = rg.first + local;
-    const uint8_t f = pflag[p];
-    if (f & PF_NONFINITE) {
-        if (!FILL) cnt[p] = 0;
-        return;
-    }
-    int c[N], fl[N];
-#pragma unroll
-    for (int d = 0; d < N; d++) {
-        c[d] = rng[p * 2 * N + d];
-        fl[d] = rng[p * 2 * N + N + d];
-    }
-    const int Lf = I.Lf;
-    auto rf = [&](int L, int d, int &a, int &b) { level_range(c[d], fl[d], Lf - L, I.n0[d] << L, a, b); };
-    int32_t count = 0;
-    bool touch = false;
-    int64_t w = FILL ? off[p] : 0;
-    auto visit = [&](int node, uint8_t st) {
-        if (st == ST_ALIVE) {
-            if (FILL) tgt[w++] = I.slot[node];
-            count++;
-        } else {
-            touch = true;
-        }
-        return true;
-    };
-    if (descend<N>(I, rf, visit)) atomicExch(err, GIS_EBOUNDS);
-    if (!FILL) {
-        cnt[p] = count;
-        if (touch) pflag[p] = f | PF_TOUCH_DEAD;
-    }
-}
-
-cudaError_t launch_edges(bool fill, int n, const InstDesc *D, const WorkList &w, const int32_t *rng,
-                         uint8_t *pflag, int32_t *cnt, const int64_t *off, int32_t *tgt, int32_t *err,
-                         cudaStream_t st)
-{
-    if (w.n_blocks == 0) return cudaSuccess;
-    dim3 g((unsigned)w.n_blocks), b(256);
-#define EDGES_CASE(NN)                                                                          \
-    case NN:                                                                                    \
-        if (fill) k_edges<NN, true><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges, rng, pflag, cnt, off, tgt, err); \
-        else k_edges<NN, false><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges, rng, pflag, cnt, off, tgt, err); \
-        note_launch(); \
-        break;
-    switch (n) {
-        EDGES_CASE(1) EDGES_CASE(2) EDGES_CASE(3) EDGES_CASE(4)
-    default: return cudaErrorInvalidValue;
-    }
-#undef EDGES_CASE
-    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -261,28 +200,6 @@ cudaError_t launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, void *sc
 }
 
 // ---------------------------------------------------------------------------
-// Slot gather: global slot of every live node, slot of every pair.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_gather(const InstDesc *__restrict__ D, const Range *__restrict__ R, int nr,
-                                                int32_t *__restrict__ pair_slot)
-{
-    RANGE_HEAD(256)
-    const int64_t s = rg.first + local;
-    const int ls = (int)(s - I.slot_base);
-    const int node = I.live[ls];
-    I.slot[node] = (int32_t)s;
-    const int64_t p0 = I.pair_base + (int64_t)ls * I.nu;
-    for (int u = 0; u < I.nu; u++) pair_slot[p0 + u] = (int32_t)s;
-}
-
-cudaError_t launch_gather(const InstDesc *D, const WorkList &w, int32_t *pair_slot, cudaStream_t st)
-{
-    if (w.n_blocks == 0) return cudaSuccess;
-    k_gather<<<(unsigned)w.n_blocks, 256, 0, st>>>(D, w.d_ranges, w.n_ranges, pair_slot); note_launch();
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
 // Transpose of the graph: rsrc lists, per target cell, the pairs entering it.
 // ---------------------------------------------------------------------------
 __global__ void k_indeg(const int32_t *__restrict__ tgt, int64_t E, int32_t *__restrict__ rcnt)
@@ -324,44 +241,6 @@ cudaError_t launch_rscatter(const int64_t *off, const int32_t *tgt, int64_t P, i
 // kills them. A cell dies when its last viable pair dies; dying cells form
 // the frontier of the next round.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_prune_init(const InstDesc *__restrict__ D, const Range *__restrict__ R,
-                                                    int nr, const int64_t *__restrict__ off,
-                                                    const uint8_t *__restrict__ pflag, int32_t *__restrict__ pstate,
-                                                    int32_t *__restrict__ ncnt, uint8_t *__restrict__ alive,
-                                                    int32_t *__restrict__ frontier0, uint32_t *__restrict__ sizes)
-{
-    RANGE_HEAD(256)
-    const int64_t s = rg.first + local;
-    const int64_t p0 = I.pair_base + (s - I.slot_base) * I.nu;
-    int32_t viable = 0;
-    for (int u = 0; u < I.nu; u++) {
-        const int64_t p = p0 + u;
-        int32_t b;
-        if (I.rule == GIS_RULE_OUTER) {
-            b = (int32_t)(off[p + 1] - off[p]);
-        } else {
-            const uint8_t f = pflag[p];
-            b = ((f & PF_INX) && !(f & (PF_TOUCH_DEAD | PF_NONFINITE))) ? 1 : 0;
-        }
-        pstate[p] = b;
-        viable += b > 0;
-    }
-    ncnt[s] = viable;
-    alive[s] = viable > 0;
-    if (viable == 0) frontier0[atomicAdd(&sizes[0], 1u)] = (int32_t)s;
-}
-
-cudaError_t launch_prune_init(int rule, const InstDesc *D, const WorkList &w, const int64_t *off,
-                              const uint8_t *pflag, int32_t *pstate, int32_t *ncnt, uint8_t *alive,
-                              int32_t *frontier0, uint32_t *sizes, cudaStream_t st)
-{
-    (void)rule;
-    if (w.n_blocks == 0) return cudaSuccess;
-    k_prune_init<<<(unsigned)w.n_blocks, 256, 0, st>>>(D, w.d_ranges, w.n_ranges, off, pflag, pstate, ncnt, alive,
-                                                       frontier0, sizes); note_launch();
-    return cudaGetLastError();
-}
-
 __global__ void __launch_bounds__(256) k_prune(PruneArgs a)
 {
     __shared__ uint32_t s_nf;
@@ -614,19 +493,6 @@ cudaError_t launch_count_kept(const WorkList &w, const uint8_t *alive, int64_t *
 {
     if (w.n_blocks == 0) return cudaSuccess;
     k_count_kept<<<(unsigned)w.n_blocks, 256, 0, st>>>(w.d_ranges, w.n_ranges, alive, per_inst); note_launch();
-    return cudaGetLastError();
-}
-
-__global__ void k_localize(const int32_t *__restrict__ tgt, int64_t E, int32_t base, int32_t *__restrict__ out)
-{
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x)
-        out[e] = tgt[e] - base;
-}
-
-cudaError_t launch_localize(const int32_t *tgt, int64_t E, int32_t base, int32_t *out, cudaStream_t st)
-{
-    if (E == 0) return cudaSuccess;
-    k_localize<<<grid_for(E, 256, 152 * 8), 256, 0, st>>>(tgt, E, base, out); note_launch();
     return cudaGetLastError();
 }
 

@@ -53,10 +53,6 @@ struct RecheckArgs {
     uint8_t *pflag;
 };
 cudaError_t launch_recheck(int phase, int dyn, int n, const RecheckArgs &a, cudaStream_t st);
-// count (fill = false) / fill (fill = true) by tree descent
-cudaError_t launch_edges(bool fill, int n, const InstDesc *D, const WorkList &w, const int32_t *rng,
-                         uint8_t *pflag, int32_t *cnt, const int64_t *off, int32_t *tgt,
-                         int32_t *err, cudaStream_t st);
 // exclusive scan of n int32 (or int64) values into int64 out[n + 1]; scratch >= scan_scratch_bytes(n)
 size_t scan_scratch_bytes(int64_t n);
 cudaError_t launch_scan_i32(const int32_t *in, int64_t *out, int64_t n, void *scratch, cudaStream_t st);
@@ -65,16 +61,11 @@ cudaError_t launch_scan_u8(const uint8_t *in, int64_t *out, int64_t n, void *scr
 cudaError_t launch_inst_totals(const int64_t *pscan, const int64_t *be, int n, int64_t *out, cudaStream_t st);
 cudaError_t launch_init_roots(uint8_t *lvl, uint8_t *state, int32_t *const *idx, int32_t *child, int32_t *live,
                               int n, const int32_t *n0, int64_t R, cudaStream_t st);
-// slot gather: node -> global slot, pair -> slot
-cudaError_t launch_gather(const InstDesc *D, const WorkList &wslots, int32_t *pair_slot, cudaStream_t st);
 // transpose
 cudaError_t launch_indeg(const int32_t *tgt, int64_t E, int32_t *rcnt, cudaStream_t st);
 cudaError_t launch_rscatter(const int64_t *off, const int32_t *tgt, int64_t P, int64_t *rcur,
                             int32_t *rsrc, cudaStream_t st);
 // prune
-cudaError_t launch_prune_init(int rule, const InstDesc *D, const WorkList &wslots, const int64_t *off,
-                              const uint8_t *pflag, int32_t *pstate, int32_t *ncnt, uint8_t *alive,
-                              int32_t *frontier0, uint32_t *sizes, cudaStream_t st);
 struct PruneArgs {
     int rule;
     const int64_t *roff;
@@ -152,8 +143,6 @@ cudaError_t launch_export_cells(const InstDesc *D, const WorkList &wslots, const
                                 const uint8_t *bnd, gis_cell *out, int only_kept, const int64_t *kept_scan,
                                 cudaStream_t st);
 cudaError_t launch_count_kept(const WorkList &wslots, const uint8_t *alive, int64_t *per_inst, cudaStream_t st);
-// graph export: tgt (global slot) -> instance-local cell index
-cudaError_t launch_localize(const int32_t *tgt, int64_t E, int32_t base, int32_t *out, cudaStream_t st);
 // boxes export
 cudaError_t launch_export_boxes(int n, const InstDesc *D, const WorkList &wpairs, float *box32, double *box64,
                                 uint8_t *exact, cudaStream_t st);

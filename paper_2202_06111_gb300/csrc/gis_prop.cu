@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(256) k_bin(const InstDesc *__restrict__ D, con
         return;
     }
 #pragma unroll
-    for (int e = 0; e < 2 * N; e++) rng[p * 2 * N + e] = out[e];
+    for (int e = 0; e < 2 * N; e++) rng[p * 2 * MAXN + e] = out[e];
     pflag[p] = inx ? PF_INX : 0;
 }
 
@@ -313,8 +313,8 @@ __global__ void __launch_bounds__(256) k_rc_cand(const InstDesc *__restrict__ D,
         const int64_t q = (int64_t)node * I.nu + u;
         const bool all64 = (I.exact[q] & EX_NF32) != 0;
         if (lane < N) {
-            mnk[(int64_t)it * N + lane] = dkey(INFINITY);
-            mxk[(int64_t)it * N + lane] = dkey(-INFINITY);
+            mnk[(int64_t)it * MAXN + lane] = dkey(INFINITY);
+            mxk[(int64_t)it * MAXN + lane] = dkey(-INFINITY);
         }
         if (lane == 0) bad[it] = 0;
         int32_t idx[N];
@@ -396,8 +396,8 @@ __global__ void __launch_bounds__(256) k_rc_fp64(const InstDesc *__restrict__ D,
                 atomicOr(&bad[c.x], 1);
                 continue;
             }
-            atomicMin(&mnk[(int64_t)c.x * N + d], dkey(y[d]));
-            atomicMax(&mxk[(int64_t)c.x * N + d], dkey(y[d]));
+            atomicMin(&mnk[(int64_t)c.x * MAXN + d], dkey(y[d]));
+            atomicMax(&mxk[(int64_t)c.x * MAXN + d], dkey(y[d]));
         }
     }
 }
@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(256) k_rc_final(const InstDesc *__restrict__ D
         for (int e = 0; e < 2 * N; e++) {
             if (!((upd >> e) & 1)) continue;
             const int d = e % N;
-            I.box64[q * 2 * N + e] = e < N ? dkey_inv(mnk[(int64_t)it * N + d]) : dkey_inv(mxk[(int64_t)it * N + d]);
+            I.box64[q * 2 * N + e] = e < N ? dkey_inv(mnk[(int64_t)it * MAXN + d]) : dkey_inv(mxk[(int64_t)it * MAXN + d]);
             ex |= 1u << e;
         }
         I.exact[q] = (uint16_t)ex;
@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(256) k_rc_final(const InstDesc *__restrict__ D
             else decide_approx<N>(I, e, I.box32[q * 4 * N + 2 * e], I.box32[q * 4 * N + 2 * e + 1], out[e], inx);
         }
 #pragma unroll
-        for (int e = 0; e < 2 * N; e++) rng[p * 2 * N + e] = out[e];
+        for (int e = 0; e < 2 * N; e++) rng[p * 2 * MAXN + e] = out[e];
         pflag[p] = inx ? PF_INX : 0;
     }
 }

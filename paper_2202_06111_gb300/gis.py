@@ -88,6 +88,19 @@ class gis_result(C.Structure):
                 ("cells_cap", C.c_int64)]
 
 
+class gis_server_opts(C.Structure):
+    _fields_ = [("max_active", C.c_int32), ("max_device_bytes", C.c_int64), ("lanes_per_pair", C.c_int32),
+                ("timing", C.c_int32)]
+
+
+_SERVER_STAT_FIELDS = [(k, C.c_int64) for k in ("submitted", "completed", "failed", "active", "queued", "steps",
+                                                "cells_built", "cell_edges", "budget_bytes", "admitted_bytes")]
+
+
+class gis_server_stats(C.Structure):
+    _fields_ = _SERVER_STAT_FIELDS
+
+
 # Names and signatures of every entry point of include/gis.h.
 SIGNATURES = {
     "gis_default_options": (None, [C.POINTER(gis_options)]),
@@ -106,6 +119,11 @@ SIGNATURES = {
     "gis_destroy": (None, [C.c_void_p]),
     "gis_batch_solve": (C.c_int32, [C.POINTER(gis_request), C.c_int32, C.POINTER(gis_result),
                                     C.POINTER(gis_options), C.c_void_p, C.POINTER(gis_stats)]),
+    "gis_server_create": (C.c_int32, [C.POINTER(C.c_void_p), C.POINTER(gis_server_opts), C.c_int32]),
+    "gis_server_submit": (C.c_int32, [C.c_void_p, C.POINTER(gis_request), C.POINTER(C.c_uint64)]),
+    "gis_server_poll": (C.c_int32, [C.c_void_p, C.c_uint64, C.POINTER(gis_result), C.POINTER(C.c_int32), C.c_int32]),
+    "gis_server_get_stats": (C.c_int32, [C.c_void_p, C.POINTER(gis_server_stats)]),
+    "gis_server_destroy": (None, [C.c_void_p]),
     "gis_prune_graph_noalloc": (C.c_int32, [C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                             C.c_int32, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p]),
 }
@@ -326,3 +344,83 @@ def batch_solve(problems: list[dict], stream: int | None = None, want_cells: boo
             d["kept"] = (a[:, 0].copy(), a[:, 2:2 + p["n"]].copy())
         out.append(d)
     return out, {k: getattr(st, k) for k, _ in _STAT_FIELDS}
+
+
+def _request(p: dict, keep: list) -> gis_request:
+    r = gis_request()
+    r.dyn = _dynamics(p)
+    r.grid = _grid(p)
+    c, u = _controls(p)
+    keep.append(u)
+    r.controls = c
+    r.levels = p.get("levels", 0)
+    r.rule = RULES[p.get("rule", "inner")]
+    r.precision = PRECISIONS[p.get("precision", "fp32")]
+    r.band = p.get("band", 0.0)
+    return r
+
+
+class Server:
+    """Continuous-batching server (gis_server_*): submit problems at any time,
+    poll or wait for their kept cells."""
+
+    def __init__(self, device: int = 0, max_active: int = 0, max_device_bytes: int = 0, lanes_per_pair: int = 0):
+        L = load()
+        o = gis_server_opts(max_active, max_device_bytes, lanes_per_pair, 0)
+        h = C.c_void_p()
+        _check(L.gis_server_create(C.byref(h), C.byref(o), device))
+        self._h = h
+        self._meta = {}
+
+    def submit(self, prob: dict) -> int:
+        keep = []
+        r = _request(prob, keep)
+        t = C.c_uint64()
+        _check(load().gis_server_submit(self._h, C.byref(r), C.byref(t)))
+        self._meta[t.value] = prob
+        return t.value
+
+    def poll(self, ticket: int, wait: bool = False, want_cells: bool = True):
+        """None while running; else a result dict (as batch_solve's)."""
+        prob = self._meta[ticket]
+        res = gis_result()
+        buf = None
+        if want_cells:
+            cap = prob.get("cells_cap", 2 * int(np.prod(prob["n0"])) * (1 + prob.get("levels", 0)))
+            buf = (gis_cell * cap)()
+            res.cells = C.cast(buf, C.POINTER(gis_cell))
+            res.cells_cap = cap
+        done = C.c_int32()
+        rc = load().gis_server_poll(self._h, ticket, C.byref(res), C.byref(done), 1 if wait else 0)
+        if rc == EBOUNDS and want_cells:          # buffer too small: size it from the result
+            cap = res.n_kept
+            buf = (gis_cell * max(cap, 1))()
+            res.cells = C.cast(buf, C.POINTER(gis_cell))
+            res.cells_cap = cap
+            rc = load().gis_server_poll(self._h, ticket, C.byref(res), C.byref(done), 1)
+        _check(rc)
+        if not done.value:
+            return None
+        del self._meta[ticket]
+        d = {"status": res.status, "n_kept": res.n_kept, "n_cells": res.n_cells, "n_edges_total": res.n_edges_total,
+             "cells_built": res.cells_built, "levels_done": res.levels_done}
+        if want_cells:
+            a = np.frombuffer(buf, dtype=np.int32).reshape(-1, 2 + MAXN)[:min(res.n_kept, res.cells_cap)]
+            d["kept"] = (a[:, 0].copy(), a[:, 2:2 + prob["n"]].copy())
+        return d
+
+    def stats(self) -> dict:
+        s = gis_server_stats()
+        _check(load().gis_server_get_stats(self._h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in _SERVER_STAT_FIELDS}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gis_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
