@@ -310,6 +310,8 @@ def run_gis(a, prob):
                                                                        "p99": max(per_step)},
             "cells_per_step": cells / len(stats), "edges_per_step": edges / len(stats),
             "recheck_pairs_per_step": agg["cum_recheck"] / len(stats),
+            "recheck_samples_per_step": agg["cum_recheck_samples"] / len(stats),
+            "pairs_propagated_per_step": agg["cum_pairs_propagated"] / len(stats),
             "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
             "fp64_plain": {"ms_per_step": statistics.mean(fp64_ms),
                            "speedup_of_fp32_recheck": statistics.mean(fp64_ms) / (total_ms / len(per_step)),

@@ -5,10 +5,12 @@
 // the bitmask of the controls u whose image box meets B_j, so the per-(cell,
 // control) graph is recovered without storing it:
 //   k_cgather     global slot of every live node, per-cell pair start / info
-//   k_cedges<0>   one warp per cell: lane u holds control u's box; the warp
-//                 descends the subdivision tree once over the union of the
-//                 boxes and a ballot gives each leaf's control mask; counts
-//                 edges per cell, targets per pair, in-degrees, removed leaves
+//   k_cchunks     per cell the number of chunks of its union box
+//   k_cedges<0>   persistent warps over runs of chunks: lane u holds control
+//                 u's box; the warp descends the subdivision tree over the
+//                 union of the boxes and a ballot gives each leaf's control
+//                 mask; counts edges per cell, targets per pair, in-degrees,
+//                 removed leaves
 //   k_cedges<1>   same descent: writes the edges (target, mask), coalesced,
 //                 and scatters the reverse edges (source, mask)
 //   k_cprune      greatest fixed point (Sec. 2.3): INNER clears a dead
@@ -31,7 +33,8 @@ namespace gis {
 // Global slot of every live node; per cell the index of its first pair and
 // its control count / rule (cinfo = n_controls | rule << 6).
 __global__ void __launch_bounds__(256) k_cgather(const InstDesc *__restrict__ D, const Range *__restrict__ R, int nr,
-                                                 int32_t *__restrict__ cps, uint8_t *__restrict__ cinfo)
+                                                 int32_t *__restrict__ cps, uint8_t *__restrict__ cinfo,
+                                                 int32_t *__restrict__ cinst)
 {
     CRANGE_HEAD(256)
     const int64_t local = (int64_t)(blockIdx.x - rg.block_start) * 256 + threadIdx.x;
@@ -41,12 +44,14 @@ __global__ void __launch_bounds__(256) k_cgather(const InstDesc *__restrict__ D,
     I.slot[I.live[ls]] = (int32_t)s;
     cps[s] = (int32_t)(I.pair_base + (int64_t)ls * I.nu);
     cinfo[s] = (uint8_t)(I.nu | (I.rule << 6));
+    cinst[s] = rg.inst;
 }
 
-cudaError_t launch_cgather(const InstDesc *D, const WorkList &w, int32_t *cps, uint8_t *cinfo, cudaStream_t st)
+cudaError_t launch_cgather(const InstDesc *D, const WorkList &w, int32_t *cps, uint8_t *cinfo, int32_t *cinst,
+                           cudaStream_t st)
 {
     if (w.n_blocks == 0) return cudaSuccess;
-    k_cgather<<<(unsigned)w.n_blocks, 256, 0, st>>>(D, w.d_ranges, w.n_ranges, cps, cinfo);
+    k_cgather<<<(unsigned)w.n_blocks, 256, 0, st>>>(D, w.d_ranges, w.n_ranges, cps, cinfo, cinst);
     note_launch();
     return cudaGetLastError();
 }
@@ -66,37 +71,113 @@ __device__ __forceinline__ int warp_max(int v)
     return v;
 }
 
-// Controls (bits of `live`) whose level-L index range holds idx; the ranges
-// come from each control's finest-level decisions c (ceil) and f (floor).
-template <int N>
-__device__ __forceinline__ uint32_t ctl_mask(const int (*sc)[N], const int (*sf)[N], uint32_t live, int shift,
-                                             const int *NL, const int *idx)
+// Work of the edge kernels comes in chunks of CE_CHUNK root cells of a
+// cell's union box (the union over its controls of their level-0 index
+// boxes), so that the few cells whose images reach far across X are shared by
+// many warps instead of trailing behind all the others. A cell has
+// max(1, ceil(roots / CE_CHUNK)) chunks; the exclusive scan of these counts
+// numbers the chunks of a run of cells contiguously.
+constexpr int64_t CE_CHUNK = 64;
+
+__global__ void __launch_bounds__(256) k_cchunks(const InstDesc *__restrict__ D, int64_t NL,
+                                                 const int32_t *__restrict__ cinst, const int32_t *__restrict__ rng,
+                                                 const uint8_t *__restrict__ pflag, int32_t *__restrict__ nch)
 {
-    uint32_t m = 0;
-    for (uint32_t b = live; b; b &= b - 1) {
-        const int u = __ffs(b) - 1;
-        bool in = true;
-#pragma unroll
-        for (int d = 0; d < N; d++) {
-            int a, e;
-            level_range(sc[u][d], sf[u][d], shift, NL[d], a, e);
-            in = in && idx[d] >= a && idx[d] <= e;
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= NL) return;
+    const InstDesc &I = D[cinst[s]];
+    const int n = I.n, Lf = I.Lf;
+    const int64_t p0 = I.pair_base + (s - I.slot_base) * I.nu;
+    int ua[MAXN], ub[MAXN];
+    bool any = false;
+    for (int d = 0; d < MAXN; d++) { ua[d] = INT_MAX; ub[d] = INT_MIN; }
+    for (int u = 0; u < I.nu; u++) {
+        const int64_t p = p0 + u;
+        if (pflag[p] & PF_NONFINITE) continue;
+        int a[MAXN], b[MAXN];
+        bool ok = true;
+        for (int d = 0; d < n; d++) {
+            level_range(rng[p * 2 * MAXN + d], rng[p * 2 * MAXN + n + d], Lf, I.n0[d], a[d], b[d]);
+            ok = ok && a[d] <= b[d];
         }
-        m |= (uint32_t)in << u;
+        if (!ok) continue;
+        any = true;
+        for (int d = 0; d < n; d++) { ua[d] = min(ua[d], a[d]); ub[d] = max(ub[d], b[d]); }
     }
-    return m;
+    int64_t roots = any ? 1 : 0;
+    for (int d = 0; d < n && any; d++) roots *= (int64_t)(ub[d] - ua[d] + 1);
+    nch[s] = (int32_t)max((int64_t)1, (roots + CE_CHUNK - 1) / CE_CHUNK);
 }
 
-// Edges of one cell, one warp: the lanes walk the leaves of the union of the
-// controls' boxes in parallel (root cells of the union box, then each lane its
-// own subtree stack); a leaf's control mask is the set of controls whose box
-// holds it. Edges found in the same step are compacted across the warp.
-// FILL = false: edges per cell (ccnt), targets per pair (pcnt), in-degrees
-// (rcnt), removed-leaf flags, pair-edge total. FILL = true: edges at
-// coff[cell] (cent, cmask) and reverse edges at rcur[target]++ (rsrc, rmask).
+cudaError_t launch_cchunks(const InstDesc *D, int64_t NL, const int32_t *cinst, const int32_t *rng,
+                           const uint8_t *pflag, int32_t *nch, cudaStream_t st)
+{
+    if (NL == 0) return cudaSuccess;
+    k_cchunks<<<(unsigned)((NL + 255) / 256), 256, 0, st>>>(D, NL, cinst, rng, pflag, nch);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// Control u's level-L index range on dimension d is
+//   ceil(c / 2^sh) - 1 <= i <= floor(f / 2^sh),   sh = Lf - L,
+// with c (ceil) and f (floor) its finest-level decisions; equivalently
+//   (i + 1) << sh >= c  and  i << sh <= f,
+// so a node tests each control with two compares against the shifted corners
+// of its own index (lo = i << sh, hi = (i + 1) << sh). The ranges' clamps to
+// [0, n0 << L) do not change membership of an index inside the grid.
+template <int N>
+struct alignas(N == 2 || N == 4 ? 16 : 8) CtlBox {
+    int cf[2 * N];   // c_0, f_0, c_1, f_1, ...
+};
+
+template <int N>
+__device__ __forceinline__ uint32_t ctl_mask(const CtlBox<N> *__restrict__ box, int nu, uint32_t mask,
+                                             const int *lo, const int *hi)
+{
+    uint32_t m = 0;
+    for (int u = 0; u < nu; u++) {
+        const CtlBox<N> b = box[u];
+        bool in = true;
+#pragma unroll
+        for (int d = 0; d < N; d++) in = in && hi[d] >= b.cf[2 * d] && lo[d] <= b.cf[2 * d + 1];
+        m |= (uint32_t)in << u;
+    }
+    return m & mask;
+}
+
+// k-th set bit (from 0) of m; m has more than k set bits.
+__device__ __forceinline__ int nth_set(uint32_t m, int k)
+{
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1)
+        if (__popc(m & ((1u << (pos + w)) - 1u)) <= k) pos += w;
+    return pos;
+}
+
+static_assert((STACK & (STACK - 1)) == 0, "descent stack is a ring of 2^k entries");
+
+// Edges of the cells c0 <= s < c1 (all of dimension N). The chunks
+// cbase[c0] .. cbase[c1] are split evenly over the grid's warps; a warp finds
+// the cell of its first chunk by a 32-way search of cbase, then walks its
+// chunks in order, one cell at a time. Lane u holds control u's box. The lanes
+// take the run's root cells 32 at a time; a split node's 2^n children go on
+// the lane's own stack (a ring: the lane pops the newest entry, and a lane
+// with no work left takes the oldest entry of another lane's stack, the
+// largest subtree still waiting). A node's control mask is the set of its
+// parent's controls whose box holds it; edges found in the same step are
+// compacted across the warp.
+// FILL = false: edges per cell (ccnt) and targets per pair (pcnt), added up
+// over the warps that share a cell (both zeroed beforehand), in-degrees
+// (rcnt), removed-leaf flags, the pair-edge total, and per warp the edges it
+// found in its last cell (wpart). FILL = true: a cell's edges at coff[cell]
+// plus the edges its earlier chunks hold (cent, cmask), reverse edges at
+// rcur[target]++ (rsrc, rmask).
 template <int N, bool FILL>
-__global__ void __launch_bounds__(CE_WARPS * 32) k_cedges(const InstDesc *__restrict__ D, const Range *__restrict__ R,
-                                                         int nr, const int32_t *__restrict__ rng,
+__global__ void __launch_bounds__(CE_WARPS * 32) k_cedges(const InstDesc *__restrict__ D, int64_t c0, int64_t c1,
+                                                         const int64_t *__restrict__ cbase,
+                                                         const int32_t *__restrict__ cinst,
+                                                         const int32_t *__restrict__ rng,
                                                          uint8_t *__restrict__ pflag, int32_t *__restrict__ pcnt,
                                                          int32_t *__restrict__ ccnt, int32_t *__restrict__ rcnt,
                                                          const int64_t *__restrict__ coff, int32_t *__restrict__ cent,
@@ -104,158 +185,289 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cedges(const InstDesc *__rest
                                                          unsigned long long *__restrict__ rcur,
                                                          int32_t *__restrict__ rsrc, uint32_t *__restrict__ rmask,
                                                          unsigned long long *__restrict__ pair_edges,
-                                                         int32_t *__restrict__ err)
+                                                         int32_t *__restrict__ wpart, int32_t *__restrict__ err)
 {
-    __shared__ int s_c[CE_WARPS][32][N], s_f[CE_WARPS][32][N];
-    __shared__ int s_cnt[CE_WARPS][32];
-    __shared__ uint32_t s_touch[CE_WARPS];
-    CRANGE_HEAD(CE_WARPS)
+    constexpr uint32_t FULL = 0xffffffffu;
+    __shared__ CtlBox<N> s_box[CE_WARPS][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t local = (int64_t)(blockIdx.x - rg.block_start) * CE_WARPS + warp;
-    if (local >= rg.count) return;                 // whole warp
-    const int64_t s = rg.first + local;
-    const int ls = (int)(s - I.slot_base);
-    const int nu = I.nu, Lf = I.Lf;
-    const int64_t p = I.pair_base + (int64_t)ls * nu + lane;
-    int (*sc)[N] = s_c[warp];
-    int (*sf)[N] = s_f[warp];
-    // control `lane`: finest-level decisions, level-0 box
-    bool live_box = false;
-    int a0[N], b0[N];
-#pragma unroll
-    for (int d = 0; d < N; d++) { a0[d] = INT_MAX; b0[d] = INT_MIN; }
-    if (lane < nu) {
-        live_box = !(pflag[p] & PF_NONFINITE);
-        if (live_box) {
-#pragma unroll
-            for (int d = 0; d < N; d++) {
-                const int c = rng[p * 2 * MAXN + d], f = rng[p * 2 * MAXN + N + d];
-                sc[lane][d] = c;
-                sf[lane][d] = f;
-                int a, b;
-                level_range(c, f, Lf, I.n0[d], a, b);
-                live_box = live_box && a <= b;
-                a0[d] = a;
-                b0[d] = b;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t W = (int64_t)gridDim.x * CE_WARPS, w = (int64_t)blockIdx.x * CE_WARPS + warp;
+    const int64_t kb = cbase[c0], K = cbase[c1] - kb;
+    const int64_t k0 = kb + w * K / W, k1 = kb + (w + 1) * K / W;
+    if (k0 == k1) {
+        if (!FILL && lane == 0) wpart[w] = 0;
+        return;                                    // whole warp
+    }
+    // cell of chunk k0: cbase[lo] <= k0 < cbase[hi], 32 probes per round
+    int64_t lo = c0, hi = c1;
+    while (hi - lo > 1) {
+        const int64_t span = hi - lo;
+        const int64_t pos = span <= 32 ? lo + 1 + lane : lo + span * (lane + 1) / 33;
+        const bool valid = pos < hi;
+        const uint32_t le = __ballot_sync(FULL, valid && cbase[pos] <= k0);
+        const int nv = __popc(__ballot_sync(FULL, valid));
+        const int t = __popc(le);
+        const int64_t plo = __shfl_sync(FULL, pos, t > 0 ? t - 1 : 0);
+        const int64_t phi = __shfl_sync(FULL, pos, t < nv ? t : 0);
+        if (t > 0) lo = plo;
+        if (t < nv) hi = phi;
+    }
+    int64_t s = lo, k = k0;
+    int64_t wpos = 0;
+    if (FILL) {
+        const int64_t cb = cbase[s];
+        int64_t skip = 0;
+        if (k0 > cb)                               // the cell began in earlier warps' runs
+            for (int64_t j = w - 1; j >= 0; j--) {
+                skip += wpart[j];
+                if (kb + j * K / W <= cb) break;
             }
-        }
-        s_cnt[warp][lane] = 0;
+        wpos = coff[s] + skip;
     }
-    if (lane == 0) s_touch[warp] = 0;
-    const uint32_t live = __ballot_sync(0xffffffffu, live_box);
-    int ua[N], ub[N], ext[N];
-    int64_t nroots = live ? 1 : 0;
-#pragma unroll
-    for (int d = 0; d < N; d++) {
-        ua[d] = warp_min(live_box ? a0[d] : INT_MAX);
-        ub[d] = warp_max(live_box ? b0[d] : INT_MIN);
-        ext[d] = ub[d] - ua[d] + 1;
-        nroots *= live ? ext[d] : 1;
-    }
-    __syncwarp();
-    int nl[N];
-    int stack[STACK];
-    int sp = 0;
-    int64_t next = lane;
-    int64_t wpos = FILL ? coff[s] : 0;
-    int32_t nent = 0;
+    CtlBox<N> *box = s_box[warp];
     unsigned long long pe = 0;
-    for (;;) {
-        int node = -1;
-        int idx[N];
-        int L = 0;
-        if (sp > 0) {
-            node = stack[--sp];
-        } else if (next < nroots) {
-            int64_t q = next;
-            int r = 0;
-            int rc[N];
+    while (k < k1) {
+        const InstDesc &I = D[cinst[s]];
+        const int ls = (int)(s - I.slot_base);
+        const int nu = I.nu, Lf = I.Lf;
+        const int64_t p = I.pair_base + (int64_t)ls * nu + lane;
+        int n0[N];
 #pragma unroll
-            for (int d = N - 1; d >= 0; d--) {
-                rc[d] = ua[d] + (int)(q % ext[d]);
-                q /= ext[d];
-            }
+        for (int d = 0; d < N; d++) n0[d] = I.n0[d];
+        // control `lane`: finest-level decisions, level-0 box
+        bool live_box = false;
+        int a0[N], b0[N];
 #pragma unroll
-            for (int d = 0; d < N; d++) r = r * I.n0[d] + rc[d];
-            node = r;
-            next += 32;
-        }
-        const bool active = node >= 0;
-        if (!__any_sync(0xffffffffu, active)) break;
-        uint32_t m = 0;
-        uint8_t st = ST_DEAD;
-        if (active) {
-            st = I.state[node];
-            L = I.lvl[node];
-#pragma unroll
-            for (int d = 0; d < N; d++) {
-                idx[d] = I.idx[d][node];
-                nl[d] = I.n0[d] << L;
-            }
-            m = ctl_mask<N>(sc, sf, live, Lf - L, nl, idx);
-            if (m && st == ST_SPLIT) {
-                const int ch = I.child[node];
-#pragma unroll
-                for (int d = 0; d < N; d++) nl[d] <<= 1;
-                for (int cc = (1 << N) - 1; cc >= 0; cc--) {
-                    int ci[N];
-#pragma unroll
-                    for (int d = 0; d < N; d++) ci[d] = 2 * idx[d] + ((cc >> (N - 1 - d)) & 1);
-                    if (!ctl_mask<N>(sc, sf, m, Lf - L - 1, nl, ci)) continue;
-                    if (sp >= STACK) { atomicExch(err, GIS_EBOUNDS); continue; }
-                    stack[sp++] = ch + cc;
-                }
-            } else if (m && st == ST_DEAD) {
-                atomicOr(&s_touch[warp], m);
-            }
-        }
-        const bool emit = active && st == ST_ALIVE && m != 0;
-        const uint32_t b = __ballot_sync(0xffffffffu, emit);
-        if (emit) {
-            const int t = I.slot[node];
-            if (FILL) {
-                const int64_t pos = wpos + __popc(b & ((1u << lane) - 1u));
-                cent[pos] = t;
-                cmask[pos] = m;
-                const unsigned long long r = atomicAdd(&rcur[t], 1ull);
-                rsrc[r] = (int32_t)s;
-                rmask[r] = m;
-            } else {
-                atomicAdd(&rcnt[t], 1);
-                for (uint32_t mm = m; mm; mm &= mm - 1) atomicAdd(&s_cnt[warp][__ffs(mm) - 1], 1);
-            }
-        }
-        pe += (unsigned long long)__reduce_add_sync(0xffffffffu, emit ? (unsigned)__popc(m) : 0u);
-        wpos += __popc(b);
-        nent += __popc(b);
-    }
-    __syncwarp();
-    if (!FILL) {
+        for (int d = 0; d < N; d++) { a0[d] = INT_MAX; b0[d] = INT_MIN; }
         if (lane < nu) {
-            pcnt[p] = s_cnt[warp][lane];
-            if ((s_touch[warp] >> lane) & 1) pflag[p] |= PF_TOUCH_DEAD;
+            live_box = !(pflag[p] & PF_NONFINITE);
+            if (live_box) {
+                CtlBox<N> cb_;
+#pragma unroll
+                for (int d = 0; d < N; d++) {
+                    const int c = rng[p * 2 * MAXN + d], f = rng[p * 2 * MAXN + N + d];
+                    cb_.cf[2 * d] = c;
+                    cb_.cf[2 * d + 1] = f;
+                    int a, b;
+                    level_range(c, f, Lf, n0[d], a, b);
+                    live_box = live_box && a <= b;
+                    a0[d] = a;
+                    b0[d] = b;
+                }
+                box[lane] = cb_;
+            }
         }
-        if (lane == 0) {
-            ccnt[s] = nent;
-            if (pe) atomicAdd(pair_edges, pe);
+        const uint32_t live = __ballot_sync(FULL, live_box);
+        int ua[N], ext[N];
+        int64_t nroots = live ? 1 : 0;
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            ua[d] = warp_min(live_box ? a0[d] : INT_MAX);
+            const int ub = warp_max(live_box ? b0[d] : INT_MIN);
+            ext[d] = ub - ua[d] + 1;
+            nroots *= live ? ext[d] : 1;
         }
+        __syncwarp();
+        const int64_t cb = cbase[s], ce = cbase[s + 1], kend = min(ce, k1);
+        const int64_t r1 = min(nroots, (kend - cb) * CE_CHUNK);
+        const bool small = r1 < ((int64_t)1 << 31);
+        int64_t next = (k - cb) * CE_CHUNK + lane;
+        // per-lane ring stack of (node, level, index, parent's mask)
+        int stn[STACK], stl[STACK], sti[STACK][N];
+        uint32_t stm[STACK];
+        int sb = 0, sp = 0;                        // entries sb .. sp-1 (mod STACK)
+        int32_t nent = 0, myc = 0;
+        uint32_t tch = 0;
+        for (;;) {
+            // lanes with nothing left take the oldest entry of a lane holding two or more
+            const uint32_t idle = __ballot_sync(FULL, sp == sb && next >= r1);
+            if (idle) {
+                const uint32_t rich = __ballot_sync(FULL, sp - sb >= 2);
+                if (rich && idle != FULL) {
+                    const int nt = min(__popc(idle), __popc(rich));
+                    const bool donor = ((rich >> lane) & 1u) && __popc(rich & lt) < nt;
+                    const bool recv = ((idle >> lane) & 1u) && __popc(idle & lt) < nt;
+                    int gn = 0, gl = 0, gi[N];
+                    uint32_t gm = 0;
+#pragma unroll
+                    for (int d = 0; d < N; d++) gi[d] = 0;
+                    if (donor) {
+                        const int q = sb & (STACK - 1);
+                        gn = stn[q];
+                        gl = stl[q];
+#pragma unroll
+                        for (int d = 0; d < N; d++) gi[d] = sti[q][d];
+                        gm = stm[q];
+                        sb++;
+                    }
+                    const int src = recv ? nth_set(rich, __popc(idle & lt)) : lane;
+                    gn = __shfl_sync(FULL, gn, src);
+                    gl = __shfl_sync(FULL, gl, src);
+#pragma unroll
+                    for (int d = 0; d < N; d++) gi[d] = __shfl_sync(FULL, gi[d], src);
+                    gm = __shfl_sync(FULL, gm, src);
+                    if (recv) {
+                        sb = 0;
+                        sp = 1;
+                        stn[0] = gn;
+                        stl[0] = gl;
+#pragma unroll
+                        for (int d = 0; d < N; d++) sti[0][d] = gi[d];
+                        stm[0] = gm;
+                    }
+                }
+            }
+            int node = -1, L = 0, idx[N];
+            uint32_t pm = live;
+            if (sp != sb) {
+                const int q = (--sp) & (STACK - 1);
+                node = stn[q];
+                L = stl[q];
+#pragma unroll
+                for (int d = 0; d < N; d++) idx[d] = sti[q][d];
+                pm = stm[q];
+                if (sp == sb) sb = sp = 0;
+            } else if (next < r1) {
+                int r = 0;
+                if (small) {
+                    uint32_t q = (uint32_t)next;
+#pragma unroll
+                    for (int d = N - 1; d > 0; d--) {
+                        const uint32_t qq = q / (uint32_t)ext[d];
+                        idx[d] = ua[d] + (int)(q - qq * (uint32_t)ext[d]);
+                        q = qq;
+                    }
+                    idx[0] = ua[0] + (int)q;
+                } else {
+                    int64_t q = next;
+#pragma unroll
+                    for (int d = N - 1; d >= 0; d--) {
+                        idx[d] = ua[d] + (int)(q % ext[d]);
+                        q /= ext[d];
+                    }
+                }
+#pragma unroll
+                for (int d = 0; d < N; d++) r = r * n0[d] + idx[d];
+                node = r;
+                next += 32;
+            }
+            const bool active = node >= 0;
+            if (!__any_sync(FULL, active)) break;
+            uint32_t m = 0;
+            uint8_t st = ST_DEAD;
+            if (active) {
+                st = I.state[node];
+                const int sh = Lf - L;
+                int clo[N], chi[N];
+#pragma unroll
+                for (int d = 0; d < N; d++) {
+                    clo[d] = idx[d] << sh;
+                    chi[d] = (idx[d] + 1) << sh;
+                }
+                m = ctl_mask<N>(box, nu, pm, clo, chi);
+                if (m && st == ST_SPLIT) {
+                    if (sp - sb + (1 << N) > STACK) {
+                        atomicExch(err, GIS_EBOUNDS);
+                    } else {
+                        const int ch = I.child[node];
+                        for (int cc = (1 << N) - 1; cc >= 0; cc--) {
+                            const int q = (sp++) & (STACK - 1);
+                            stn[q] = ch + cc;
+                            stl[q] = L + 1;
+#pragma unroll
+                            for (int d = 0; d < N; d++) sti[q][d] = 2 * idx[d] + ((cc >> (N - 1 - d)) & 1);
+                            stm[q] = m;
+                        }
+                    }
+                } else if (m && st == ST_DEAD) {
+                    tch |= m;
+                }
+            }
+            const bool emit = active && st == ST_ALIVE && m != 0;
+            const uint32_t b = __ballot_sync(FULL, emit);
+            if (emit) {
+                const int t = I.slot[node];
+                if (FILL) {
+                    const int64_t pos = wpos + __popc(b & lt);
+                    cent[pos] = t;
+                    cmask[pos] = m;
+                    const unsigned long long r = atomicAdd(&rcur[t], 1ull);
+                    rsrc[r] = (int32_t)s;
+                    rmask[r] = m;
+                } else {
+                    atomicAdd(&rcnt[t], 1);
+                }
+            }
+            if (!FILL && b) {
+                // targets per control: one ballot per control present in the step
+                const uint32_t orm = __reduce_or_sync(FULL, emit ? m : 0u);
+                for (uint32_t mm = orm; mm; mm &= mm - 1) {
+                    const int u = __ffs(mm) - 1;
+                    const uint32_t bu = __ballot_sync(FULL, emit && ((m >> u) & 1u));
+                    if (lane == u) myc += __popc(bu);
+                }
+            }
+            wpos += __popc(b);
+            nent += __popc(b);
+        }
+        if (!FILL) {
+            const uint32_t touched = __reduce_or_sync(FULL, tch);
+            const bool whole = k == cb && ce <= k1;
+            if (lane < nu) {
+                if (whole) pcnt[p] = myc;
+                else if (myc) atomicAdd(&pcnt[p], myc);
+                if ((touched >> lane) & 1) pflag[p] |= PF_TOUCH_DEAD;
+            }
+            pe += (unsigned long long)__reduce_add_sync(FULL, lane < nu ? (unsigned)myc : 0u);
+            if (lane == 0) {
+                if (whole) ccnt[s] = nent;
+                else if (nent) atomicAdd(&ccnt[s], nent);
+                if (kend == k1) wpart[w] = nent;
+            }
+        }
+        __syncwarp();
+        k = kend;
+        s++;
+        if (FILL && k < k1) wpos = coff[s];        // the next cell starts at its first chunk
     }
+    if (!FILL && lane == 0 && pe) atomicAdd(pair_edges, pe);
 }
 
-cudaError_t launch_cedges(bool fill, int n, const InstDesc *D, const WorkList &w, const CellGraph &g, cudaStream_t st)
+// Persistent grid, the same for the count and the fill pass (the fill reads
+// the count's per-warp partials): as many blocks as fit on the device at once
+// for both.
+template <int N>
+static int cedges_grid(int dev)
 {
-    if (w.n_blocks == 0) return cudaSuccess;
-    dim3 gr((unsigned)w.n_blocks), b(CE_WARPS * 32);
+    static int cached[64] = {};
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int a = 0, b = 0, sms = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_cedges<N, false>, CE_WARPS * 32, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cedges<N, true>, CE_WARPS * 32, 0);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = std::max(1, std::min(a, b)) * std::max(1, sms);
+    }
+    return cached[dev];
+}
+
+cudaError_t launch_cedges(bool fill, int n, const InstDesc *D, int64_t c0, int64_t c1, const int64_t *cbase,
+                          const int32_t *cinst, const CellGraph &g, int32_t *wpart, cudaStream_t st)
+{
+    if (c1 <= c0) return cudaSuccess;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    dim3 b(CE_WARPS * 32);
 #define CE_CASE(NN)                                                                                        \
     case NN:                                                                                               \
         if (fill)                                                                                          \
-            k_cedges<NN, true><<<gr, b, 0, st>>>(D, w.d_ranges, w.n_ranges, g.rng, g.pflag, g.pcnt, g.ccnt,  \
-                                                 g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rsrc, g.rmask,  \
-                                                 g.pair_edges, g.err);                                     \
+            k_cedges<NN, true><<<cedges_grid<NN>(dev), b, 0, st>>>(                                  \
+                D, c0, c1, cbase, cinst, g.rng, g.pflag, g.pcnt, g.ccnt, g.rcnt, g.coff, g.cent, g.cmask,  \
+                g.rcur, g.rsrc, g.rmask, g.pair_edges, wpart, g.err);                                      \
         else                                                                                               \
-            k_cedges<NN, false><<<gr, b, 0, st>>>(D, w.d_ranges, w.n_ranges, g.rng, g.pflag, g.pcnt, g.ccnt, \
-                                                  g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rsrc, g.rmask, \
-                                                  g.pair_edges, g.err);                                    \
+            k_cedges<NN, false><<<cedges_grid<NN>(dev), b, 0, st>>>(                                 \
+                D, c0, c1, cbase, cinst, g.rng, g.pflag, g.pcnt, g.ccnt, g.rcnt, g.coff, g.cent, g.cmask,  \
+                g.rcur, g.rsrc, g.rmask, g.pair_edges, wpart, g.err);                                      \
         note_launch();                                                                                     \
         break;
     switch (n) {
@@ -266,7 +478,16 @@ cudaError_t launch_cedges(bool fill, int n, const InstDesc *D, const WorkList &w
     return cudaGetLastError();
 }
 
-int cedges_cells_per_block() { return CE_WARPS; }
+// Upper bound of the warps of one edge launch (size of wpart per dimension).
+int cedges_max_warps(int dev)
+{
+    int m = 0;
+    m = std::max(m, cedges_grid<1>(dev));
+    m = std::max(m, cedges_grid<2>(dev));
+    m = std::max(m, cedges_grid<3>(dev));
+    m = std::max(m, cedges_grid<4>(dev));
+    return m * CE_WARPS;
+}
 
 // ---------------------------------------------------------------------------
 // Prune on the cell graph. vmask[i] holds the controls of cell i that are

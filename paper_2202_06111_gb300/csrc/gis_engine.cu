@@ -119,12 +119,13 @@ gis_status gis_solve(gis_ctx *ctx, int32_t levels)
     Engine &E = ctx->eng;
     for (int L = 0; L <= levels; L++) {
         E.build_graph({0});
-        E.prune();
+        E.prune(false);
         if (L < levels) {
             check_depth(*E.inst[0], E.inst[0]->level + 1);
             E.subdivide({0});
         }
     }
+    E.finish_prune();
     E.sync();
     API_END(ctx)
 }

@@ -55,8 +55,35 @@ struct Error {
     } while (0)
 
 // ------------------------------------------------------------------ memory --
+// The library's own stream-ordered memory pool per device, which keeps freed
+// memory (no release threshold) so that contexts created one after another
+// reuse it instead of mapping new memory.
+inline cudaMemPool_t library_pool(int dev)
+{
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr);
+        pools[dev] = p;
+    }
+    return pools[dev];
+}
+
 struct Mem {
     cudaStream_t st = nullptr;
+    cudaMemPool_t pool = nullptr;
     int64_t limit = 0, used = 0;
     std::map<void *, size_t> sizes;
 
@@ -66,7 +93,7 @@ struct Mem {
         if (limit > 0 && used + (int64_t)bytes > limit)
             throw Error{GIS_ENOMEM, "device memory limit reached (" + std::to_string(used + bytes) + " bytes)"};
         void *p = nullptr;
-        cudaError_t e = cudaMallocAsync(&p, bytes, st);
+        cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, st) : cudaMallocAsync(&p, bytes, st);
         if (e != cudaSuccess) {
             cudaGetLastError();
             throw Error{GIS_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e)};
@@ -440,6 +467,10 @@ struct Engine {
     uint32_t *cmask = nullptr; size_t c_cmask = 0;
     uint32_t *rmask = nullptr; size_t c_rmask = 0;
     uint32_t *vmask = nullptr; size_t c_vmask = 0;
+    int32_t *cinst = nullptr; size_t c_cinst = 0;
+    int32_t *cnch = nullptr; size_t c_cnch = 0;
+    int64_t *cbase = nullptr; size_t c_cbase = 0;
+    int32_t *wpart = nullptr; size_t c_wpart = 0;
     int32_t *rng = nullptr; size_t c_rng = 0;
     uint8_t *pflag = nullptr; size_t c_pflag = 0;
     int32_t *cnt = nullptr; size_t c_cnt = 0;
@@ -462,6 +493,8 @@ struct Engine {
     int64_t *pscan = nullptr; size_t c_pscan = 0;
     uint8_t *scratch = nullptr; size_t c_scratch = 0;
     int64_t *inst_i64 = nullptr; size_t c_inst_i64 = 0;
+    int64_t *kept_i64 = nullptr; size_t c_kept_i64 = 0;
+    bool prune_pending = false;
     int32_t *inst_i32 = nullptr; size_t c_inst_i32 = 0;
     SplitInst *d_split = nullptr; size_t c_split = 0;
     // small control block: [0..2] sizes, [3] bar, [4] err, [5] rounds, [6] rq count, [7] edge err, [8..9] scanned
@@ -487,6 +520,7 @@ struct Engine {
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         st = (cudaStream_t)stream;
         mem.st = st;
+        mem.pool = library_pool(dev);
         mem.limit = opt.max_device_bytes;
         timer.on = opt.timing != 0;
         timer.st = st;
@@ -719,12 +753,16 @@ struct Engine {
     // ---- one level --------------------------------------------------------
     void number(const std::vector<int> &ids)
     {
+        // problems ordered by dimension, so that the cells of each dimension
+        // take one contiguous run of slots
         step = ids;
+        std::stable_sort(step.begin(), step.end(),
+                         [&](int a, int b) { return inst[a]->dyn.n < inst[b]->dyn.n; });
         rng_used = 0;
         NL = 0;
         P = 0;
-        for (size_t j = 0; j < ids.size(); j++) inst[ids[j]]->tix = (int)j;
-        for (int i : ids) {
+        for (size_t j = 0; j < step.size(); j++) inst[step[j]]->tix = (int)j;
+        for (int i : step) {
             Inst &I = *inst[i];
             I.slot_base = NL;
             I.pair_base = P;
@@ -740,6 +778,7 @@ struct Engine {
     void build_graph(const std::vector<int> &ids)
     {
         LaunchScope ls_(cum);
+        finish_prune();
         number(ids);
         have_graph = have_prune = have_bnd = false;
         const size_t Ps = (size_t)std::max<int64_t>(P, 1), NLs = (size_t)std::max<int64_t>(NL, 1);
@@ -752,7 +791,8 @@ struct Engine {
         WorkList ws = make_work(slot_ranges(ids), 256);
         mem.ensure(cps, c_cps, NLs);
         mem.ensure(cinfo, c_cinfo, NLs);
-        CK(launch_cgather(d_desc, ws, cps, cinfo, st));
+        mem.ensure(cinst, c_cinst, NLs);
+        CK(launch_cgather(d_desc, ws, cps, cinfo, cinst, st));
         timer.end();
 
         // propagation of new cells, grouped by (dynamics, n, precision, lanes)
@@ -792,14 +832,12 @@ struct Engine {
             CK(launch_bin(n, d_desc, make_work(pair_ranges(sub), 256), rng, pflag, rq, ctl + 6, (int64_t)Ps, st));
         }
         timer.end();
-        // the FP64 recheck needs the number of flagged pairs for its buffers
-        int32_t hq0 = 0;
-        CK(cudaMemcpyAsync(&hq0, ctl + 6, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        sync();
-        last_recheck = hq0;
-        if (hq0 > 0) {
-            timer.begin(PH_RECHECK);
+        // FP64 recheck of the flagged extremes. Buffers are sized for every FP32
+        // pair being flagged (no read-back of the flagged count) unless that
+        // bound is large; then the flagged count is read first.
+        {
             int Smax = 1;
+            int64_t P32 = 0;
             std::map<std::pair<int, int>, int> kinds;
             std::map<int, int> dims;
             for (int i : ids)
@@ -807,18 +845,29 @@ struct Engine {
                     kinds[{inst[i]->dyn.dyn_id, inst[i]->dyn.n}] = 1;
                     dims[inst[i]->dyn.n] = 1;
                     Smax = std::max(Smax, inst[i]->S);
+                    P32 += inst[i]->n_live * inst[i]->nu;
                 }
-            mem.ensure(rc_mnk, c_rc_mnk, (size_t)hq0 * MAXN);
-            mem.ensure(rc_mxk, c_rc_mxk, (size_t)hq0 * MAXN);
-            mem.ensure(rc_bad, c_rc_bad, (size_t)hq0);
-            mem.ensure(rc_cand, c_rc_cand, (size_t)hq0 * Smax);
-            CK(cudaMemsetAsync(ctl + 10, 0, sizeof(int32_t), st));
-            RecheckArgs ra{d_desc, rq, ctl + 6, (int64_t)Ps, rc_mnk, rc_mxk, rc_bad, rc_cand, ctl + 10,
-                           (int64_t)hq0 * Smax, rng, pflag};
-            for (auto &k : kinds) CK(launch_recheck(0, k.first.first, k.first.second, ra, st));
-            for (auto &k : kinds) CK(launch_recheck(1, k.first.first, k.first.second, ra, st));
-            for (auto &d : dims) CK(launch_recheck(2, 0, d.first, ra, st));
-            timer.end();
+            int64_t nq = P32;
+            if (P32 > 0 && (double)P32 * Smax * sizeof(int2) > (double)(256 << 20)) {
+                int32_t hq0 = 0;
+                CK(cudaMemcpyAsync(&hq0, ctl + 6, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+                sync();
+                nq = hq0;
+            }
+            if (nq > 0) {
+                timer.begin(PH_RECHECK);
+                mem.ensure(rc_mnk, c_rc_mnk, (size_t)nq * MAXN);
+                mem.ensure(rc_mxk, c_rc_mxk, (size_t)nq * MAXN);
+                mem.ensure(rc_bad, c_rc_bad, (size_t)nq);
+                mem.ensure(rc_cand, c_rc_cand, (size_t)nq * Smax);
+                CK(cudaMemsetAsync(ctl + 10, 0, sizeof(int32_t), st));
+                RecheckArgs ra{d_desc, rq, ctl + 6, nq, rc_mnk, rc_mxk, rc_bad, rc_cand, ctl + 10,
+                               nq * Smax, rng, pflag};
+                for (auto &k : kinds) CK(launch_recheck(0, k.first.first, k.first.second, ra, st));
+                for (auto &k : kinds) CK(launch_recheck(1, k.first.first, k.first.second, ra, st));
+                for (auto &d : dims) CK(launch_recheck(2, 0, d.first, ra, st));
+                timer.end();
+            }
         }
 
         // count the cell graph, scan edges and in-degrees, fill edges and
@@ -834,11 +883,22 @@ struct Engine {
         CellGraph g{rng, pflag, pcnt, ccnt, rcnt, coff, nullptr, nullptr, (unsigned long long *)rcur, nullptr,
                     nullptr, (unsigned long long *)(ctl + 12), ctl + 7};
         timer.begin(PH_COUNT);
-        for (int n = 1; n <= MAXN; n++) {
-            auto sub = with_n(ids, n);
-            if (sub.empty()) continue;
-            CK(launch_cedges(false, n, d_desc, make_work(slot_ranges(sub), cedges_cells_per_block()), g, st));
-        }
+        // work chunks of the cells' union boxes; cells of one dimension are
+        // contiguous (number() orders the problems by dimension)
+        mem.ensure(cnch, c_cnch, NLs);
+        mem.ensure(cbase, c_cbase, NLs + 1);
+        const int Wmax = cedges_max_warps(dev);
+        mem.ensure(wpart, c_wpart, (size_t)MAXN * Wmax);
+        CK(launch_cchunks(d_desc, NL, cinst, rng, pflag, cnch, st));
+        CK(launch_scan_i32(cnch, cbase, NL, scratch, st));
+        CK(cudaMemsetAsync(ccnt, 0, NLs * sizeof(int32_t), st));
+        CK(cudaMemsetAsync(pcnt, 0, Ps * sizeof(int32_t), st));
+        int64_t seg_base[MAXN + 2] = {0};
+        for (int i : ids) seg_base[inst[i]->dyn.n + 1] += inst[i]->n_live;
+        for (int n = 1; n <= MAXN; n++) seg_base[n + 1] += seg_base[n];
+        for (int n = 1; n <= MAXN; n++)
+            CK(launch_cedges(false, n, d_desc, seg_base[n], seg_base[n + 1], cbase, cinst, g,
+                             wpart + (size_t)(n - 1) * Wmax, st));
         timer.end();
         timer.begin(PH_SCAN);
         CK(launch_scan_i32(ccnt, coff, NL, scratch, st));
@@ -849,6 +909,7 @@ struct Engine {
         CK(cudaMemcpyAsync(&hEc, coff + NL, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(hq, ctl + 6, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         sync();
+        last_recheck = hq[0];
         if (last_recheck > 0) cum.cum_recheck_samples += hq[4];
         if (hq[1] != 0) throw Error{GIS_EBOUNDS, "subdivision tree descent overflow"};
         unsigned long long hpe = 0;
@@ -865,11 +926,9 @@ struct Engine {
         g.rmask = rmask;
         timer.begin(PH_FILL);
         CK(cudaMemcpyAsync(rcur, roff, NLs * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
-        for (int n = 1; n <= MAXN; n++) {
-            auto sub = with_n(ids, n);
-            if (sub.empty()) continue;
-            CK(launch_cedges(true, n, d_desc, make_work(slot_ranges(sub), cedges_cells_per_block()), g, st));
-        }
+        for (int n = 1; n <= MAXN; n++)
+            CK(launch_cedges(true, n, d_desc, seg_base[n], seg_base[n + 1], cbase, cinst, g,
+                             wpart + (size_t)(n - 1) * Wmax, st));
         timer.end();
 
         for (int i : ids) inst[i]->cells_built += inst[i]->n_live;
@@ -898,7 +957,9 @@ struct Engine {
         have_graph = true;
     }
 
-    void prune()
+    // sync_now = false leaves the read-back of the counts to the next
+    // subdivide (or finish_prune), saving a host round trip per level
+    void prune(bool sync_now = true)
     {
         LaunchScope ls_(cum);
         if (!have_graph) throw Error{GIS_ESTATE, "prune needs a graph"};
@@ -933,14 +994,24 @@ struct Engine {
         a.spin_limit = (int64_t)1 << 25;
         if (NL > 0) CK(launch_cprune(a, NL, st));
         timer.end();
-        mem.ensure(inst_i64, c_inst_i64, step.size() + 1);
-        CK(cudaMemsetAsync(inst_i64, 0, step.size() * sizeof(int64_t), st));
-        CK(launch_count_kept(ws, alive, inst_i64, st));
+        mem.ensure(kept_i64, c_kept_i64, step.size() + 1);
+        CK(cudaMemsetAsync(kept_i64, 0, step.size() * sizeof(int64_t), st));
+        CK(launch_count_kept(ws, alive, kept_i64, st));
+        prune_pending = true;
+        have_prune = true;
+        if (sync_now) finish_prune();
+    }
+
+    // read the prune's counts back (after a stream sync)
+    void finish_prune()
+    {
+        if (!prune_pending) return;
         int32_t hc[10];
         std::vector<int64_t> kept(step.size());
         CK(cudaMemcpyAsync(hc, ctl, 10 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(kept.data(), inst_i64, step.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(kept.data(), kept_i64, step.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         sync();
+        prune_pending = false;
         if (hc[4] != 0) throw Error{(gis_status)hc[4], "prune: round or wait limit reached"};
         last_rounds = hc[5];
         unsigned long long scanned = 0;
@@ -955,7 +1026,6 @@ struct Engine {
         // per removed cell its reverse offsets and frontier slots (24); per reverse
         // edge walked its source, mask, info byte and the mask update (17)
         cum.prune_bytes += (double)P * 9 + (double)NL * 5 + 24.0 * dead + 17.0 * (double)scanned;
-        have_prune = true;
     }
 
     // classify + split for instances in `cont` (a subset of the current step)
@@ -995,6 +1065,7 @@ struct Engine {
         CK(cudaMemcpyAsync(d_be, be.data(), be.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
         CK(launch_inst_totals(pscan, d_be, (int)cont.size(), d_tot, st));
         timer.end();
+        finish_prune();
         std::vector<int64_t> tot(cont.size());
         std::vector<int32_t> maxl(step.size());
         if (!cont.empty())

@@ -100,9 +100,17 @@ struct CellGraph {
     unsigned long long *pair_edges;  // total (cell, control) -> cell edges
     int32_t *err;
 };
-cudaError_t launch_cgather(const InstDesc *D, const WorkList &wslots, int32_t *cps, uint8_t *cinfo, cudaStream_t st);
-cudaError_t launch_cedges(bool fill, int n, const InstDesc *D, const WorkList &w, const CellGraph &g, cudaStream_t st);
-int cedges_cells_per_block();
+cudaError_t launch_cgather(const InstDesc *D, const WorkList &wslots, int32_t *cps, uint8_t *cinfo, int32_t *cinst,
+                           cudaStream_t st);
+// per cell the chunk count of its union box (the work unit of the edge kernels)
+cudaError_t launch_cchunks(const InstDesc *D, int64_t NL, const int32_t *cinst, const int32_t *rng,
+                           const uint8_t *pflag, int32_t *nch, cudaStream_t st);
+// edges of the cells c0 <= s < c1, all of dimension n; cbase = exclusive scan
+// of the chunk counts; wpart holds cedges_max_warps() words, written by the
+// count pass and read by the fill pass of the same cells
+cudaError_t launch_cedges(bool fill, int n, const InstDesc *D, int64_t c0, int64_t c1, const int64_t *cbase,
+                          const int32_t *cinst, const CellGraph &g, int32_t *wpart, cudaStream_t st);
+int cedges_max_warps(int dev);
 cudaError_t launch_cprune_init(const InstDesc *D, const WorkList &wslots, const uint8_t *pflag, const int32_t *pcnt,
                                int32_t *pc, uint32_t *vmask, uint8_t *alive, int32_t *frontier0, uint32_t *sizes,
                                cudaStream_t st);
