@@ -137,7 +137,7 @@ typedef struct {
     int64_t n_kept;         /* kept by the last prune                             */
     int64_t n_split;        /* split by the last subdivision                      */
     int64_t n_new_pairs;    /* pairs propagated by the last build                 */
-    int64_t n_recheck;      /* pairs with an FP64 recheck at the last build        */
+    int64_t n_recheck;      /* pairs rechecked at the last build                  */
     int32_t prune_rounds;   /* frontier rounds of the last prune                  */
     int32_t lanes_per_pair; /* propagation shape in use                           */
     /* cumulative over the context lifetime */
@@ -153,11 +153,13 @@ typedef struct {
     double prune_bytes;     /* algorithmic bytes of the prune                      */
     double count_bytes, fill_bytes, transpose_bytes; /* the parts of graph_bytes   */
     int64_t cum_launches;   /* kernel launches issued by the library              */
-    int64_t cum_recheck_samples; /* samples recomputed in FP64 by the recheck      */
+    int64_t cum_recheck_samples; /* samples recomputed by the recheck (double-word
+                                    enclosure, FP64 where that leaves a grid line) */
     int64_t n_cell_edges;   /* edges B_i -> B_j of the current symbolic image (Def. 1:
                                the union over the controls); n_edges counts the
                                (cell, control) -> cell edges                       */
     int64_t cum_cell_edges;
+    int64_t cum_recheck_fp64; /* rechecked pairs that needed FP64 samples          */
 } gis_stats;
 
 typedef struct gis_ctx gis_ctx;
@@ -202,8 +204,9 @@ gis_status gis_get_graph(gis_ctx *ctx, int64_t *off, int32_t *tgt, uint8_t *flag
 
 /* Image boxes of the current pairs: box32 [n_pairs x 2n] FP32 extremes
  * (ymin_0..ymin_{n-1}, ymax_0..; the midpoint of each certified interval),
- * box64 the same in FP64 where `exact` has the extreme's bit set (bit e for
- * extreme e), else the FP32 value widened.
+ * box64 the same in FP64: the FP64 extreme itself where `exact` has the
+ * extreme's bit set (bit e for extreme e), else the midpoint of the tightest
+ * enclosure known (double-word or FP32).
  * Any output may be NULL. For testing and calibration.                       */
 gis_status gis_get_boxes(gis_ctx *ctx, float *box32, double *box64, uint8_t *exact, int64_t cap_pairs);
 

@@ -67,6 +67,14 @@ struct InstDesc {
     const float *u32;           // nu x m controls
     const float *ur32;          // their radii
     const double *u64;
+    // ---- the FP64 constants as double words {h, l, r}: |v - (h + l)| <= r ----
+    float pdd[GIS_NPARAM][3];   // p64
+    float hdd[3][3];            // h64, hh64, h6_64
+    float lodd[MAXN][3];
+    float wdd[MAXL + 1][MAXN][3];
+    float fdd[MAXK][3];         // frac64
+    const float *udd;           // u64, nu x m x 3
+    int32_t dd_ok;              // every constant has a finite double word
     // ---- subdivision tree ----
     uint8_t *lvl, *state;
     int32_t *idx[MAXN];
@@ -76,7 +84,9 @@ struct InstDesc {
     // ---- image-box cache, indexed node * nu + u ----
     float *box32;               // [.. x 2n x 2]: per extreme e (ymin_0..ymin_{n-1}, ymax_0..)
                                 // a certified interval [lo, hi] that holds its exact value
-    double *box64;
+    double *box64;              // [.. x 2n x 2]: an interval [lo, hi] that holds the FP64
+                                // value of extreme e where bit e of `exact` is set (lo == hi:
+                                // the FP64 value itself)
     uint16_t *exact;
 };
 

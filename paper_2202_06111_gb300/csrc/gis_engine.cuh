@@ -225,8 +225,9 @@ struct Inst {
     float *box32 = nullptr;
     double *box64 = nullptr;
     uint16_t *exact = nullptr;
-    float *u32 = nullptr, *ur32 = nullptr;
+    float *u32 = nullptr, *ur32 = nullptr, *udd = nullptr;
     double *u64 = nullptr;
+    bool udd_ok = true;
     InstDesc desc{};
 };
 
@@ -359,6 +360,27 @@ inline float radius_of(double v, float f)
     return rf;
 }
 
+// Double word {h, l, r} of an FP64 constant: h + l within r of v; false if v
+// is out of FP32 range.
+inline bool dword_of(double v, float *o)
+{
+    const float h = (float)v;
+    if (!std::isfinite(h)) {
+        o[0] = o[1] = 0.0f;
+        o[2] = INFINITY;
+        return false;
+    }
+    const long double r1 = (long double)v - (long double)h;
+    const float l = (float)r1;
+    const long double r2 = std::fabs(r1 - (long double)l);
+    float r = (float)r2;
+    if ((long double)r < r2) r = std::nextafter(r, INFINITY);
+    o[0] = h;
+    o[1] = l;
+    o[2] = r;
+    return true;
+}
+
 inline void fill_desc(Inst &I)
 {
     InstDesc &D = I.desc;
@@ -422,6 +444,18 @@ inline void fill_desc(Inst &I)
     D.u32 = I.u32;
     D.ur32 = I.ur32;
     D.u64 = I.u64;
+    bool ok = I.udd_ok;
+    for (int i = 0; i < GIS_NPARAM; i++) ok &= dword_of(D.p64[i], D.pdd[i]);
+    ok &= dword_of(D.h64, D.hdd[0]);
+    ok &= dword_of(D.hh64, D.hdd[1]);
+    ok &= dword_of(D.h6_64, D.hdd[2]);
+    for (int d = 0; d < MAXN; d++) {
+        ok &= dword_of(D.lo[d], D.lodd[d]);
+        for (int L = 0; L <= MAXL; L++) ok &= dword_of(D.w64[L][d], D.wdd[L][d]);
+    }
+    for (int j = 0; j < MAXK; j++) ok &= dword_of(D.frac64[j], D.fdd[j]);
+    D.udd = I.udd;
+    D.dd_ok = ok ? 1 : 0;
     D.lvl = I.lvl;
     D.state = I.state;
     for (int d = 0; d < MAXN; d++) D.idx[d] = I.idx[d];
@@ -478,8 +512,11 @@ struct Engine {
     int32_t *tgt = nullptr; size_t c_tgt = 0;
     int2 *rq = nullptr; size_t c_rq = 0;
     long long *rc_mnk = nullptr, *rc_mxk = nullptr; size_t c_rc_mnk = 0, c_rc_mxk = 0;
+    long long *rc_ddk = nullptr; size_t c_rc_ddk = 0;
+    int32_t *rc_need64 = nullptr; size_t c_rc_need64 = 0;
     int32_t *rc_bad = nullptr; size_t c_rc_bad = 0;
     int2 *rc_cand = nullptr; size_t c_rc_cand = 0;
+    int2 *rc_cand64 = nullptr; size_t c_rc_cand64 = 0;
     int32_t *rcnt = nullptr; size_t c_rcnt = 0;
     int64_t *roff = nullptr; size_t c_roff = 0;
     int64_t *rcur = nullptr; size_t c_rcur = 0;
@@ -558,7 +595,7 @@ struct Engine {
             mem.grow(I->live[0], I->cap_live[0], R, 0);
             mem.grow(I->box32, I->cap_pairs, (size_t)R * I->nu * 4 * dyn.n, 0);
             size_t c64 = 0, cex = 0;
-            mem.grow(I->box64, c64, (size_t)R * I->nu * 2 * dyn.n, 0);
+            mem.grow(I->box64, c64, (size_t)R * I->nu * 4 * dyn.n, 0);
             mem.grow(I->exact, cex, (size_t)R * I->nu, 0);
             I->cap_pairs = (size_t)R * I->nu;
             std::vector<float> u32(I->u.begin(), I->u.end()), ur32(I->u.size());
@@ -566,6 +603,10 @@ struct Engine {
             I->u32 = (float *)mem.alloc(u32.size() * sizeof(float));
             I->ur32 = (float *)mem.alloc(ur32.size() * sizeof(float));
             I->u64 = (double *)mem.alloc(I->u.size() * sizeof(double));
+            std::vector<float> udd(I->u.size() * 3);
+            for (size_t j = 0; j < I->u.size(); j++) I->udd_ok &= dword_of(I->u[j], &udd[3 * j]);
+            I->udd = (float *)mem.alloc(udd.size() * sizeof(float));
+            CK(cudaMemcpyAsync(I->udd, udd.data(), udd.size() * sizeof(float), cudaMemcpyHostToDevice, st));
             CK(cudaMemcpyAsync(I->u32, u32.data(), u32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
             CK(cudaMemcpyAsync(I->ur32, ur32.data(), ur32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
             CK(cudaMemcpyAsync(I->u64, I->u.data(), I->u.size() * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -603,9 +644,9 @@ struct Engine {
             alloc_nodes(I, target);
             const size_t n2 = (size_t)2 * I.dyn.n;
             const size_t keep = (size_t)I.n_nodes * I.nu;
-            size_t c32 = I.cap_pairs * 2 * n2, c64 = I.cap_pairs * n2, cex = I.cap_pairs;
+            size_t c32 = I.cap_pairs * 2 * n2, c64 = I.cap_pairs * 2 * n2, cex = I.cap_pairs;
             mem.grow(I.box32, c32, I.cap_nodes * I.nu * 2 * n2, keep * 2 * n2);
-            mem.grow(I.box64, c64, I.cap_nodes * I.nu * n2, keep * n2);
+            mem.grow(I.box64, c64, I.cap_nodes * I.nu * 2 * n2, keep * 2 * n2);
             mem.grow(I.exact, cex, I.cap_nodes * I.nu, keep);
             I.cap_pairs = I.cap_nodes * I.nu;
         }
@@ -621,11 +662,11 @@ struct Engine {
         for (int d = 0; d < MAXN; d++) { mem.free(I.idx[d]); I.idx[d] = nullptr; }
         mem.free(I.live[0]); mem.free(I.live[1]);
         mem.free(I.box32); mem.free(I.box64); mem.free(I.exact);
-        mem.free(I.u32); mem.free(I.ur32); mem.free(I.u64);
+        mem.free(I.u32); mem.free(I.ur32); mem.free(I.u64); mem.free(I.udd);
         I.lvl = I.state = nullptr;
         I.child = I.slot = I.live[0] = I.live[1] = nullptr;
         I.box32 = nullptr; I.box64 = nullptr; I.exact = nullptr;
-        I.u32 = I.ur32 = nullptr; I.u64 = nullptr;
+        I.u32 = I.ur32 = I.udd = nullptr; I.u64 = nullptr;
         I.cap_nodes = I.cap_live[0] = I.cap_live[1] = I.cap_pairs = 0;
         I.active = false;
     }
@@ -859,13 +900,21 @@ struct Engine {
                 mem.ensure(rc_mnk, c_rc_mnk, (size_t)nq * MAXN);
                 mem.ensure(rc_mxk, c_rc_mxk, (size_t)nq * MAXN);
                 mem.ensure(rc_bad, c_rc_bad, (size_t)nq);
+                mem.ensure(rc_need64, c_rc_need64, (size_t)nq);
+                mem.ensure(rc_ddk, c_rc_ddk, (size_t)nq * MAXN * 4);
                 mem.ensure(rc_cand, c_rc_cand, (size_t)nq * Smax);
-                CK(cudaMemsetAsync(ctl + 10, 0, sizeof(int32_t), st));
-                RecheckArgs ra{d_desc, rq, ctl + 6, nq, rc_mnk, rc_mxk, rc_bad, rc_cand, ctl + 10,
-                               nq * Smax, rng, pflag};
-                for (auto &k : kinds) CK(launch_recheck(0, k.first.first, k.first.second, ra, st));
-                for (auto &k : kinds) CK(launch_recheck(1, k.first.first, k.first.second, ra, st));
-                for (auto &d : dims) CK(launch_recheck(2, 0, d.first, ra, st));
+                mem.ensure(rc_cand64, c_rc_cand64, (size_t)nq * Smax);
+                CK(cudaMemsetAsync(ctl + 10, 0, 2 * sizeof(int32_t), st));
+                CK(cudaMemsetAsync(ctl + 16, 0, sizeof(int32_t), st));
+                RecheckArgs ra{d_desc, rq, ctl + 6, nq, rc_mnk, rc_mxk, rc_ddk, rc_need64, ctl + 11, rc_bad,
+                               rc_cand, ctl + 10, nq * Smax, rc_cand64, ctl + 16, Smax, rng, pflag};
+                // candidates; double-word enclosures and their decisions; FP64 for the rest
+                for (auto &k : kinds) CK(launch_recheck(RC_CAND, k.first.first, k.first.second, ra, st));
+                for (auto &k : kinds) CK(launch_recheck(RC_DD, k.first.first, k.first.second, ra, st));
+                for (auto &d : dims) CK(launch_recheck(RC_MID, 0, d.first, ra, st));
+                CK(launch_recheck(RC_C64, 0, 0, ra, st));
+                for (auto &k : kinds) CK(launch_recheck(RC_FP64, k.first.first, k.first.second, ra, st));
+                for (auto &d : dims) CK(launch_recheck(RC_FINAL, 0, d.first, ra, st));
                 timer.end();
             }
         }
@@ -910,7 +959,10 @@ struct Engine {
         CK(cudaMemcpyAsync(hq, ctl + 6, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         sync();
         last_recheck = hq[0];
-        if (last_recheck > 0) cum.cum_recheck_samples += hq[4];
+        if (last_recheck > 0) {
+            cum.cum_recheck_samples += hq[4];
+            cum.cum_recheck_fp64 += hq[5];
+        }
         if (hq[1] != 0) throw Error{GIS_EBOUNDS, "subdivision tree descent overflow"};
         unsigned long long hpe = 0;
         std::memcpy(&hpe, hq + 6, sizeof(hpe));

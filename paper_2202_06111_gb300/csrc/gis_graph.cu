@@ -507,13 +507,20 @@ __global__ void __launch_bounds__(256) k_export_boxes(const InstDesc *__restrict
     const int u = (int)(lp - (int64_t)ls * I.nu);
     const int64_t q = (int64_t)I.live[ls] * I.nu + u;
     const uint16_t x = I.exact[q];
+    unsigned xb = 0;                                   // extremes whose FP64 value is known
     for (int e = 0; e < 2 * N; e++) {
         const float lo = I.box32[q * 4 * N + 2 * e], hi = I.box32[q * 4 * N + 2 * e + 1];
         const float f = 0.5f * lo + 0.5f * hi;
         if (b32) b32[lp * 2 * N + e] = f;
-        if (b64) b64[lp * 2 * N + e] = ((x >> e) & 1) ? I.box64[q * 2 * N + e] : (double)f;
+        double v = (double)f;
+        if ((x >> e) & 1) {
+            const double a = I.box64[q * 4 * N + 2 * e], b = I.box64[q * 4 * N + 2 * e + 1];
+            v = a == b ? a : 0.5 * a + 0.5 * b;
+            if (a == b) xb |= 1u << e;
+        }
+        if (b64) b64[lp * 2 * N + e] = v;
     }
-    if (ex) ex[lp] = (uint8_t)(x & 0xff);
+    if (ex) ex[lp] = (uint8_t)xb;
 }
 
 cudaError_t launch_export_boxes(int n, const InstDesc *D, const WorkList &w, float *b32, double *b64, uint8_t *ex,

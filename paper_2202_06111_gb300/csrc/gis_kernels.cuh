@@ -41,17 +41,25 @@ cudaError_t launch_bin(int n, const InstDesc *D, const WorkList &w, int32_t *rng
 // phase 1 FP64 samples (per dynamics kind), phase 2 finalize (per n).
 struct RecheckArgs {
     const InstDesc *D;
-    const int2 *items;           // (global pair, inst | mask << 16)
+    const int2 *items;           // (global pair, inst | mdd << 16 | m64 << 24)
     const int32_t *count;        // device count of items
     int64_t qcap;
-    long long *mnk, *mxk;        // [item x n] ordered keys of the FP64 extremes
+    long long *mnk, *mxk;        // [item x MAXN] ordered keys of the FP64 extremes
+    long long *ddk;              // [item x MAXN x 4] keys of the double-word enclosures
+    int32_t *need64;             // [item] the pair is computed in FP64
+    int32_t *n64;                // count of pairs computed in FP64
     int32_t *bad;                // [item] an FP64 sample was not finite
     int2 *cand;                  // (item, sample)
     int32_t *ncand;
     int64_t ccap;
+    int2 *cand64;                // the candidates of the pairs computed in FP64
+    int32_t *ncand64;
+    int smax;                    // largest sample count of the rechecked problems
     int32_t *rng;
     uint8_t *pflag;
 };
+// recheck phases, in launch order
+enum { RC_CAND = 0, RC_DD = 1, RC_MID = 2, RC_C64 = 3, RC_FP64 = 4, RC_FINAL = 5 };
 cudaError_t launch_recheck(int phase, int dyn, int n, const RecheckArgs &a, cudaStream_t st);
 // exclusive scan of n int32 (or int64) values into int64 out[n + 1]; scratch >= scan_scratch_bytes(n)
 size_t scan_scratch_bytes(int64_t n);

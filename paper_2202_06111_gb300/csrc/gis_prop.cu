@@ -8,10 +8,13 @@
 //  k_prop64   FP64 samples in the defining operation order (plain FP64 mode)
 //  k_bin      decisions at the finest level; an extreme whose interval may
 //             straddle a grid line goes to the recheck queue
-//  k_rc_*     FP64 recomputation of those extremes over the samples whose
-//             ball can reach the extreme (dense: one FP64 sample per lane)
+//  k_rc_*     recheck of those extremes over the samples whose ball can reach
+//             the extreme: first a double-word enclosure of each sample's
+//             FP64 image (k_rc_dd, one sample per thread), which settles
+//             nearly every decision; the rest in FP64 (k_rc_fp64)
 #include <cfloat>
 
+#include "gis_dd_models.cuh"
 #include "gis_kernels.cuh"
 
 namespace gis {
@@ -170,8 +173,8 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop64(const InstDesc *__restr
     const int64_t q = (int64_t)node * I.nu + u;
 #pragma unroll
     for (int d = 0; d < N; d++) {
-        I.box64[q * 2 * N + d] = mn[d];
-        I.box64[q * 2 * N + N + d] = mx[d];
+        I.box64[q * 4 * N + 2 * d] = I.box64[q * 4 * N + 2 * d + 1] = mn[d];
+        I.box64[q * 4 * N + 2 * (N + d)] = I.box64[q * 4 * N + 2 * (N + d) + 1] = mx[d];
         I.box32[q * 4 * N + 2 * d] = __double2float_rd(mn[d]);
         I.box32[q * 4 * N + 2 * d + 1] = __double2float_ru(mn[d]);
         I.box32[q * 4 * N + 2 * (N + d)] = __double2float_rd(mx[d]);
@@ -224,6 +227,28 @@ __device__ __forceinline__ bool decide_approx(const InstDesc &I, int e, float a,
     return true;
 }
 
+// Decision from an interval [a, b] that holds the FP64 value of an extreme:
+// the decision is monotone in the value, so equal decisions at both ends
+// settle it; false otherwise.
+template <int N>
+__device__ __forceinline__ bool decide_enc(const InstDesc &I, int e, double a, double b, int32_t &out, bool &inx)
+{
+    int32_t oa = 0, ob = 0;
+    bool ia = true, ib = true;
+    decide_exact<N>(I, e, a, oa, ia);
+    if (a != b) {
+        decide_exact<N>(I, e, b, ob, ib);
+        if (oa != ob || ia != ib) return false;
+    }
+    out = oa;
+    inx = inx && ia;
+    return true;
+}
+
+__device__ __forceinline__ int item_inst(int y) { return y & 0xFFFF; }
+__device__ __forceinline__ unsigned item_mdd(int y) { return ((unsigned)y >> 16) & 0xFFu; }
+__device__ __forceinline__ unsigned item_m64(int y) { return (unsigned)y >> 24; }
+
 template <int N>
 __global__ void __launch_bounds__(256) k_bin(const InstDesc *__restrict__ D, const Range *__restrict__ R, int nr,
                                              int32_t *__restrict__ rng, uint8_t *__restrict__ pflag,
@@ -249,22 +274,28 @@ __global__ void __launch_bounds__(256) k_bin(const InstDesc *__restrict__ D, con
         pflag[p] = PF_NONFINITE;
         return;
     }
-    unsigned mask = 0;
+    // mdd: extremes known only to FP32, to be enclosed in double words;
+    // m64: extremes whose FP64 enclosure holds a grid line, to be computed in FP64
+    unsigned mdd = 0, m64 = 0;
     int32_t out[2 * N];
     bool inx = true;
     if ((ex & EX_NF32) && (ex & FULL) != FULL) {
-        mask = FULL;
+        mdd = FULL;
     } else {
 #pragma unroll
         for (int e = 0; e < 2 * N; e++) {
-            if ((ex >> e) & 1) decide_exact<N>(I, e, I.box64[q * 2 * N + e], out[e], inx);
-            else if (!decide_approx<N>(I, e, I.box32[q * 4 * N + 2 * e], I.box32[q * 4 * N + 2 * e + 1], out[e], inx))
-                mask |= 1u << e;
+            if ((ex >> e) & 1) {
+                if (!decide_enc<N>(I, e, I.box64[q * 4 * N + 2 * e], I.box64[q * 4 * N + 2 * e + 1], out[e], inx))
+                    m64 |= 1u << e;
+            } else if (!decide_approx<N>(I, e, I.box32[q * 4 * N + 2 * e], I.box32[q * 4 * N + 2 * e + 1], out[e],
+                                         inx)) {
+                mdd |= 1u << e;
+            }
         }
     }
-    if (mask) {
+    if (mdd | m64) {
         int pos = atomicAdd(qcount, 1);
-        if (pos < qcap) qitems[pos] = make_int2((int)p, rg.inst | (int)(mask << 16));
+        if (pos < qcap) qitems[pos] = make_int2((int)p, rg.inst | (int)(mdd << 16) | (int)(m64 << 24));
         pflag[p] = PF_RECHECK;
         return;
     }
@@ -284,54 +315,72 @@ __device__ __forceinline__ double dkey_inv(long long k)
     return __longlong_as_double(k >= 0 ? k : k ^ 0x7fffffffffffffffll);
 }
 
-// Recheck, phase A: one warp per flagged pair recomputes its FP32 samples and
+// Recheck, phase A: a group of G lanes per flagged pair (G = the sample count
+// rounded up to a power of two, at most 32) recomputes its FP32 samples and
 // appends the candidates of the flagged extremes -- the samples whose FP32
 // image lies within the candidate window of the FP32 extreme -- or all samples
-// if some FP32 image was not finite. Also resets the pair's FP64 reductions.
-template <class DY, int DYN>
+// if some FP32 image was not finite. Also resets the pair's reductions, and
+// marks for FP64 the pairs with an FP64 enclosure that holds a grid line.
+template <class DY, int DYN, int G>
 __global__ void __launch_bounds__(256) k_rc_cand(const InstDesc *__restrict__ D, const int2 *__restrict__ items,
                                                  const int32_t *__restrict__ count, int64_t qcap,
                                                  long long *__restrict__ mnk, long long *__restrict__ mxk,
+                                                 long long *__restrict__ ddk, int32_t *__restrict__ need64,
                                                  int32_t *__restrict__ bad, int2 *__restrict__ cand,
                                                  int32_t *__restrict__ ncand)
 {
     constexpr int N = DY::N;
-    const int lane = threadIdx.x & 31;
+    constexpr int PER = 32 / G;                    // pairs per warp
+    const int lane = threadIdx.x & 31, gl = lane & (G - 1);
     const int nw = gridDim.x * (blockDim.x / 32);
     const int total = (int)min((int64_t)*count, qcap);
-    for (int it = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; it < total; it += nw) {
-        const int2 item = items[it];
-        const int inst = item.y & 0xFFFF;
-        const unsigned mask = (unsigned)item.y >> 16;
-        const InstDesc &I = D[inst];
-        if (I.dyn != DYN || I.n != N) continue;
-        const int64_t lp = (int64_t)item.x - I.pair_base;
-        const int ls = (int)(lp / I.nu);
-        const int u = (int)(lp - (int64_t)ls * I.nu);
-        const int node = I.live[ls];
-        const int L = I.lvl[node];
-        const int64_t q = (int64_t)node * I.nu + u;
-        const bool all64 = (I.exact[q] & EX_NF32) != 0;
-        if (lane < N) {
-            mnk[(int64_t)it * MAXN + lane] = dkey(INFINITY);
-            mxk[(int64_t)it * MAXN + lane] = dkey(-INFINITY);
+    for (int base = (blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32) * PER; base < total; base += nw * PER) {
+        const int it = base + lane / G;
+        bool valid = it < total;
+        int2 item = make_int2(0, 0);
+        if (valid) {
+            item = items[it];
+            const InstDesc &J = D[item_inst(item.y)];
+            valid = J.dyn == DYN && J.n == N;
         }
-        if (lane == 0) bad[it] = 0;
+        const InstDesc &I = D[valid ? item_inst(item.y) : 0];
+        const unsigned mask = item_mdd(item.y) | item_m64(item.y);
+        int S = 0, L = 0, u = 0;
+        int64_t q = 0;
+        bool all64 = false;
         int32_t idx[N];
 #pragma unroll
-        for (int d = 0; d < N; d++) idx[d] = I.idx[d][node];
-        Ball uu[MAXN];
-        for (int j = 0; j < I.m; j++) uu[j] = Ball{I.u32[u * I.m + j], I.ur32[u * I.m + j]};
-        float lim[2 * N];                  // hi end of a min extreme, lo end of a max extreme
+        for (int d = 0; d < N; d++) idx[d] = 0;
+        if (valid) {
+            const int64_t lp = (int64_t)item.x - I.pair_base;
+            const int ls = (int)(lp / I.nu);
+            u = (int)(lp - (int64_t)ls * I.nu);
+            const int node = I.live[ls];
+            L = I.lvl[node];
+            q = (int64_t)node * I.nu + u;
+            all64 = (I.exact[q] & EX_NF32) != 0;
+            S = I.S;
 #pragma unroll
-        for (int e = 0; e < 2 * N; e++) lim[e] = I.box32[q * 4 * N + 2 * e + (e < N ? 1 : 0)];
-        const MB M{I.p32, I.pr32, I.m, I.substeps, {I.h32, I.hr32}, {I.hh32, I.hhr32}, {I.h6_32, I.h6r32}};
-        for (int s0 = 0; s0 < I.S; s0 += 32) {
-            const int s = s0 + lane;
+            for (int d = 0; d < N; d++) idx[d] = I.idx[d][node];
+            if (gl < N) {
+                mnk[(int64_t)it * MAXN + gl] = dkey(INFINITY);
+                mxk[(int64_t)it * MAXN + gl] = dkey(-INFINITY);
+            }
+            for (int j = gl; j < 4 * N; j += G) ddk[(int64_t)it * 4 * MAXN + j] = dkey((j & 3) < 2 ? INFINITY : -INFINITY);
+            if (gl == 0) {
+                bad[it] = 0;
+                need64[it] = item_m64(item.y) != 0;
+            }
+        }
+        for (int s0 = 0; __any_sync(0xffffffffu, s0 < S); s0 += G) {
+            const int s = s0 + gl;
             bool c = false;
-            if (s < I.S) {
+            if (s < S) {
                 c = all64;
                 if (!c) {
+                    Ball uu[MAXN];
+                    for (int j = 0; j < I.m; j++) uu[j] = Ball{I.u32[u * I.m + j], I.ur32[u * I.m + j]};
+                    const MB M{I.p32, I.pr32, I.m, I.substeps, {I.h32, I.hr32}, {I.hh32, I.hhr32}, {I.h6_32, I.h6r32}};
                     float fr[N], frr[N];
                     int r = s;
 #pragma unroll
@@ -346,10 +395,12 @@ __global__ void __launch_bounds__(256) k_rc_cand(const InstDesc *__restrict__ D,
 #pragma unroll
                     for (int e = 0; e < 2 * N; e++) {
                         if (!((mask >> e) & 1)) continue;
+                        // hi end of a min extreme, lo end of a max extreme
+                        const float lim = I.box32[q * 4 * N + 2 * e + (e < N ? 1 : 0)];
                         const Ball yb = bfinal(y[e % N]);
                         // the sample can hold the extreme unless its ball lies beyond the limit
-                        if (e < N) c |= !(__fsub_rd(yb.m, yb.r) > lim[e]);
-                        else c |= !(__fadd_ru(yb.m, yb.r) < lim[e]);
+                        if (e < N) c |= !(__fsub_rd(yb.m, yb.r) > lim);
+                        else c |= !(__fadd_ru(yb.m, yb.r) < lim);
                     }
                 }
             }
@@ -362,7 +413,144 @@ __global__ void __launch_bounds__(256) k_rc_cand(const InstDesc *__restrict__ D,
     }
 }
 
-// Recheck, phase B: one thread per candidate sample, in FP64 (every lane busy).
+// Recheck, phase B1: one thread per candidate sample of a pair with extremes
+// known only to FP32: a double-word enclosure [lo, hi] of the sample's FP64
+// image per dimension, reduced per pair into enclosures of the FP64 extremes
+// (min over samples of lo and of hi for a lower extreme, max for an upper one:
+// ddk[(item, d)] = {min lo, min hi, max lo, max hi}). A sample without a finite
+// enclosure sends its pair to FP64.
+template <class DY, int DYN>
+__global__ void __launch_bounds__(256) k_rc_dd(const InstDesc *__restrict__ D, const int2 *__restrict__ items,
+                                               const int2 *__restrict__ cand, const int32_t *__restrict__ ncand,
+                                               int64_t ccap, long long *__restrict__ ddk,
+                                               int32_t *__restrict__ need64)
+{
+    constexpr int N = DY::N;
+    const int total = (int)min((int64_t)*ncand, ccap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int2 c = cand[i];
+        const int2 item = items[c.x];
+        if (item_mdd(item.y) == 0) continue;
+        const InstDesc &I = D[item_inst(item.y)];
+        if (I.dyn != DYN || I.n != N) continue;
+        if (!I.dd_ok) {
+            need64[c.x] = 1;
+            continue;
+        }
+        const int64_t lp = (int64_t)item.x - I.pair_base;
+        const int ls = (int)(lp / I.nu);
+        const int u = (int)(lp - (int64_t)ls * I.nu);
+        const int node = I.live[ls];
+        const int L = I.lvl[node];
+        int32_t idx[N];
+#pragma unroll
+        for (int d = 0; d < N; d++) idx[d] = I.idx[d][node];
+        DB uu[MAXN];
+        for (int j = 0; j < I.m; j++) uu[j] = dbof(I.udd + 3 * (u * I.m + j));
+        DB x[N], y[N];
+        sampleD<N>(I, L, idx, c.y, x);
+        stepD<DY>(I, x, uu, y);
+        bool ok = true;
+#pragma unroll
+        for (int d = 0; d < N; d++) ok = ok && db_ok(y[d]);
+        if (!ok) {
+            need64[c.x] = 1;
+            continue;
+        }
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            const double m = (double)y[d].h + (double)y[d].l;     // exact
+            const long long klo = dkey(__dsub_rd(m, (double)y[d].r));
+            const long long khi = dkey(__dadd_ru(m, (double)y[d].r));
+            long long *k = ddk + ((int64_t)c.x * MAXN + d) * 4;
+            atomicMin(k + 0, klo);
+            atomicMin(k + 1, khi);
+            atomicMax(k + 2, klo);
+            atomicMax(k + 3, khi);
+        }
+    }
+}
+
+// Recheck, phase B2: per pair with extremes known only to FP32, store the
+// enclosures of those extremes and decide; a pair with an undecided extreme
+// goes on to FP64.
+template <int N>
+__global__ void __launch_bounds__(256) k_rc_mid(const InstDesc *__restrict__ D, const int2 *__restrict__ items,
+                                                const int32_t *__restrict__ count, int64_t qcap,
+                                                const long long *__restrict__ ddk, int32_t *__restrict__ need64,
+                                                int32_t *__restrict__ rng, uint8_t *__restrict__ pflag)
+{
+    constexpr unsigned FULL = (1u << (2 * N)) - 1u;
+    const int total = (int)min((int64_t)*count, qcap);
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+        const int2 item = items[it];
+        const unsigned mdd = item_mdd(item.y);
+        const InstDesc &I = D[item_inst(item.y)];
+        if (I.n != N || mdd == 0 || need64[it]) continue;
+        const int64_t p = item.x;
+        const int64_t lp = p - I.pair_base;
+        const int ls = (int)(lp / I.nu);
+        const int u = (int)(lp - (int64_t)ls * I.nu);
+        const int64_t q = (int64_t)I.live[ls] * I.nu + u;
+        unsigned ex = I.exact[q];
+#pragma unroll
+        for (int e = 0; e < 2 * N; e++) {
+            if (!((mdd >> e) & 1)) continue;
+            const long long *k = ddk + ((int64_t)it * MAXN + e % N) * 4 + (e < N ? 0 : 2);
+            I.box64[q * 4 * N + 2 * e] = dkey_inv(k[0]);
+            I.box64[q * 4 * N + 2 * e + 1] = dkey_inv(k[1]);
+            ex |= 1u << e;
+        }
+        I.exact[q] = (uint16_t)ex;
+        bool inx = true, done = true;
+        int32_t out[2 * N];
+#pragma unroll
+        for (int e = 0; e < 2 * N; e++) {
+            if ((ex >> e) & 1)
+                done = done && decide_enc<N>(I, e, I.box64[q * 4 * N + 2 * e], I.box64[q * 4 * N + 2 * e + 1], out[e], inx);
+            else
+                done = done && decide_approx<N>(I, e, I.box32[q * 4 * N + 2 * e], I.box32[q * 4 * N + 2 * e + 1], out[e], inx);
+        }
+        (void)FULL;
+        if (!done) {
+            need64[it] = 1;
+            continue;
+        }
+#pragma unroll
+        for (int e = 0; e < 2 * N; e++) rng[p * 2 * MAXN + e] = out[e];
+        pflag[p] = inx ? PF_INX : 0;
+    }
+}
+
+// Candidates of the pairs still undecided, compacted so that the FP64 phase
+// runs on full warps (an FP64 instruction costs its warp the same pipe time
+// however few lanes are active).
+__global__ void __launch_bounds__(256) k_rc_c64(const int2 *__restrict__ cand, const int32_t *__restrict__ ncand,
+                                                int64_t ccap, const int32_t *__restrict__ need64,
+                                                int2 *__restrict__ cand64, int32_t *__restrict__ ncand64)
+{
+    const int total = (int)min((int64_t)*ncand, ccap);
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < total; i0 += stride) {
+        const int i = i0 + lane;
+        int2 c = make_int2(0, 0);
+        bool take = false;
+        if (i < total) {
+            c = cand[i];
+            take = need64[c.x] != 0;
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, take);
+        if (!b) continue;
+        int pos = 0;
+        if (lane == 0) pos = atomicAdd(ncand64, __popc(b));
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if (take) cand64[pos + __popc(b & ((1u << lane) - 1u))] = c;
+    }
+}
+
+// Recheck, phase C1: one thread per candidate sample of a pair still undecided
+// (the compacted list), in FP64.
 template <class DY, int DYN>
 __global__ void __launch_bounds__(256) k_rc_fp64(const InstDesc *__restrict__ D, const int2 *__restrict__ items,
                                                  const int2 *__restrict__ cand, const int32_t *__restrict__ ncand,
@@ -374,7 +562,7 @@ __global__ void __launch_bounds__(256) k_rc_fp64(const InstDesc *__restrict__ D,
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         const int2 c = cand[i];
         const int2 item = items[c.x];
-        const InstDesc &I = D[item.y & 0xFFFF];
+        const InstDesc &I = D[item_inst(item.y)];
         if (I.dyn != DYN || I.n != N) continue;
         const int64_t lp = (int64_t)item.x - I.pair_base;
         const int ls = (int)(lp / I.nu);
@@ -402,22 +590,26 @@ __global__ void __launch_bounds__(256) k_rc_fp64(const InstDesc *__restrict__ D,
     }
 }
 
-// Recheck, phase C: exact extremes into the cache, decisions of the pair.
+// Recheck, phase C2: for the pairs computed in FP64, the FP64 extremes into the
+// cache and the decisions of the pair.
 template <int N>
 __global__ void __launch_bounds__(256) k_rc_final(const InstDesc *__restrict__ D, const int2 *__restrict__ items,
                                                   const int32_t *__restrict__ count, int64_t qcap,
                                                   const long long *__restrict__ mnk,
                                                   const long long *__restrict__ mxk,
+                                                  const int32_t *__restrict__ need64,
                                                   const int32_t *__restrict__ bad, int32_t *__restrict__ rng,
-                                                  uint8_t *__restrict__ pflag)
+                                                  uint8_t *__restrict__ pflag, int32_t *__restrict__ n64)
 {
     constexpr unsigned FULL = (1u << (2 * N)) - 1u;
     const int total = (int)min((int64_t)*count, qcap);
     for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+        if (!need64[it]) continue;
         const int2 item = items[it];
-        const unsigned mask = (unsigned)item.y >> 16;
-        const InstDesc &I = D[item.y & 0xFFFF];
+        const unsigned mask = item_mdd(item.y) | item_m64(item.y);
+        const InstDesc &I = D[item_inst(item.y)];
         if (I.n != N) continue;
+        atomicAdd(n64, 1);
         const int64_t p = item.x;
         const int64_t lp = p - I.pair_base;
         const int ls = (int)(lp / I.nu);
@@ -435,7 +627,8 @@ __global__ void __launch_bounds__(256) k_rc_final(const InstDesc *__restrict__ D
         for (int e = 0; e < 2 * N; e++) {
             if (!((upd >> e) & 1)) continue;
             const int d = e % N;
-            I.box64[q * 2 * N + e] = e < N ? dkey_inv(mnk[(int64_t)it * MAXN + d]) : dkey_inv(mxk[(int64_t)it * MAXN + d]);
+            const double v = e < N ? dkey_inv(mnk[(int64_t)it * MAXN + d]) : dkey_inv(mxk[(int64_t)it * MAXN + d]);
+            I.box64[q * 4 * N + 2 * e] = I.box64[q * 4 * N + 2 * e + 1] = v;
             ex |= 1u << e;
         }
         I.exact[q] = (uint16_t)ex;
@@ -443,8 +636,12 @@ __global__ void __launch_bounds__(256) k_rc_final(const InstDesc *__restrict__ D
         int32_t out[2 * N];
 #pragma unroll
         for (int e = 0; e < 2 * N; e++) {
-            if ((ex >> e) & 1) decide_exact<N>(I, e, I.box64[q * 2 * N + e], out[e], inx);
-            else decide_approx<N>(I, e, I.box32[q * 4 * N + 2 * e], I.box32[q * 4 * N + 2 * e + 1], out[e], inx);
+            // every extreme is decided: those in `upd` hold their FP64 value, the
+            // others were decided before (FP32 or an enclosure)
+            if ((ex >> e) & 1)
+                decide_enc<N>(I, e, I.box64[q * 4 * N + 2 * e], I.box64[q * 4 * N + 2 * e + 1], out[e], inx);
+            else
+                decide_approx<N>(I, e, I.box32[q * 4 * N + 2 * e], I.box32[q * 4 * N + 2 * e + 1], out[e], inx);
         }
 #pragma unroll
         for (int e = 0; e < 2 * N; e++) rng[p * 2 * MAXN + e] = out[e];
@@ -544,26 +741,56 @@ template <class DY, int DYN>
 static cudaError_t recheck_l(int phase, const RecheckArgs &a, cudaStream_t st)
 {
     const int g = sm_count() * 8;
-    if (phase == 0) {
-        k_rc_cand<DY, DYN><<<g, 256, 0, st>>>(a.D, a.items, a.count, a.qcap, a.mnk, a.mxk, a.bad, a.cand, a.ncand); note_launch();
+    if (phase == RC_CAND) {
+        if (a.smax <= 8)
+            k_rc_cand<DY, DYN, 8><<<g, 256, 0, st>>>(a.D, a.items, a.count, a.qcap, a.mnk, a.mxk, a.ddk, a.need64,
+                                                     a.bad, a.cand, a.ncand);
+        else if (a.smax <= 16)
+            k_rc_cand<DY, DYN, 16><<<g, 256, 0, st>>>(a.D, a.items, a.count, a.qcap, a.mnk, a.mxk, a.ddk, a.need64,
+                                                      a.bad, a.cand, a.ncand);
+        else
+            k_rc_cand<DY, DYN, 32><<<g, 256, 0, st>>>(a.D, a.items, a.count, a.qcap, a.mnk, a.mxk, a.ddk, a.need64,
+                                                      a.bad, a.cand, a.ncand);
+        note_launch();
+    } else if (phase == RC_DD) {
+        k_rc_dd<DY, DYN><<<g, 256, 0, st>>>(a.D, a.items, a.cand, a.ncand, a.ccap, a.ddk, a.need64); note_launch();
+    } else if (phase == RC_FP64) {
+        k_rc_fp64<DY, DYN><<<g, 256, 0, st>>>(a.D, a.items, a.cand64, a.ncand64, a.ccap, a.mnk, a.mxk, a.bad);
+        note_launch();
     } else {
-        k_rc_fp64<DY, DYN><<<g, 256, 0, st>>>(a.D, a.items, a.cand, a.ncand, a.ccap, a.mnk, a.mxk, a.bad); note_launch();
+        return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t recheck_n(int phase, const RecheckArgs &a, cudaStream_t st)
+{
+    const int g = sm_count() * 8;
+    if (phase == RC_MID)
+        k_rc_mid<N><<<g, 256, 0, st>>>(a.D, a.items, a.count, a.qcap, a.ddk, a.need64, a.rng, a.pflag);
+    else
+        k_rc_final<N><<<g, 256, 0, st>>>(a.D, a.items, a.count, a.qcap, a.mnk, a.mxk, a.need64, a.bad, a.rng,
+                                         a.pflag, a.n64);
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_recheck(int phase, int dyn, int n, const RecheckArgs &a, cudaStream_t st)
 {
-    if (phase == 2) {
-        const int g = sm_count() * 8;
+    if (phase == RC_C64) {
+        k_rc_c64<<<sm_count() * 8, 256, 0, st>>>(a.cand, a.ncand, a.ccap, a.need64, a.cand64, a.ncand64);
+        note_launch();
+        return cudaGetLastError();
+    }
+    if (phase == RC_MID || phase == RC_FINAL) {
         switch (n) {
-        case 1: k_rc_final<1><<<g, 256, 0, st>>>(a.D, a.items, a.count, a.qcap, a.mnk, a.mxk, a.bad, a.rng, a.pflag); note_launch(); break;
-        case 2: k_rc_final<2><<<g, 256, 0, st>>>(a.D, a.items, a.count, a.qcap, a.mnk, a.mxk, a.bad, a.rng, a.pflag); note_launch(); break;
-        case 3: k_rc_final<3><<<g, 256, 0, st>>>(a.D, a.items, a.count, a.qcap, a.mnk, a.mxk, a.bad, a.rng, a.pflag); note_launch(); break;
-        case 4: k_rc_final<4><<<g, 256, 0, st>>>(a.D, a.items, a.count, a.qcap, a.mnk, a.mxk, a.bad, a.rng, a.pflag); note_launch(); break;
+        case 1: return recheck_n<1>(phase, a, st);
+        case 2: return recheck_n<2>(phase, a, st);
+        case 3: return recheck_n<3>(phase, a, st);
+        case 4: return recheck_n<4>(phase, a, st);
         default: return cudaErrorInvalidValue;
         }
-        return cudaGetLastError();
     }
     switch (dyn) {
     case GIS_DYN_VDP: return recheck_l<DynVdp, GIS_DYN_VDP>(phase, a, st);

@@ -70,7 +70,8 @@ _STAT_FIELDS = [("finest_level", C.c_int32), ("level", C.c_int32), ("n_nodes", C
                 ("ms_split", C.c_double), ("ms_other", C.c_double), ("prop_flops", C.c_double),
                 ("graph_bytes", C.c_double), ("prune_bytes", C.c_double), ("count_bytes", C.c_double),
                 ("fill_bytes", C.c_double), ("transpose_bytes", C.c_double), ("cum_launches", C.c_int64),
-                ("cum_recheck_samples", C.c_int64), ("n_cell_edges", C.c_int64), ("cum_cell_edges", C.c_int64)]
+                ("cum_recheck_samples", C.c_int64), ("n_cell_edges", C.c_int64), ("cum_cell_edges", C.c_int64),
+                ("cum_recheck_fp64", C.c_int64)]
 
 
 class gis_stats(C.Structure):
