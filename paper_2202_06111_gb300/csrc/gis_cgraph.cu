@@ -30,28 +30,33 @@ namespace gis {
     const Range rg = R[s_r];                                                  \
     const InstDesc &I = D[rg.inst];
 
-// Global slot of every live node; per cell the index of its first pair and
-// its control count / rule (cinfo = n_controls | rule << 6).
+// Global slot of every live node; per cell the index of its first pair, its
+// control count / rule (cinfo = n_controls | rule << 6), its problem, its node
+// and the slot the node had at the previous level (meaningful for carried cells).
 __global__ void __launch_bounds__(256) k_cgather(const InstDesc *__restrict__ D, const Range *__restrict__ R, int nr,
                                                  int32_t *__restrict__ cps, uint8_t *__restrict__ cinfo,
-                                                 int32_t *__restrict__ cinst)
+                                                 int32_t *__restrict__ cinst, int32_t *__restrict__ s2n,
+                                                 int32_t *__restrict__ oslot)
 {
     CRANGE_HEAD(256)
     const int64_t local = (int64_t)(blockIdx.x - rg.block_start) * 256 + threadIdx.x;
     if (local >= rg.count) return;
     const int64_t s = rg.first + local;
     const int ls = (int)(s - I.slot_base);
-    I.slot[I.live[ls]] = (int32_t)s;
+    const int node = I.live[ls];
+    if (ls < I.n_carry) oslot[s] = I.slot[node];
+    I.slot[node] = (int32_t)s;
     cps[s] = (int32_t)(I.pair_base + (int64_t)ls * I.nu);
     cinfo[s] = (uint8_t)(I.nu | (I.rule << 6));
     cinst[s] = rg.inst;
+    s2n[s] = node;
 }
 
 cudaError_t launch_cgather(const InstDesc *D, const WorkList &w, int32_t *cps, uint8_t *cinfo, int32_t *cinst,
-                           cudaStream_t st)
+                           int32_t *s2n, int32_t *oslot, cudaStream_t st)
 {
     if (w.n_blocks == 0) return cudaSuccess;
-    k_cgather<<<(unsigned)w.n_blocks, 256, 0, st>>>(D, w.d_ranges, w.n_ranges, cps, cinfo, cinst);
+    k_cgather<<<(unsigned)w.n_blocks, 256, 0, st>>>(D, w.d_ranges, w.n_ranges, cps, cinfo, cinst, s2n, oslot);
     note_launch();
     return cudaGetLastError();
 }
@@ -76,44 +81,50 @@ __device__ __forceinline__ int warp_max(int v)
 // boxes), so that the few cells whose images reach far across X are shared by
 // many warps instead of trailing behind all the others. A cell has
 // max(1, ceil(roots / CE_CHUNK)) chunks; the exclusive scan of these counts
-// numbers the chunks of a run of cells contiguously.
+// numbers the chunks of a run of cells contiguously. Cells carried over from
+// the previous level have no chunks (k_cinc builds their edges).
 constexpr int64_t CE_CHUNK = 64;
 
+// One warp per cell (lane = control), as the edge kernels read the boxes.
 __global__ void __launch_bounds__(256) k_cchunks(const InstDesc *__restrict__ D, int64_t NL,
                                                  const int32_t *__restrict__ cinst, const int32_t *__restrict__ rng,
                                                  const uint8_t *__restrict__ pflag, int32_t *__restrict__ nch)
 {
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= NL) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t s = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (s >= NL) return;                           // whole warp
     const InstDesc &I = D[cinst[s]];
-    const int n = I.n, Lf = I.Lf;
-    const int64_t p0 = I.pair_base + (s - I.slot_base) * I.nu;
-    int ua[MAXN], ub[MAXN];
-    bool any = false;
-    for (int d = 0; d < MAXN; d++) { ua[d] = INT_MAX; ub[d] = INT_MIN; }
-    for (int u = 0; u < I.nu; u++) {
-        const int64_t p = p0 + u;
-        if (pflag[p] & PF_NONFINITE) continue;
-        int a[MAXN], b[MAXN];
-        bool ok = true;
-        for (int d = 0; d < n; d++) {
-            level_range(rng[p * 2 * MAXN + d], rng[p * 2 * MAXN + n + d], Lf, I.n0[d], a[d], b[d]);
-            ok = ok && a[d] <= b[d];
-        }
-        if (!ok) continue;
-        any = true;
-        for (int d = 0; d < n; d++) { ua[d] = min(ua[d], a[d]); ub[d] = max(ub[d], b[d]); }
+    if (s - I.slot_base < I.n_carry) {             // edges from the previous level's
+        if (lane == 0) nch[s] = 0;
+        return;
     }
+    const int n = I.n, Lf = I.Lf;
+    bool live = false;
+    int a[MAXN], b[MAXN];
+    for (int d = 0; d < MAXN; d++) { a[d] = INT_MAX; b[d] = INT_MIN; }
+    if (lane < I.nu) {
+        const int64_t p = I.pair_base + (s - I.slot_base) * I.nu + lane;
+        live = !(pflag[p] & PF_NONFINITE);
+        if (live)
+            for (int d = 0; d < n; d++) {
+                level_range(rng[p * 2 * MAXN + d], rng[p * 2 * MAXN + n + d], Lf, I.n0[d], a[d], b[d]);
+                live = live && a[d] <= b[d];
+            }
+    }
+    const bool any = __any_sync(0xffffffffu, live);
     int64_t roots = any ? 1 : 0;
-    for (int d = 0; d < n && any; d++) roots *= (int64_t)(ub[d] - ua[d] + 1);
-    nch[s] = (int32_t)max((int64_t)1, (roots + CE_CHUNK - 1) / CE_CHUNK);
+    for (int d = 0; d < n; d++) {
+        const int lo = warp_min(live ? a[d] : INT_MAX), hi = warp_max(live ? b[d] : INT_MIN);
+        if (any) roots *= (int64_t)(hi - lo + 1);
+    }
+    if (lane == 0) nch[s] = (int32_t)max((int64_t)1, (roots + CE_CHUNK - 1) / CE_CHUNK);
 }
 
 cudaError_t launch_cchunks(const InstDesc *D, int64_t NL, const int32_t *cinst, const int32_t *rng,
                            const uint8_t *pflag, int32_t *nch, cudaStream_t st)
 {
     if (NL == 0) return cudaSuccess;
-    k_cchunks<<<(unsigned)((NL + 255) / 256), 256, 0, st>>>(D, NL, cinst, rng, pflag, nch);
+    k_cchunks<<<(unsigned)((NL + 7) / 8), 256, 0, st>>>(D, NL, cinst, rng, pflag, nch);
     note_launch();
     return cudaGetLastError();
 }
@@ -227,6 +238,11 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cedges(const InstDesc *__rest
     CtlBox<N> *box = s_box[warp];
     unsigned long long pe = 0;
     while (k < k1) {
+        if (cbase[s + 1] == k) {                   // no chunks: a carried cell
+            s++;
+            continue;
+        }
+        if (FILL && cbase[s] == k) wpos = coff[s];  // the cell starts at its first chunk
         const InstDesc &I = D[cinst[s]];
         const int ls = (int)(s - I.slot_base);
         const int nu = I.nu, Lf = I.Lf;
@@ -428,9 +444,181 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cedges(const InstDesc *__rest
         __syncwarp();
         k = kend;
         s++;
-        if (FILL && k < k1) wpos = coff[s];        // the next cell starts at its first chunk
     }
     if (!FILL && lane == 0 && pe) atomicAdd(pair_edges, pe);
+}
+
+// Edges of a cell carried over from the previous level (kept, not split),
+// derived from its previous edges, one warp per cell. The cell's image and the
+// level ranges of coarse cells do not change between levels (a coarse range
+// follows from the finer decisions by an exact shift), so a target that is
+// still a leaf keeps its edge and control mask; a target split since is
+// replaced by those of its 2^n children that meet the controls of the edge's
+// mask; a target removed since sets the removed-leaf flag of those controls,
+// as do the flags the cell's pairs had before.
+// FILL = false: edges per cell (ccnt), targets per pair (pcnt), in-degrees
+// (rcnt), removed-leaf flags, pair-edge total. FILL = true: edges at coff[cell]
+// (cent, cmask) and reverse edges at rcur[target]++ (rsrc, rmask).
+template <int N, bool FILL>
+__global__ void __launch_bounds__(CE_WARPS * 32) k_cinc(const InstDesc *__restrict__ D, const Range *__restrict__ R,
+                                                       int nr, const int32_t *__restrict__ rng,
+                                                       uint8_t *__restrict__ pflag, int32_t *__restrict__ pcnt,
+                                                       int32_t *__restrict__ ccnt, int32_t *__restrict__ rcnt,
+                                                       const int64_t *__restrict__ coff, int32_t *__restrict__ cent,
+                                                       uint32_t *__restrict__ cmask,
+                                                       unsigned long long *__restrict__ rcur,
+                                                       int32_t *__restrict__ rsrc, uint32_t *__restrict__ rmask,
+                                                       unsigned long long *__restrict__ pair_edges,
+                                                       int32_t *__restrict__ err, const CellPrev prev)
+{
+    constexpr uint32_t FULL = 0xffffffffu;
+    constexpr int NC = 1 << N;
+    __shared__ CtlBox<N> s_box[CE_WARPS][32];
+    __shared__ int s_cnt[CE_WARPS][32];
+    CRANGE_HEAD(CE_WARPS)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t local = (int64_t)(blockIdx.x - rg.block_start) * CE_WARPS + warp;
+    if (local >= rg.count) return;                 // whole warp
+    const int64_t s = rg.first + local;
+    const int ls = (int)(s - I.slot_base);
+    const int nu = I.nu, Lf = I.Lf;
+    const int64_t p = I.pair_base + (int64_t)ls * nu + lane;
+    const int64_t so = prev.oslot[s];
+    if (so < 0 || so >= prev.n_old) {              // not a slot of the previous build
+        if (lane == 0) atomicExch(err, GIS_EBOUNDS);
+        return;                                    // whole warp
+    }
+    CtlBox<N> *box = s_box[warp];
+    bool live_box = false;
+    uint32_t tch = 0;
+    if (lane < nu) {
+        live_box = !(pflag[p] & PF_NONFINITE);
+        if (live_box) {
+            CtlBox<N> b;
+#pragma unroll
+            for (int d = 0; d < N; d++) {
+                b.cf[2 * d] = rng[p * 2 * MAXN + d];
+                b.cf[2 * d + 1] = rng[p * 2 * MAXN + N + d];
+            }
+            box[lane] = b;
+        }
+        if (prev.pflag[prev.cps[so] + lane] & PF_TOUCH_DEAD) tch = 1u << lane;
+        if (!FILL) s_cnt[warp][lane] = 0;
+    }
+    const uint32_t live = __ballot_sync(FULL, live_box);
+    __syncwarp();
+    const int64_t e0 = prev.coff[so], e1 = prev.coff[so + 1];
+    int64_t wpos = FILL ? coff[s] : 0;
+    int32_t nent = 0;
+    unsigned long long pe = 0;
+    for (int64_t eb = e0; eb < e1; eb += 32) {
+        const int64_t e = eb + lane;
+        int ne = 0;
+        int tn[NC];
+        uint32_t tm[NC];
+        const int to = e < e1 ? prev.cent[e] : 0;
+        if (e < e1 && (to < 0 || to >= prev.n_old)) atomicExch(err, GIS_EBOUNDS);
+        else if (e < e1) {
+            const uint32_t m = prev.cmask[e] & live;
+            const int node = prev.s2n[to];
+            const uint8_t st = I.state[node];
+            if (m && st == ST_ALIVE) {
+                tn[0] = node;
+                tm[0] = m;
+                ne = 1;
+            } else if (m && st == ST_DEAD) {
+                tch |= m;
+            } else if (m && st == ST_SPLIT) {
+                const int ch = I.child[node];
+                const int sh = Lf - (I.lvl[node] + 1);
+                int idx[N];
+#pragma unroll
+                for (int d = 0; d < N; d++) idx[d] = I.idx[d][node];
+#pragma unroll
+                for (int cc = 0; cc < NC; cc++) {
+                    int clo[N], chi[N];
+#pragma unroll
+                    for (int d = 0; d < N; d++) {
+                        const int ci = 2 * idx[d] + ((cc >> (N - 1 - d)) & 1);
+                        clo[d] = ci << sh;
+                        chi[d] = (ci + 1) << sh;
+                    }
+                    const uint32_t mc = ctl_mask<N>(box, nu, m, clo, chi);
+                    if (mc) {
+                        tn[ne] = ch + cc;
+                        tm[ne] = mc;
+                        ne++;
+                    }
+                }
+            }
+        }
+        // warp exclusive scan of the per-lane edge counts
+        int incl = ne;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int tot = __shfl_sync(FULL, incl, 31);
+        const int64_t base = wpos + (incl - ne);
+        for (int j = 0; j < ne; j++) {
+            const int t = I.slot[tn[j]];
+            const uint32_t mm = tm[j];
+            if (FILL) {
+                cent[base + j] = t;
+                cmask[base + j] = mm;
+                const unsigned long long r = atomicAdd(&rcur[t], 1ull);
+                rsrc[r] = (int32_t)s;
+                rmask[r] = mm;
+            } else {
+                atomicAdd(&rcnt[t], 1);
+                for (uint32_t b = mm; b; b &= b - 1) atomicAdd(&s_cnt[warp][__ffs(b) - 1], 1);
+                pe += (unsigned long long)__popc(mm);
+            }
+        }
+        wpos += tot;
+        nent += tot;
+    }
+    (void)lt;
+    if (!FILL) {
+        const uint32_t touched = __reduce_or_sync(FULL, tch);
+        const unsigned long long pet = __reduce_add_sync(FULL, (unsigned)pe);
+        __syncwarp();
+        if (lane < nu) {
+            pcnt[p] = s_cnt[warp][lane];
+            if ((touched >> lane) & 1) pflag[p] |= PF_TOUCH_DEAD;
+        }
+        if (lane == 0) {
+            ccnt[s] = nent;
+            if (pet) atomicAdd(pair_edges, pet);
+        }
+    }
+}
+
+cudaError_t launch_cinc(bool fill, int n, const InstDesc *D, const WorkList &w, const CellGraph &g,
+                        const CellPrev &prev, cudaStream_t st)
+{
+    if (w.n_blocks == 0) return cudaSuccess;
+    dim3 gr((unsigned)w.n_blocks), b(CE_WARPS * 32);
+#define CI_CASE(NN)                                                                                          \
+    case NN:                                                                                                 \
+        if (fill)                                                                                            \
+            k_cinc<NN, true><<<gr, b, 0, st>>>(D, w.d_ranges, w.n_ranges, g.rng, g.pflag, g.pcnt, g.ccnt,    \
+                                               g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rsrc, g.rmask,     \
+                                               g.pair_edges, g.err, prev);                                   \
+        else                                                                                                 \
+            k_cinc<NN, false><<<gr, b, 0, st>>>(D, w.d_ranges, w.n_ranges, g.rng, g.pflag, g.pcnt, g.ccnt,   \
+                                                g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rsrc, g.rmask,    \
+                                                g.pair_edges, g.err, prev);                                  \
+        note_launch();                                                                                       \
+        break;
+    switch (n) {
+        CI_CASE(1) CI_CASE(2) CI_CASE(3) CI_CASE(4)
+    default: return cudaErrorInvalidValue;
+    }
+#undef CI_CASE
+    return cudaGetLastError();
 }
 
 // Persistent grid, the same for the count and the fill pass (the fill reads
@@ -477,6 +665,8 @@ cudaError_t launch_cedges(bool fill, int n, const InstDesc *D, int64_t c0, int64
 #undef CE_CASE
     return cudaGetLastError();
 }
+
+int cedges_cells_per_block() { return CE_WARPS; }
 
 // Upper bound of the warps of one edge launch (size of wpart per dimension).
 int cedges_max_warps(int dev)

@@ -45,6 +45,7 @@ struct InstDesc {
     // ---- problem ----
     int32_t dyn, n, m, nu, k, S, substeps, rule, precision, Lf;
     int64_t slot_base, pair_base, n_live;
+    int64_t n_carry;            // leading live cells whose edges derive from the previous level's
     float p32[GIS_NPARAM];      // derived constants for the FP32 model
     float pr32[GIS_NPARAM];     // their radii: |p32 - exact value|, rounded up
     double p64[GIS_NPARAM];     // derived constants for the FP64 model (same ops as the definition)

@@ -210,6 +210,8 @@ struct Inst {
     // host view of device state
     int level = 0, Lf = 0;
     int64_t n_nodes = 0, n_live = 0, n_fresh = 0;
+    int64_t n_carry = 0;        // leading live cells whose edges derive from the previous build's
+    int64_t built_at = -1;      // engine build counter of this problem's last graph
     int64_t slot_base = 0, pair_base = 0;
     bool active = true;
     int tix = -1;               // index in the descriptor table of the current level
@@ -398,6 +400,7 @@ inline void fill_desc(Inst &I)
     D.slot_base = I.slot_base;
     D.pair_base = I.pair_base;
     D.n_live = I.n_live;
+    D.n_carry = I.n_carry;
     derive_params(I, D);
     for (int i = 0; i < GIS_NPARAM; i++) D.pr32[i] = radius_of(D.p64_exact[i], D.p32[i]);
     if (I.dyn.substeps > 0) {
@@ -503,6 +506,17 @@ struct Engine {
     uint32_t *vmask = nullptr; size_t c_vmask = 0;
     int32_t *cinst = nullptr; size_t c_cinst = 0;
     int32_t *cnch = nullptr; size_t c_cnch = 0;
+    // the previous build's graph (swapped with the current arrays per build)
+    int32_t *s2n = nullptr, *s2n_o = nullptr; size_t c_s2n = 0, c_s2n_o = 0;
+    int32_t *oslot = nullptr; size_t c_oslot = 0;
+    int32_t *cps_o = nullptr; size_t c_cps_o = 0;
+    int64_t *coff_o = nullptr; size_t c_coff_o = 0;
+    int32_t *cent_o = nullptr; size_t c_cent_o = 0;
+    uint32_t *cmask_o = nullptr; size_t c_cmask_o = 0;
+    uint8_t *pflag_o = nullptr; size_t c_pflag_o = 0;
+    int64_t build_no = 0;
+    bool have_prev = false;     // the *_o arrays hold the previous build's complete graph
+    int64_t prev_NL = 0;        // cells of that build
     int64_t *cbase = nullptr; size_t c_cbase = 0;
     int32_t *wpart = nullptr; size_t c_wpart = 0;
     int32_t *rng = nullptr; size_t c_rng = 0;
@@ -629,7 +643,7 @@ struct Engine {
         mem.grow(I.lvl, c1, need, k);
         mem.grow(I.state, c2, need, k);
         mem.grow(I.child, c3, need, k);
-        mem.grow(I.slot, c4, need, 0);
+        mem.grow(I.slot, c4, need, k);             // carried cells read their previous slot
         for (int d = 0; d < I.dyn.n; d++) {
             size_t cd = c;
             mem.grow(I.idx[d], cd, need, k);
@@ -820,6 +834,21 @@ struct Engine {
     {
         LaunchScope ls_(cum);
         finish_prune();
+        // cells kept from this problem's previous build (which must be the
+        // engine's previous build) take their edges from that graph
+        for (int i : ids) {
+            Inst &I = *inst[i];
+            I.n_carry = (have_prev && I.built_at == build_no - 1) ? I.n_live - I.n_fresh : 0;
+            I.built_at = build_no;
+        }
+        build_no++;
+        std::swap(s2n, s2n_o); std::swap(c_s2n, c_s2n_o);
+        std::swap(cps, cps_o); std::swap(c_cps, c_cps_o);
+        std::swap(coff, coff_o); std::swap(c_coff, c_coff_o);
+        std::swap(cent, cent_o); std::swap(c_cent, c_cent_o);
+        std::swap(cmask, cmask_o); std::swap(c_cmask, c_cmask_o);
+        std::swap(pflag, pflag_o); std::swap(c_pflag, c_pflag_o);
+        have_prev = false;
         number(ids);
         have_graph = have_prune = have_bnd = false;
         const size_t Ps = (size_t)std::max<int64_t>(P, 1), NLs = (size_t)std::max<int64_t>(NL, 1);
@@ -833,7 +862,9 @@ struct Engine {
         mem.ensure(cps, c_cps, NLs);
         mem.ensure(cinfo, c_cinfo, NLs);
         mem.ensure(cinst, c_cinst, NLs);
-        CK(launch_cgather(d_desc, ws, cps, cinfo, cinst, st));
+        mem.ensure(s2n, c_s2n, NLs);
+        mem.ensure(oslot, c_oslot, NLs);
+        CK(launch_cgather(d_desc, ws, cps, cinfo, cinst, s2n, oslot, st));
         timer.end();
 
         // propagation of new cells, grouped by (dynamics, n, precision, lanes)
@@ -948,6 +979,17 @@ struct Engine {
         for (int n = 1; n <= MAXN; n++)
             CK(launch_cedges(false, n, d_desc, seg_base[n], seg_base[n + 1], cbase, cinst, g,
                              wpart + (size_t)(n - 1) * Wmax, st));
+        const CellPrev prev{oslot, coff_o, cent_o, cmask_o, s2n_o, cps_o, pflag_o, prev_NL};
+        WorkList wcar[MAXN + 1];
+        for (int n = 1; n <= MAXN; n++) {
+            std::vector<RangeSpec> r;
+            for (int i : ids)
+                if (inst[i]->dyn.n == n && inst[i]->n_carry > 0)
+                    r.push_back({inst[i]->tix, inst[i]->slot_base, inst[i]->n_carry});
+            if (r.empty()) continue;
+            wcar[n] = make_work(r, cedges_cells_per_block());
+            CK(launch_cinc(false, n, d_desc, wcar[n], g, prev, st));
+        }
         timer.end();
         timer.begin(PH_SCAN);
         CK(launch_scan_i32(ccnt, coff, NL, scratch, st));
@@ -981,6 +1023,16 @@ struct Engine {
         for (int n = 1; n <= MAXN; n++)
             CK(launch_cedges(true, n, d_desc, seg_base[n], seg_base[n + 1], cbase, cinst, g,
                              wpart + (size_t)(n - 1) * Wmax, st));
+        for (int n = 1; n <= MAXN; n++) {
+            if (!wcar[n].n_blocks) continue;
+            std::vector<RangeSpec> r;
+            for (int i : ids)
+                if (inst[i]->dyn.n == n && inst[i]->n_carry > 0)
+                    r.push_back({inst[i]->tix, inst[i]->slot_base, inst[i]->n_carry});
+            CK(launch_cinc(true, n, d_desc, make_work(r, cedges_cells_per_block()), g, prev, st));
+        }
+        have_prev = true;
+        prev_NL = NL;
         timer.end();
 
         for (int i : ids) inst[i]->cells_built += inst[i]->n_live;

@@ -83,9 +83,12 @@ __device__ __forceinline__ int descend(const InstDesc &I, const RF &rf, V &visit
 }
 
 // ---------------------------------------------------------------------------
-// Exclusive scan (reduce / scan-of-partials / apply), int64 output of n + 1.
+// Exclusive scan, int64 output of n + 1: per tile sums, then each tile adds
+// the sums of the tiles before it (read directly while there are at most
+// SCAN_DIRECT tiles, else from a recursive scan of the sums) and scans itself.
 // ---------------------------------------------------------------------------
-constexpr int SCAN_T = 256, SCAN_IPT = 16, SCAN_TILE = SCAN_T * SCAN_IPT;
+constexpr int SCAN_T = 256, SCAN_IPT = 4, SCAN_TILE = SCAN_T * SCAN_IPT;
+constexpr int64_t SCAN_DIRECT = 4096;
 
 __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *total)
 {
@@ -129,11 +132,23 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const T *__restrict__ in
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
+// part_scan: the scanned tile sums, or (raw) the tile sums themselves
 template <class T>
 __global__ void __launch_bounds__(SCAN_T) k_scan_apply(const T *__restrict__ in, int64_t n,
-                                                       const int64_t *__restrict__ part_scan, int64_t *__restrict__ out)
+                                                       const int64_t *__restrict__ part_scan, bool raw,
+                                                       int64_t *__restrict__ out)
 {
     __shared__ int64_t s_v[SCAN_TILE];
+    __shared__ int64_t s_pre;
+    if (raw) {
+        int64_t acc = 0;
+        for (int64_t j = threadIdx.x; j < (int64_t)blockIdx.x; j += SCAN_T) acc += part_scan[j];
+        int64_t tot;
+        block_excl_scan(acc, &tot);
+        if (threadIdx.x == 0) s_pre = tot;
+    } else if (threadIdx.x == 0) {
+        s_pre = part_scan ? part_scan[blockIdx.x] : 0;
+    }
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
     for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_T) {
         const int64_t j = base + i;
@@ -148,7 +163,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_apply(const T *__restrict__ in,
         sum += s_v[threadIdx.x * SCAN_IPT + i];
     }
     int64_t tot;
-    const int64_t pre = block_excl_scan(sum, &tot) + (part_scan ? part_scan[blockIdx.x] : 0);
+    const int64_t pre = block_excl_scan(sum, &tot) + s_pre;
 #pragma unroll
     for (int i = 0; i < SCAN_IPT; i++) s_v[threadIdx.x * SCAN_IPT + i] = pre + loc[i];
     __syncthreads();
@@ -178,14 +193,18 @@ static cudaError_t scan_rec(const T *in, int64_t *out, int64_t n, int64_t *scrat
     }
     const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (nb == 1) {
-        k_scan_apply<T><<<1, SCAN_T, 0, st>>>(in, n, nullptr, out); note_launch();
+        k_scan_apply<T><<<1, SCAN_T, 0, st>>>(in, n, nullptr, false, out); note_launch();
         return cudaGetLastError();
     }
     int64_t *part = scratch, *part_scan = scratch + nb;
     k_scan_reduce<T><<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, part); note_launch();
+    if (nb <= SCAN_DIRECT) {
+        k_scan_apply<T><<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, part, true, out); note_launch();
+        return cudaGetLastError();
+    }
     cudaError_t e = scan_rec<int64_t>(part, part_scan, nb, scratch + 2 * nb + 1, st);
     if (e != cudaSuccess) return e;
-    k_scan_apply<T><<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, part_scan, out); note_launch();
+    k_scan_apply<T><<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, part_scan, false, out); note_launch();
     return cudaGetLastError();
 }
 

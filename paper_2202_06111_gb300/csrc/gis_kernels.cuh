@@ -109,7 +109,20 @@ struct CellGraph {
     int32_t *err;
 };
 cudaError_t launch_cgather(const InstDesc *D, const WorkList &wslots, int32_t *cps, uint8_t *cinfo, int32_t *cinst,
-                           cudaStream_t st);
+                           int32_t *s2n, int32_t *oslot, cudaStream_t st);
+// the previous level's graph, for cells carried over
+struct CellPrev {
+    const int32_t *oslot;        // [new slot] the cell's slot at the previous level
+    const int64_t *coff;         // previous edge offsets per slot
+    const int32_t *cent;         // previous edge targets (previous slots)
+    const uint32_t *cmask;
+    const int32_t *s2n;          // previous slot -> node
+    const int32_t *cps;          // previous slot -> first pair
+    const uint8_t *pflag;        // previous pair flags
+    int64_t n_old;               // previous cell count (slots are checked against it)
+};
+cudaError_t launch_cinc(bool fill, int n, const InstDesc *D, const WorkList &wcarried, const CellGraph &g,
+                        const CellPrev &prev, cudaStream_t st);
 // per cell the chunk count of its union box (the work unit of the edge kernels)
 cudaError_t launch_cchunks(const InstDesc *D, int64_t NL, const int32_t *cinst, const int32_t *rng,
                            const uint8_t *pflag, int32_t *nch, cudaStream_t st);
@@ -119,6 +132,7 @@ cudaError_t launch_cchunks(const InstDesc *D, int64_t NL, const int32_t *cinst, 
 cudaError_t launch_cedges(bool fill, int n, const InstDesc *D, int64_t c0, int64_t c1, const int64_t *cbase,
                           const int32_t *cinst, const CellGraph &g, int32_t *wpart, cudaStream_t st);
 int cedges_max_warps(int dev);
+int cedges_cells_per_block();     // cells per block of k_cinc
 cudaError_t launch_cprune_init(const InstDesc *D, const WorkList &wslots, const uint8_t *pflag, const int32_t *pcnt,
                                int32_t *pc, uint32_t *vmask, uint8_t *alive, int32_t *frontier0, uint32_t *sizes,
                                cudaStream_t st);
