@@ -124,14 +124,16 @@ __device__ __forceinline__ DB dbmul(DB a, DB b)
 }
 
 // |a/b - ma/mb| <= (|ma| rb + |mb| ra) / (|mb| (|mb| - rb)) when |mb| > rb
+// (the quotient rounded to nearest, raised by 2^-23 upward)
 __device__ __forceinline__ DB dbdiv(DB a, DB b)
 {
     const float bl = dw_abs_dn(dwof(b));
-    if (!(bl > b.r)) return {NAN, NAN, INFINITY};
     const DW m = dw_div(dwof(a), dwof(b));
     const float num = __fmaf_ru(dw_abs_up(dwof(a)), b.r, __fmul_ru(dw_abs_up(dwof(b)), a.r));
     const float den = __fmul_rd(bl, __fsub_rd(bl, b.r));
-    return {m.h, m.l, __fadd_ru(__fdiv_ru(num, den), db_round(m))};
+    const float q = __fmul_ru(__fdiv_rn(num, den), 1.00000012f);
+    const bool ok = bl > b.r;
+    return {ok ? m.h : NAN, ok ? m.l : NAN, ok ? __fadd_ru(q, db_round(m)) : INFINITY};
 }
 
 // ---- exp ---------------------------------------------------------------------

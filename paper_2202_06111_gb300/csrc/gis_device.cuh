@@ -151,31 +151,30 @@ __device__ __forceinline__ Ball bfma(Ball a, Ball b, Ball c)
     const float r = __fmaf_ru(fabsf(a.m), b.r, __fmaf_ru(fabsf(b.m), a.r, __fmaf_ru(a.r, b.r, c.r)));
     return {m, __fadd_ru(r, b_rerr(m))};
 }
-// |a/b - am/bm| <= (|am| rb + |bm| ra) / (|bm| (|bm| - rb)) when |bm| > rb
+// |a/b - am/bm| <= (|am| rb + |bm| ra) / (|bm| (|bm| - rb)) when |bm| > rb;
+// the quotient of the bound is rounded to nearest (within 2^-24 of itself) and
+// raised by 2^-23 upward. |bm| <= rb gives the non-finite ball.
 __device__ __forceinline__ Ball bdiv(Ball a, Ball b)
 {
     const float ab = fabsf(b.m);
-    if (!(ab > b.r)) return {NAN, INFINITY};
     const float m = a.m / b.m;
     const float num = __fmaf_ru(fabsf(a.m), b.r, __fmul_ru(ab, a.r));
     const float den = __fmul_rd(ab, __fsub_rd(ab, b.r));
-    return {m, __fadd_ru(__fdiv_ru(num, den), b_rerr(m))};
+    const float q = __fmul_ru(num / den, 1.00000012f);
+    const bool ok = ab > b.r;
+    return {ok ? m : NAN, ok ? __fadd_ru(q, b_rerr(m)) : INFINITY};
 }
-// exp is increasing: the ball of exp over [m - r, m + r] spans
-// [expf(m - r) (1 - 2^-21), expf(m + r) (1 + 2^-21)] (library error bound);
-// for small r the midpoint is expf(m) and the radius e^m (r + r^2) + error.
+// exp is increasing and e^r - 1 <= r + r^2 for r <= 1: over [m - r, m + r]
+// the ball is expf(m) with radius e^m (r + r^2) plus the library error
+// (expf within 2^-21 relative). A radius above 1/4 gives the non-finite ball
+// (the pair is then rechecked over all its samples).
 __device__ __forceinline__ Ball bexp(Ball a)
 {
-    if (a.r <= 0.25f) {
-        const float e = expf(a.m);
-        const float eup = __fmaf_ru(e, B_F, e);
-        const float grow = __fmaf_ru(a.r, a.r, a.r);
-        return {e, __fmaf_ru(eup, grow, __fmaf_ru(e, B_F, B_ETA))};
-    }
-    const float lo = __fmul_rd(expf(__fsub_rd(a.m, a.r)), 1.0f - B_F);
-    const float hi = __fmul_ru(expf(__fadd_ru(a.m, a.r)), 1.0f + B_F);
-    const float m = 0.5f * lo + 0.5f * hi;
-    return {m, __fadd_ru(fmaxf(__fsub_ru(hi, m), __fsub_ru(m, lo)), b_rerr(m))};
+    const float e = expf(a.m);
+    const float eup = __fmaf_ru(e, B_F, e);
+    const float grow = __fmaf_ru(a.r, a.r, a.r);
+    const bool ok = a.r <= 0.25f;
+    return {ok ? e : NAN, ok ? __fmaf_ru(eup, grow, __fmaf_ru(e, B_F, B_ETA)) : INFINITY};
 }
 
 // sin and cos are 1-Lipschitz
