@@ -46,6 +46,8 @@ struct InstDesc {
     int32_t dyn, n, m, nu, k, S, substeps, rule, precision, Lf;
     int64_t slot_base, pair_base, n_live;
     int64_t n_carry;            // leading live cells whose edges derive from the previous level's
+    int32_t tile[MAXN];         // root cells per dimension of a lattice tile (first build)
+    int32_t ntile[MAXN];        // tiles per dimension
     float p32[GIS_NPARAM];      // derived constants for the FP32 model
     float pr32[GIS_NPARAM];     // their radii: |p32 - exact value|, rounded up
     double p64[GIS_NPARAM];     // derived constants for the FP64 model (same ops as the definition)
@@ -61,6 +63,7 @@ struct InstDesc {
     float w32[MAXL + 1][MAXN];
     float wr32[MAXL + 1][MAXN]; // radius of w32
     float invwf32[MAXN];        // 1 / w at Lf
+    double iw64[MAXN];          // 1 / w at Lf, rounded to nearest
     float tmargin[MAXN];        // FP32 t-computation error bound plus the optional band, Lf cells
     float frac32[MAXK];
     float fracr32[MAXK];        // radius of frac32

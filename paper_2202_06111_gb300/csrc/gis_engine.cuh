@@ -428,6 +428,7 @@ inline void fill_desc(Inst &I)
         }
         const double wf = D.w64[I.Lf][d];
         D.invwf32[d] = (float)(1.0 / wf);
+        D.iw64[d] = 1.0 / wf;
         // FP32 t = (y - lo32) * invw for |y| within the box of X widened by its
         // size: rounding of lo, of the difference, of the product and of 1/w,
         // bounded in Lf cell widths (x2 margin), plus the optional band.
@@ -437,6 +438,8 @@ inline void fill_desc(Inst &I)
         const double tb = 2.0 * (lo_err + scale * 4.0 * 5.96e-8);
         D.tmargin[d] = (float)(I.band + tb);
     }
+    const bool lat = lattice_tile(n, I.grid.k_samples, D.n0, D.tile);
+    for (int d = 0; d < MAXN; d++) D.ntile[d] = !lat ? 0 : d < n ? (D.n0[d] + D.tile[d] - 1) / D.tile[d] : 1;
     const int k = I.grid.k_samples;
     for (int j = 0; j < MAXK; j++) {
         const double f = (k == 1) ? 0.5 : (j < k ? (double)j / (double)(k - 1) : 0.0);
@@ -875,11 +878,29 @@ struct Engine {
             Inst &I = *inst[i];
             if (I.n_fresh == 0) continue;
             const int64_t first = I.pair_base + (I.n_live - I.n_fresh) * I.nu;
-            const int lanes = I.precision == GIS_FP64_PLAIN ? 1 : lanes_for(I);
-            groups[{I.dyn.dyn_id, I.dyn.n, I.precision, lanes}].push_back({I.tix, first, I.n_fresh * I.nu});
+            // first build of an FP32 problem with boundary samples: shared
+            // lattice points (lanes = 0 marks the lattice kernel; items are
+            // tiles x controls)
+            if (I.precision == GIS_FP32_RECHECK && I.desc.ntile[0] > 0 && I.level == 0 &&
+                I.n_fresh == I.n_live && I.n_live == I.n_nodes && opt.lanes_per_pair == 0) {
+                int64_t tiles = 1;
+                double points = 1;             // lattice points propagated, summed over tiles
+                const int k1 = I.grid.k_samples - 1;
+                for (int d = 0; d < I.dyn.n; d++) {
+                    const int T = I.desc.tile[d], n0 = I.desc.n0[d], nt = I.desc.ntile[d];
+                    tiles *= nt;
+                    points *= (double)n0 * k1 + nt;
+                    (void)T;
+                }
+                groups[{I.dyn.dyn_id, I.dyn.n, I.precision, 0}].push_back({I.tix, 0, tiles * I.nu});
+                cum.prop_flops += pair_flops(I) / I.S * points * I.nu;
+            } else {
+                const int lanes = I.precision == GIS_FP64_PLAIN ? 1 : lanes_for(I);
+                groups[{I.dyn.dyn_id, I.dyn.n, I.precision, lanes}].push_back({I.tix, first, I.n_fresh * I.nu});
+                cum.prop_flops += pair_flops(I) * (double)(I.n_fresh * I.nu);
+            }
             last_new_pairs += I.n_fresh * I.nu;
             I.pairs_prop += I.n_fresh * I.nu;
-            cum.prop_flops += pair_flops(I) * (double)(I.n_fresh * I.nu);
             cum.cum_prop_launches += 0;
         }
         for (auto &g : groups) {
@@ -887,6 +908,8 @@ struct Engine {
             const int lanes = std::get<3>(g.first);
             if (prec == GIS_FP64_PLAIN) {
                 CK(launch_prop64(dyn, n, d_desc, make_work(g.second, 256), st));
+            } else if (lanes == 0) {
+                CK(launch_prop32_lattice(dyn, n, d_desc, make_work(g.second, 1), st));
             } else {
                 CK(launch_prop32(dyn, n, lanes, d_desc, make_work(g.second, prop_pairs_per_block(lanes)), st));
             }

@@ -32,6 +32,9 @@ struct RecheckQueue {            // per dynamics: (global pair, inst | mask << 1
 
 // FP32 propagation with `lanes` per pair (1..32), FP64 propagation (plain).
 cudaError_t launch_prop32(int dyn, int n, int lanes, const InstDesc *D, const WorkList &w, cudaStream_t st);
+// first build: one block per (tile of root cells, control), items = tiles x controls
+cudaError_t launch_prop32_lattice(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st);
+bool lattice_tile(int n, int k, const int32_t *n0, int32_t *tile);
 cudaError_t launch_prop64(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st);
 int prop_pairs_per_block(int lanes);
 // binning: decisions at the finest level, band check, recheck queue

@@ -129,6 +129,129 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop32(const InstDesc *__restr
     }
 }
 
+// First build, all root cells fresh: the k^n sample lattices of adjacent
+// cells share their boundary points (k >= 2). A shared point is formed once,
+// from the coordinates of the cell above it (j = 0); its ball holds the exact
+// lattice point, as the ball of either cell would. One block per (tile of root cells,
+// control): each lattice point of the tile is propagated once into shared
+// memory, then each cell reduces the extremes of its own k^n points: the
+// per-pair kernel's boxes (up to the radius of the shared points' fraction
+// 1, which is exact), from (T (k-1) + 1)^n instead of T^n k^n propagations
+// per tile.
+constexpr int LAT_POINTS = 4096;                   // per block, divided by n
+
+template <class DY>
+__global__ void __launch_bounds__(PROP_THREADS) k_prop32_lat(const InstDesc *__restrict__ D,
+                                                             const Range *__restrict__ R, int nr)
+{
+    constexpr int N = DY::N;
+    constexpr int PMAX = LAT_POINTS / N;
+    __shared__ int s_r;
+    __shared__ float s_p[GIS_NPARAM], s_pr[GIS_NPARAM];
+    __shared__ float s_a[PMAX * N], s_b[PMAX * N];
+    __shared__ uint8_t s_bad[PMAX];
+    if (threadIdx.x == 0) s_r = find_range(R, nr, blockIdx.x);
+    __syncthreads();
+    const Range rg = R[s_r];
+    const InstDesc &I = D[rg.inst];
+    if (threadIdx.x < GIS_NPARAM) {
+        s_p[threadIdx.x] = I.p32[threadIdx.x];
+        s_pr[threadIdx.x] = I.pr32[threadIdx.x];
+    }
+    const int64_t item = rg.first + (blockIdx.x - rg.block_start);   // one item per block
+    const int u = (int)(item % I.nu);
+    int64_t t = item / I.nu;
+    const int k1 = I.k - 1;
+    int c0[N], nc[N], np[N];
+    int P = 1, C = 1;
+#pragma unroll
+    for (int d = N - 1; d >= 0; d--) {
+        const int ti = (int)(t % I.ntile[d]);
+        t /= I.ntile[d];
+        c0[d] = ti * I.tile[d];
+        nc[d] = min(I.tile[d], I.n0[d] - c0[d]);
+        np[d] = nc[d] * k1 + 1;
+        P *= np[d];
+        C *= nc[d];
+    }
+    __syncthreads();
+    const MB M{s_p, s_pr, I.m, I.substeps, {I.h32, I.hr32}, {I.hh32, I.hhr32}, {I.h6_32, I.h6r32}};
+    Ball uu[MAXN];
+    for (int j = 0; j < I.m; j++) uu[j] = Ball{I.u32[u * I.m + j], I.ur32[u * I.m + j]};
+    for (int pt = threadIdx.x; pt < P; pt += PROP_THREADS) {
+        Ball x[N], y[N];
+        int r = pt;
+#pragma unroll
+        for (int d = N - 1; d >= 0; d--) {
+            const int g = c0[d] * k1 + r % np[d];
+            r /= np[d];
+            const int idx = min(g / k1, I.n0[d] - 1);
+            const int j = g - idx * k1;
+            const Ball tt = badd(bexact((float)idx), Ball{I.frac32[j], I.fracr32[j]});
+            x[d] = bfma(Ball{I.w32[0][d], I.wr32[0][d]}, tt, Ball{I.lo32[d], I.lor32[d]});
+        }
+        stepB<DY>(M, x, uu, y);
+        bool bad = false;
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            const Ball yb = bfinal(y[d]);
+            const float a = __fsub_rd(yb.m, yb.r), b = __fadd_ru(yb.m, yb.r);
+            bad = bad || !(fabsf(a) <= FLT_MAX && fabsf(b) <= FLT_MAX);
+            s_a[pt * N + d] = a;
+            s_b[pt * N + d] = b;
+        }
+        s_bad[pt] = bad;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += PROP_THREADS) {
+        int lc[N];
+        int r = c, node = 0;
+#pragma unroll
+        for (int d = N - 1; d >= 0; d--) {
+            lc[d] = r % nc[d];
+            r /= nc[d];
+        }
+#pragma unroll
+        for (int d = 0; d < N; d++) node = node * I.n0[d] + c0[d] + lc[d];
+        float lomin[N], himin[N], lomax[N], himax[N];
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            lomin[d] = himin[d] = INFINITY;
+            lomax[d] = himax[d] = -INFINITY;
+        }
+        bool bad = false;
+        for (int s = 0; s < I.S; s++) {
+            int rs = s, pt = 0;
+            int jd[N];                        // digit d of s: the sample offset along d
+#pragma unroll
+            for (int d = 0; d < N; d++) {
+                jd[d] = rs % I.k;
+                rs /= I.k;
+            }
+#pragma unroll
+            for (int d = 0; d < N; d++) pt = pt * np[d] + lc[d] * k1 + jd[d];
+            bad = bad || s_bad[pt];
+#pragma unroll
+            for (int d = 0; d < N; d++) {
+                const float a = s_a[pt * N + d], b = s_b[pt * N + d];
+                lomin[d] = fminf(lomin[d], a);
+                himin[d] = fminf(himin[d], b);
+                lomax[d] = fmaxf(lomax[d], a);
+                himax[d] = fmaxf(himax[d], b);
+            }
+        }
+        const int64_t q = (int64_t)node * I.nu + u;
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            I.box32[q * 4 * N + 2 * d] = lomin[d];
+            I.box32[q * 4 * N + 2 * d + 1] = himin[d];
+            I.box32[q * 4 * N + 2 * (N + d)] = lomax[d];
+            I.box32[q * 4 * N + 2 * (N + d) + 1] = himax[d];
+        }
+        I.exact[q] = bad ? EX_NF32 : 0;
+    }
+}
+
 template <class DY>
 __global__ void __launch_bounds__(PROP_THREADS) k_prop64(const InstDesc *__restrict__ D,
                                                          const Range *__restrict__ R, int nr)
@@ -192,7 +315,14 @@ template <int N>
 __device__ __forceinline__ void decide_exact(const InstDesc &I, int e, double v, int32_t &out, bool &inx)
 {
     const int d = e % N;
-    const double t = __ddiv_rn(__dsub_rn(v, I.lo[d]), I.w64[I.Lf][d]);
+    // t = fl(fl(v - lo) / w). The product with the rounded reciprocal is within
+    // 3.01 * 2^-53 of t relative, so it has the same ceil / floor unless an
+    // integer lies within 2^-50 of it (or it is tiny); only then divide.
+    const double num = __dsub_rn(v, I.lo[d]);
+    double t = __dmul_rn(num, I.iw64[d]);
+    const double at = fabs(t);
+    if (!(fabs(t - rint(t)) > at * 8.8817841970012523e-16) || !(at > 1e-290))
+        t = __ddiv_rn(num, I.w64[I.Lf][d]);
     const double Nf = (double)((int64_t)I.n0[d] << I.Lf);
     if (e < N) {
         out = (int32_t)fmin(fmax(ceil(t), 0.0), Nf + 1.0);
@@ -686,6 +816,62 @@ cudaError_t launch_prop32(int dyn, int n, int lanes, const InstDesc *D, const Wo
         }
     }
     return cudaErrorInvalidValue;
+}
+
+template <class DY>
+static cudaError_t prop32_lat_l(const InstDesc *D, const WorkList &w, cudaStream_t st)
+{
+    k_prop32_lat<DY><<<(unsigned)w.n_blocks, PROP_THREADS, 0, st>>>(D, w.d_ranges, w.n_ranges); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prop32_lattice(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st)
+{
+    if (w.n_blocks == 0) return cudaSuccess;
+    switch (dyn) {
+    case GIS_DYN_VDP: return prop32_lat_l<DynVdp>(D, w, st);
+    case GIS_DYN_CSTR_DL: return prop32_lat_l<DynCstrDl>(D, w, st);
+    case GIS_DYN_CARTPOLE: return prop32_lat_l<DynCartpole>(D, w, st);
+    case GIS_DYN_CSTR_PAPER: return prop32_lat_l<DynCstrPaper>(D, w, st);
+    case GIS_DYN_LINMAP:
+        switch (n) {
+        case 1: return prop32_lat_l<DynLin<1>>(D, w, st);
+        case 2: return prop32_lat_l<DynLin<2>>(D, w, st);
+        case 3: return prop32_lat_l<DynLin<3>>(D, w, st);
+        case 4: return prop32_lat_l<DynLin<4>>(D, w, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Tile of root cells for the lattice kernel: grow the extents in turn while
+// the tile's lattice points fit a block and its cells fit one pass; false if
+// one cell's k^n points do not fit.
+bool lattice_tile(int n, int k, const int32_t *n0, int32_t *tile)
+{
+    const int pmax = LAT_POINTS / n;
+    int64_t one = 1;
+    for (int d = 0; d < n; d++) {
+        tile[d] = 1;
+        one *= k;
+    }
+    if (k < 2 || one > pmax) return false;
+    for (bool grew = true; grew;) {
+        grew = false;
+        for (int d = n - 1; d >= 0; d--) {
+            if (tile[d] >= n0[d]) continue;
+            int64_t pts = 1, cells = 1;
+            for (int e = 0; e < n; e++) {
+                const int te = e == d ? std::min(2 * tile[e], (int)n0[e]) : tile[e];
+                pts *= (int64_t)te * (k - 1) + 1;
+                cells *= te;
+            }
+            if (pts > pmax || cells > PROP_THREADS) continue;
+            tile[d] = std::min(2 * tile[d], (int)n0[d]);
+            grew = true;
+        }
+    }
+    return true;
 }
 
 template <class DY>
