@@ -53,6 +53,8 @@ def _workload(name):
         return W.vdp_64()
     if name == "serving_2000":
         return {"serving": W.serving_2000()}
+    if name == "batch_512":
+        return {"batch": W.batch_512()}
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -387,9 +389,68 @@ def run_serving(a, reqs):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(a, probs):
+    """512 uneven instances solved together (gis_batch_solve: every level of
+    every active instance in the same launches), against the same instances
+    solved one context at a time."""
+    import torch
+    from paper_2202_06111_gb300 import build, gis
+
+    build.build()
+    gis.load()
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        gis.batch_solve(probs[:16], stream=stream.cuda_stream, want_cells=False)
+    torch.cuda.synchronize()
+    clk = Clocks(dev)
+    times, stats = [], []
+    for _ in range(max(1, a.steps)):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        with torch.cuda.stream(stream):
+            res, st = gis.batch_solve(probs, stream=stream.cuda_stream, want_cells=False)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t)
+        stats.append(st)
+        assert all(r["status"] == 0 for r in res)
+    clocks = clk.stop()
+    cells = stats[-1]["cum_cells_built"]
+    edges = stats[-1]["cum_edges"]
+    launches = stats[-1]["cum_launches"]
+    # the same instances one context each (sequential)
+    t = time.perf_counter()
+    seq_cells = 0
+    for p in probs:
+        with torch.cuda.stream(stream):
+            c = gis.Context(p, stream=stream.cuda_stream)
+            c.solve()
+            seq_cells += c.stats()["cum_cells_built"]
+            c.close()
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t
+    wall = statistics.median(times)
+    line = {"metric": "graph-construction cells/s", "value": cells / wall, "unit": "cells/s", "n_gpus": 1,
+            "steps": len(times), "warmup": 1, "ms_per_step": 1e3 * wall, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch_512", "instances": len(probs),
+                       "systems": "Van der Pol mu~U[0.5,2] / CSTR Da~U[0.06,0.09]",
+                       "grids": "log-uniform 32^2-512^2", "samples_per_dim": 3, "controls": "5-11",
+                       "levels": "0-3", "precision": "fp32 propagation, double-word / fp64 recheck"},
+            "edges_per_s": edges / wall, "cells_per_step": cells, "gpu_launches": launches,
+            "sequential": {"ms": 1e3 * seq, "cells": seq_cells, "speedup_of_batch": seq / wall},
+            "e2e": {"value": cells / wall, "unit": "cells/s", "note": "host request arrays to host results"},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = _args()
     prob = _workload(a.workload)
+    if "batch" in prob:
+        if a.impl == "gis":
+            run_batch(a, prob["batch"])
+        return
     if "serving" in prob:
         if a.impl == "gis":
             run_serving(a, prob["serving"][: a.steps] if a.steps < len(prob["serving"]) else prob["serving"])

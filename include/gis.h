@@ -147,8 +147,10 @@ typedef struct {
     double ms_prop, ms_bin, ms_recheck, ms_count, ms_scan, ms_fill, ms_transpose,
            ms_prune, ms_classify, ms_split, ms_other;
     /* cumulative algorithmic work of the propagation kernels */
-    double prop_flops;      /* FP32 (or FP64) arithmetic operations, as counted
-                               from the model expressions                         */
+    double prop_flops;      /* FP32: operations of the certified (midpoint-radius)
+                               samples propagated, counted from the ball formulas
+                               (an FMA counts 2); FP64 plain: the model
+                               expressions' operations                           */
     double graph_bytes;     /* algorithmic bytes of count + fill + transpose       */
     double prune_bytes;     /* algorithmic bytes of the prune                      */
     double count_bytes, fill_bytes, transpose_bytes; /* the parts of graph_bytes   */

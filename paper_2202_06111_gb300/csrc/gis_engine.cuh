@@ -258,6 +258,36 @@ inline double pair_flops(const Inst &I)
     return per * I.S;
 }
 
+// FP32 operations of one certified (midpoint-radius) sample, counted from the
+// ball formulas in gis_device.cuh (an FMA counts 2): add / sub 5, mul 9,
+// fma 11, div 11, exp 9, sin-cos 8. Per right-hand side: Van der Pol 2 fma,
+// 1 mul, 1 sub (36); CSTR 2 fma, 1 div, 1 exp, 4 sub, 3 mul (89); cart-pole
+// 9 mul, 4 fma, 1 div, 1 sin-cos (144); Eq. 4 CSTR 1 div, 4 sub, 1 exp, 2 mul,
+// 3 fma (91); linear n (n + m) fma. Per RK4 substep 4 right-hand sides plus
+// 5n fma and 2n add for the stages and the update; per sample n (add + fma)
+// for the lattice point and 9n for the final widening and the extremes.
+inline double ball_flops_rhs(const Inst &I)
+{
+    const int n = I.dyn.n, m = I.dyn.m;
+    switch (I.dyn.dyn_id) {
+    case GIS_DYN_VDP: return 36;
+    case GIS_DYN_CSTR_DL: return 89;
+    case GIS_DYN_CARTPOLE: return 144;
+    case GIS_DYN_CSTR_PAPER: return 91;
+    case GIS_DYN_LINMAP: return 11.0 * n * (n + m);
+    }
+    return 0;
+}
+
+inline double sample_ball_flops(const Inst &I)
+{
+    const int n = I.dyn.n;
+    double per = 16.0 * n + 9.0 * n;
+    if (I.dyn.substeps == 0) per += ball_flops_rhs(I);
+    else per += I.dyn.substeps * (4.0 * ball_flops_rhs(I) + 55.0 * n + 10.0 * n);
+    return per;
+}
+
 inline int ipow(int b, int e)
 {
     int r = 1;
@@ -893,11 +923,13 @@ struct Engine {
                     (void)T;
                 }
                 groups[{I.dyn.dyn_id, I.dyn.n, I.precision, 0}].push_back({I.tix, 0, tiles * I.nu});
-                cum.prop_flops += pair_flops(I) / I.S * points * I.nu;
+                cum.prop_flops += sample_ball_flops(I) * points * I.nu;
             } else {
                 const int lanes = I.precision == GIS_FP64_PLAIN ? 1 : lanes_for(I);
                 groups[{I.dyn.dyn_id, I.dyn.n, I.precision, lanes}].push_back({I.tix, first, I.n_fresh * I.nu});
-                cum.prop_flops += pair_flops(I) * (double)(I.n_fresh * I.nu);
+                cum.prop_flops += (I.precision == GIS_FP64_PLAIN ? pair_flops(I)
+                                                                 : sample_ball_flops(I) * I.S) *
+                                  (double)(I.n_fresh * I.nu);
             }
             last_new_pairs += I.n_fresh * I.nu;
             I.pairs_prop += I.n_fresh * I.nu;
