@@ -48,6 +48,8 @@ struct InstDesc {
     int64_t n_carry;            // leading live cells whose edges derive from the previous level's
     int32_t tile[MAXN];         // root cells per dimension of a lattice tile (first build)
     int32_t ntile[MAXN];        // tiles per dimension
+    int64_t fresh0;             // live index of the first fresh cell (children of split cells)
+    int32_t sib_groups;         // sibling groups (2^n children of one parent) per lattice block, 0: none
     float p32[GIS_NPARAM];      // derived constants for the FP32 model
     float pr32[GIS_NPARAM];     // their radii: |p32 - exact value|, rounded up
     double p64[GIS_NPARAM];     // derived constants for the FP64 model (same ops as the definition)

@@ -468,6 +468,8 @@ inline void fill_desc(Inst &I)
         const double tb = 2.0 * (lo_err + scale * 4.0 * 5.96e-8);
         D.tmargin[d] = (float)(I.band + tb);
     }
+    D.fresh0 = I.n_live - I.n_fresh;
+    D.sib_groups = sibling_groups(n, I.grid.k_samples);
     const bool lat = lattice_tile(n, I.grid.k_samples, D.n0, D.tile);
     for (int d = 0; d < MAXN; d++) D.ntile[d] = !lat ? 0 : d < n ? (D.n0[d] + D.tile[d] - 1) / D.tile[d] : 1;
     const int k = I.grid.k_samples;
@@ -924,6 +926,17 @@ struct Engine {
                 }
                 groups[{I.dyn.dyn_id, I.dyn.n, I.precision, 0}].push_back({I.tix, 0, tiles * I.nu});
                 cum.prop_flops += sample_ball_flops(I) * points * I.nu;
+            } else if (I.precision == GIS_FP32_RECHECK && I.desc.sib_groups > 0 && I.n_fresh < I.n_nodes &&
+                       I.n_fresh % (1 << I.dyn.n) == 0 && opt.lanes_per_pair == 0) {
+                // fresh children of split cells: shared points among siblings
+                // (lanes = -1 marks the sibling kernel; items are runs of
+                // parents x controls)
+                const int64_t ng = I.n_fresh >> I.dyn.n;
+                const int64_t blocks = (ng + I.desc.sib_groups - 1) / I.desc.sib_groups;
+                groups[{I.dyn.dyn_id, I.dyn.n, I.precision, -1}].push_back({I.tix, 0, blocks * I.nu});
+                double pts = 1;
+                for (int d = 0; d < I.dyn.n; d++) pts *= 2.0 * (I.grid.k_samples - 1) + 1;
+                cum.prop_flops += sample_ball_flops(I) * pts * (double)ng * I.nu;
             } else {
                 const int lanes = I.precision == GIS_FP64_PLAIN ? 1 : lanes_for(I);
                 groups[{I.dyn.dyn_id, I.dyn.n, I.precision, lanes}].push_back({I.tix, first, I.n_fresh * I.nu});
@@ -942,6 +955,8 @@ struct Engine {
                 CK(launch_prop64(dyn, n, d_desc, make_work(g.second, 256), st));
             } else if (lanes == 0) {
                 CK(launch_prop32_lattice(dyn, n, d_desc, make_work(g.second, 1), st));
+            } else if (lanes == -1) {
+                CK(launch_prop32_siblings(dyn, n, d_desc, make_work(g.second, 1), st));
             } else {
                 CK(launch_prop32(dyn, n, lanes, d_desc, make_work(g.second, prop_pairs_per_block(lanes)), st));
             }

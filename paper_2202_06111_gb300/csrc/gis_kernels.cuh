@@ -35,6 +35,9 @@ cudaError_t launch_prop32(int dyn, int n, int lanes, const InstDesc *D, const Wo
 // first build: one block per (tile of root cells, control), items = tiles x controls
 cudaError_t launch_prop32_lattice(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st);
 bool lattice_tile(int n, int k, const int32_t *n0, int32_t *tile);
+// fresh children: one block per (run of sib_groups parents, control)
+cudaError_t launch_prop32_siblings(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st);
+int sibling_groups(int n, int k);
 cudaError_t launch_prop64(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st);
 int prop_pairs_per_block(int lanes);
 // binning: decisions at the finest level, band check, recheck queue

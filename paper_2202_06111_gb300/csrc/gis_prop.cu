@@ -818,6 +818,153 @@ cudaError_t launch_prop32(int dyn, int n, int lanes, const InstDesc *D, const Wo
     return cudaErrorInvalidValue;
 }
 
+// Fresh children after a subdivision: the 2^n children of one parent tile
+// the parent's box, and their k^n lattices share the points on their common
+// faces: (2 (k-1) + 1)^n points per parent instead of 2^n k^n. One block per
+// (run of sib_groups parents, control); as in k_prop32_lat, each point is
+// propagated once into shared memory and each child reduces its own points.
+template <class DY>
+__global__ void __launch_bounds__(PROP_THREADS) k_prop32_sib(const InstDesc *__restrict__ D,
+                                                             const Range *__restrict__ R, int nr)
+{
+    constexpr int N = DY::N;
+    constexpr int NC = 1 << N;
+    constexpr int PMAX = LAT_POINTS / N;
+    __shared__ int s_r;
+    __shared__ float s_p[GIS_NPARAM], s_pr[GIS_NPARAM];
+    __shared__ float s_a[PMAX * N], s_b[PMAX * N];
+    __shared__ uint8_t s_bad[PMAX];
+    if (threadIdx.x == 0) s_r = find_range(R, nr, blockIdx.x);
+    __syncthreads();
+    const Range rg = R[s_r];
+    const InstDesc &I = D[rg.inst];
+    if (threadIdx.x < GIS_NPARAM) {
+        s_p[threadIdx.x] = I.p32[threadIdx.x];
+        s_pr[threadIdx.x] = I.pr32[threadIdx.x];
+    }
+    const int64_t item = rg.first + (blockIdx.x - rg.block_start);   // one item per block
+    const int u = (int)(item % I.nu);
+    const int64_t ngroups = (I.n_live - I.fresh0) >> N;
+    const int64_t g0 = (item / I.nu) * I.sib_groups;
+    const int G = (int)min((int64_t)I.sib_groups, ngroups - g0);
+    const int k1 = I.k - 1, side = 2 * k1 + 1;
+    int pts1 = 1;
+#pragma unroll
+    for (int d = 0; d < N; d++) pts1 *= side;
+    __syncthreads();
+    const MB M{s_p, s_pr, I.m, I.substeps, {I.h32, I.hr32}, {I.hh32, I.hhr32}, {I.h6_32, I.h6r32}};
+    Ball uu[MAXN];
+    for (int j = 0; j < I.m; j++) uu[j] = Ball{I.u32[u * I.m + j], I.ur32[u * I.m + j]};
+    for (int pt = threadIdx.x; pt < G * pts1; pt += PROP_THREADS) {
+        const int g = pt / pts1;
+        int r = pt - g * pts1;
+        const int node0 = I.live[I.fresh0 + ((g0 + g) << N)];   // child 0: index 2 * parent index
+        const int L = I.lvl[node0];
+        Ball x[N], y[N];
+#pragma unroll
+        for (int d = N - 1; d >= 0; d--) {
+            const int gd = r % side;
+            r /= side;
+            const int b = min(gd / k1, 1);
+            const int j = gd - b * k1;
+            const int idx = I.idx[d][node0] + b;
+            const Ball tt = badd(bexact((float)idx), Ball{I.frac32[j], I.fracr32[j]});
+            x[d] = bfma(Ball{I.w32[L][d], I.wr32[L][d]}, tt, Ball{I.lo32[d], I.lor32[d]});
+        }
+        stepB<DY>(M, x, uu, y);
+        bool bad = false;
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            const Ball yb = bfinal(y[d]);
+            const float a = __fsub_rd(yb.m, yb.r), b = __fadd_ru(yb.m, yb.r);
+            bad = bad || !(fabsf(a) <= FLT_MAX && fabsf(b) <= FLT_MAX);
+            s_a[pt * N + d] = a;
+            s_b[pt * N + d] = b;
+        }
+        s_bad[pt] = bad;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < G * NC; c += PROP_THREADS) {
+        const int g = c / NC, cc = c - g * NC;
+        const int node = I.live[I.fresh0 + ((g0 + g) << N) + cc];
+        float lomin[N], himin[N], lomax[N], himax[N];
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            lomin[d] = himin[d] = INFINITY;
+            lomax[d] = himax[d] = -INFINITY;
+        }
+        bool bad = false;
+        for (int s = 0; s < I.S; s++) {
+            int rs = s, pt = 0;
+            int jd[N];                        // digit d of s: the sample offset along d
+#pragma unroll
+            for (int d = 0; d < N; d++) {
+                jd[d] = rs % I.k;
+                rs /= I.k;
+            }
+#pragma unroll
+            for (int d = 0; d < N; d++) pt = pt * side + ((cc >> (N - 1 - d)) & 1) * k1 + jd[d];
+            pt += g * pts1;
+            bad = bad || s_bad[pt];
+#pragma unroll
+            for (int d = 0; d < N; d++) {
+                const float a = s_a[pt * N + d], b = s_b[pt * N + d];
+                lomin[d] = fminf(lomin[d], a);
+                himin[d] = fminf(himin[d], b);
+                lomax[d] = fmaxf(lomax[d], a);
+                himax[d] = fmaxf(himax[d], b);
+            }
+        }
+        const int64_t q = (int64_t)node * I.nu + u;
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            I.box32[q * 4 * N + 2 * d] = lomin[d];
+            I.box32[q * 4 * N + 2 * d + 1] = himin[d];
+            I.box32[q * 4 * N + 2 * (N + d)] = lomax[d];
+            I.box32[q * 4 * N + 2 * (N + d) + 1] = himax[d];
+        }
+        I.exact[q] = bad ? EX_NF32 : 0;
+    }
+}
+
+template <class DY>
+static cudaError_t prop32_sib_l(const InstDesc *D, const WorkList &w, cudaStream_t st)
+{
+    k_prop32_sib<DY><<<(unsigned)w.n_blocks, PROP_THREADS, 0, st>>>(D, w.d_ranges, w.n_ranges); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prop32_siblings(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st)
+{
+    if (w.n_blocks == 0) return cudaSuccess;
+    switch (dyn) {
+    case GIS_DYN_VDP: return prop32_sib_l<DynVdp>(D, w, st);
+    case GIS_DYN_CSTR_DL: return prop32_sib_l<DynCstrDl>(D, w, st);
+    case GIS_DYN_CARTPOLE: return prop32_sib_l<DynCartpole>(D, w, st);
+    case GIS_DYN_CSTR_PAPER: return prop32_sib_l<DynCstrPaper>(D, w, st);
+    case GIS_DYN_LINMAP:
+        switch (n) {
+        case 1: return prop32_sib_l<DynLin<1>>(D, w, st);
+        case 2: return prop32_sib_l<DynLin<2>>(D, w, st);
+        case 3: return prop32_sib_l<DynLin<3>>(D, w, st);
+        case 4: return prop32_sib_l<DynLin<4>>(D, w, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Parents per sibling-lattice block: their points fit the block's shared
+// memory and their children one pass of the block; 0 if one parent's points
+// do not fit.
+int sibling_groups(int n, int k)
+{
+    if (k < 2) return 0;
+    int64_t pts = 1;
+    for (int d = 0; d < n; d++) pts *= 2 * (k - 1) + 1;
+    const int64_t g = std::min<int64_t>((LAT_POINTS / n) / pts, PROP_THREADS >> n);
+    return (int)std::max<int64_t>(g, 0);
+}
+
 template <class DY>
 static cudaError_t prop32_lat_l(const InstDesc *D, const WorkList &w, cudaStream_t st)
 {
