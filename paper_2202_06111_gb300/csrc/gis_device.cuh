@@ -119,8 +119,10 @@ __device__ __forceinline__ int find_range(const Range *__restrict__ R, int nr, i
 // with round-to-nearest, radii with upward rounding: the rounding error of a
 // midpoint is at most 2^-24 |x| <= 2^-24 (1 + 2^-24) |m| (bounded here by
 // 2^-24 (1 + 2^-23) |m| + 1e-37 to cover underflow); expf / sinf / cosf are
-// within 2 ulp (CUDA's documented bounds, bounded here by 2^-21 |m|); FP32
-// division rounds correctly.
+// within 2 ulp of the exact function (CUDA's documented bounds for these
+// arguments); an ulp of y is at most 2^-23 |y|, so 2 ulp is at most 2^-22 of
+// the result, bounded here by 2^-22 (1 + 2^-16) |m|; FP32 division rounds
+// correctly.
 // ---------------------------------------------------------------------------
 struct Ball {
     float m, r;
@@ -128,7 +130,7 @@ struct Ball {
 
 constexpr float B_U = 5.9604652e-08f;    // 2^-24 (1 + 2^-23): round-to-nearest error over |fl(x)|
 constexpr float B_ETA = 1.0e-37f;
-constexpr float B_F = 4.7683716e-07f;    // 2^-21, library function error
+constexpr float B_F = 2.3843e-07f;       // 2^-22 (1 + 2^-16), library function error
 
 __device__ __forceinline__ float b_rerr(float m) { return __fmaf_ru(fabsf(m), B_U, B_ETA); }
 __device__ __forceinline__ Ball bexact(float v) { return {v, 0.0f}; }

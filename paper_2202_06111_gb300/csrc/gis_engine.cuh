@@ -459,13 +459,15 @@ inline void fill_desc(Inst &I)
         const double wf = D.w64[I.Lf][d];
         D.invwf32[d] = (float)(1.0 / wf);
         D.iw64[d] = 1.0 / wf;
-        // FP32 t = (y - lo32) * invw for |y| within the box of X widened by its
-        // size: rounding of lo, of the difference, of the product and of 1/w,
-        // bounded in Lf cell widths (x2 margin), plus the optional band.
+        // FP32 t = fl(fl(y - lo32) * invw) against t = (y - lo) / w: the
+        // difference, the product and 1/w each round within 2^-24, and lo32 is
+        // off lo by lo_err cells; a decision can change only where |t| <= Nf + 2
+        // (beyond, both sides clamp alike), so the error is at most
+        // 3 * 2^-24 * (Nf + 4) + lo_err cells (x1.25 margin, which also covers
+        // the FP64 decision's own rounding), plus the optional band.
         const double Nf = (double)((int64_t)D.n0[d] << I.Lf);
         const double lo_err = std::fabs((double)D.lo32[d] - D.lo[d]) / wf;
-        const double scale = 2.0 * std::max(std::fabs(D.lo[d]), std::fabs(D.hi[d])) / wf + Nf + 2.0;
-        const double tb = 2.0 * (lo_err + scale * 4.0 * 5.96e-8);
+        const double tb = 1.25 * (lo_err + 3.0 * 5.9604645e-8 * (Nf + 4.0));
         D.tmargin[d] = (float)(I.band + tb);
     }
     D.fresh0 = I.n_live - I.n_fresh;
@@ -620,6 +622,31 @@ struct Engine {
         mem.free_all();
         if (st) cudaStreamSynchronize(st);
         else cudaDeviceSynchronize();
+        if (pin) cudaFreeHost(pin);
+    }
+
+    // pinned host staging for read-backs, so that several copies share one sync:
+    // [0, 256) control words, then per-problem arrays
+    unsigned char *pin = nullptr;
+    size_t c_pin = 0;
+    unsigned char *pinned(size_t bytes)
+    {
+        if (bytes > c_pin) {
+            if (pin) {
+                CK(cudaStreamSynchronize(st));
+                cudaFreeHost(pin);
+                pin = nullptr;
+            }
+            const size_t c = std::max<size_t>(4096, 2 * bytes);
+            if (cudaMallocHost((void **)&pin, c) != cudaSuccess) {
+                cudaGetLastError();
+                pin = nullptr;
+                c_pin = 0;
+                throw Error{GIS_ENOMEM, "cudaMallocHost of the read-back staging"};
+            }
+            c_pin = c;
+        }
+        return pin;
     }
 
     void sync()
@@ -1065,11 +1092,14 @@ struct Engine {
         CK(launch_scan_i32(ccnt, coff, NL, scratch, st));
         CK(launch_scan_i32(rcnt, roff, NL, scratch, st));
         timer.end();
-        int64_t hEc = 0;
-        int32_t hq[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        CK(cudaMemcpyAsync(&hEc, coff + NL, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(hq, ctl + 6, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        unsigned char *hp = pinned(256);
+        CK(cudaMemcpyAsync(hp, coff + NL, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hp + 8, ctl + 6, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         sync();
+        int64_t hEc = 0;
+        int32_t hq[8];
+        std::memcpy(&hEc, hp, sizeof(hEc));
+        std::memcpy(hq, hp + 8, sizeof(hq));
         last_recheck = hq[0];
         if (last_recheck > 0) {
             cum.cum_recheck_samples += hq[4];
@@ -1176,15 +1206,29 @@ struct Engine {
         if (sync_now) finish_prune();
     }
 
-    // read the prune's counts back (after a stream sync)
+    // read the prune's counts back: enqueue the copies into the pinned staging
+    // (control words at 64, per-problem counts at 256), then, after a stream
+    // sync, take them
+    void prune_readback_enqueue()
+    {
+        unsigned char *hp = pinned(256 + 8 * step.size());
+        CK(cudaMemcpyAsync(hp + 64, ctl, 10 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hp + 256, kept_i64, step.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    }
     void finish_prune()
+    {
+        if (!prune_pending) return;
+        prune_readback_enqueue();
+        sync();
+        prune_readback_take();
+    }
+    void prune_readback_take()
     {
         if (!prune_pending) return;
         int32_t hc[10];
         std::vector<int64_t> kept(step.size());
-        CK(cudaMemcpyAsync(hc, ctl, 10 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(kept.data(), kept_i64, step.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        sync();
+        std::memcpy(hc, pin + 64, sizeof(hc));
+        std::memcpy(kept.data(), pin + 256, step.size() * sizeof(int64_t));
         prune_pending = false;
         if (hc[4] != 0) throw Error{(gis_status)hc[4], "prune: round or wait limit reached"};
         last_rounds = hc[5];
@@ -1239,13 +1283,20 @@ struct Engine {
         CK(cudaMemcpyAsync(d_be, be.data(), be.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
         CK(launch_inst_totals(pscan, d_be, (int)cont.size(), d_tot, st));
         timer.end();
-        finish_prune();
+        // the prune's counts, the split totals and the levels in one sync
+        const bool pp = prune_pending;
+        const size_t o_tot = 256 + 8 * step.size(), o_max = o_tot + 8 * cont.size();
+        pinned(o_max + 4 * step.size());
+        if (pp) prune_readback_enqueue();
+        if (!cont.empty())
+            CK(cudaMemcpyAsync(pin + o_tot, d_tot, cont.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(pin + o_max, inst_i32, step.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        sync();
         std::vector<int64_t> tot(cont.size());
         std::vector<int32_t> maxl(step.size());
-        if (!cont.empty())
-            CK(cudaMemcpyAsync(tot.data(), d_tot, cont.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(maxl.data(), inst_i32, step.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        sync();
+        std::memcpy(tot.data(), pin + o_tot, cont.size() * sizeof(int64_t));
+        std::memcpy(maxl.data(), pin + o_max, step.size() * sizeof(int32_t));
+        if (pp) prune_readback_take();
         // grow, then split
         std::vector<SplitInst> si(step.size());
         last_split = 0;

@@ -343,7 +343,7 @@ __device__ __forceinline__ bool decide_approx(const InstDesc &I, int e, float a,
     const float tA = (a - I.lo32[d]) * I.invwf32[d];
     const float tB = (b - I.lo32[d]) * I.invwf32[d];
     const float Nf = (float)(I.n0[d] << I.Lf);
-    float k0 = ceilf(tA - I.tmargin[d]), k1 = floorf(tB + I.tmargin[d]);
+    float k0 = ceilf(__fsub_rd(tA, I.tmargin[d])), k1 = floorf(__fadd_ru(tB, I.tmargin[d]));
     k0 = fmaxf(k0, 0.0f);
     k1 = fminf(k1, Nf);
     if (!(k0 > k1)) return false;       // also catches NaN
