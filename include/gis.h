@@ -105,10 +105,14 @@ typedef struct {
     int32_t rule;           /* GIS_RULE_*                                         */
     int32_t precision;      /* GIS_FP64_PLAIN | GIS_FP32_RECHECK                   */
     double band;            /* extra recheck margin, finest-level cell widths (>= 0) */
-    int32_t lanes_per_pair; /* propagation lanes per pair 1,2,4,8,16,32; 0 = auto  */
+    int32_t lanes_per_pair; /* propagation lanes per pair 1,2,4,8,16; 0 = auto     */
     int32_t timing;         /* 1: record per-kernel CUDA-event times into stats    */
     int64_t max_device_bytes; /* 0 = no limit; else allocations beyond -> ENOMEM   */
     int64_t round_limit;    /* prune rounds before GIS_ETIMEOUT; 0 = 1<<30         */
+    int32_t enclosure_store; /* FP64 enclosures of rechecked extremes: 0 = auto
+                                (dense while the roots' store is under 1 GB),
+                                1 = dense per (cell, control), 2 = compact      */
+    int32_t reserved;
 } gis_options;
 
 /* One live cell: box = prod [lo + idx w_level, lo + (idx+1) w_level],

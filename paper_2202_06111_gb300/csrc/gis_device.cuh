@@ -90,11 +90,40 @@ struct InstDesc {
     // ---- image-box cache, indexed node * nu + u ----
     float *box32;               // [.. x 2n x 2]: per extreme e (ymin_0..ymin_{n-1}, ymax_0..)
                                 // a certified interval [lo, hi] that holds its exact value
-    double *box64;              // [.. x 2n x 2]: an interval [lo, hi] that holds the FP64
-                                // value of extreme e where bit e of `exact` is set (lo == hi:
-                                // the FP64 value itself)
     uint16_t *exact;
+    // ---- FP64 enclosures of extremes: an entry is 2n intervals [lo, hi] (4n doubles)
+    // holding the FP64 value of extreme e where bit e of `exact` is set (lo == hi: the
+    // FP64 value itself). Dense (entry = node * nu + u) for FP64-plain problems; else
+    // a compact store: bxi gives the pair's entry (-1: none), bx_n counts entries used.
+    double *bx;
+    int32_t *bxi;
+    int32_t *bx_n;
+    int64_t bx_cap;             // entries allocated
+    int32_t bx_dense;
 };
+
+// The FP64 enclosures of pair q (node * nu + u): read (the pair has an entry
+// whenever a bit of exact is set), or taken for writing (a new entry if none;
+// nullptr and *err = GIS_EBOUNDS if the store is full).
+__device__ __forceinline__ const double *bx_get(const InstDesc &I, int64_t q)
+{
+    const int64_t i = I.bx_dense ? q : (int64_t)I.bxi[q];
+    return I.bx + i * 4 * I.n;
+}
+__device__ __forceinline__ double *bx_take(const InstDesc &I, int64_t q, int32_t *err)
+{
+    if (I.bx_dense) return I.bx + q * 4 * I.n;
+    int i = I.bxi[q];
+    if (i < 0) {
+        i = atomicAdd(I.bx_n, 1);
+        if (i >= I.bx_cap) {
+            atomicExch(err, GIS_EBOUNDS);
+            return nullptr;
+        }
+        I.bxi[q] = i;
+    }
+    return I.bx + (int64_t)i * 4 * I.n;
+}
 
 __device__ __forceinline__ int find_range(const Range *__restrict__ R, int nr, int64_t b)
 {

@@ -225,8 +225,13 @@ struct Inst {
     int cur = 0;
     size_t cap_nodes = 0, cap_live[2] = {0, 0}, cap_pairs = 0;
     float *box32 = nullptr;
-    double *box64 = nullptr;
     uint16_t *exact = nullptr;
+    // FP64 enclosures: dense (FP64 plain) or a compact store indexed by bxi
+    double *bx = nullptr;
+    int32_t *bxi = nullptr, *bx_n = nullptr;
+    size_t c_bx = 0;            // entries
+    int64_t bx_bound = 0;       // entries possibly in use (host upper bound)
+    bool bx_dense = false;
     float *u32 = nullptr, *ur32 = nullptr, *udd = nullptr;
     double *u64 = nullptr;
     bool udd_ok = true;
@@ -503,8 +508,12 @@ inline void fill_desc(Inst &I)
     D.slot = I.slot;
     D.live = I.live[I.cur];
     D.box32 = I.box32;
-    D.box64 = I.box64;
     D.exact = I.exact;
+    D.bx = I.bx;
+    D.bxi = I.bxi;
+    D.bx_n = I.bx_n;
+    D.bx_cap = (int64_t)I.c_bx;
+    D.bx_dense = I.bx_dense ? 1 : 0;
 }
 
 // ---------------------------------------------------------------- engine ---
@@ -599,6 +608,10 @@ struct Engine {
     {
         if (o) opt = *o;
         else gis_default_options(&opt);
+        if (opt.enclosure_store < 0 || opt.enclosure_store > 2) throw Error{GIS_EINVAL, "enclosure_store: 0, 1 or 2"};
+        if (opt.lanes_per_pair != 0 && opt.lanes_per_pair != 1 && opt.lanes_per_pair != 2 && opt.lanes_per_pair != 4 &&
+            opt.lanes_per_pair != 8 && opt.lanes_per_pair != 16)
+            throw Error{GIS_EINVAL, "lanes_per_pair: 0 (auto), 1, 2, 4, 8 or 16"};
         int ndev = 0;
         if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
             cudaGetLastError();
@@ -670,9 +683,21 @@ struct Engine {
             alloc_nodes(*I, R);
             mem.grow(I->live[0], I->cap_live[0], R, 0);
             mem.grow(I->box32, I->cap_pairs, (size_t)R * I->nu * 4 * dyn.n, 0);
-            size_t c64 = 0, cex = 0;
-            mem.grow(I->box64, c64, (size_t)R * I->nu * 4 * dyn.n, 0);
+            size_t cex = 0, cxi = 0;
             mem.grow(I->exact, cex, (size_t)R * I->nu, 0);
+            // dense enclosures while they are small (no store to manage); a compact
+            // store when the roots' dense store alone would pass 1 GB
+            I->bx_dense = precision == GIS_FP64_PLAIN ||
+                          (opt.enclosure_store == 0 && (double)R * I->nu * 4 * dyn.n * sizeof(double) <= 1e9) ||
+                          opt.enclosure_store == 1;
+            if (I->bx_dense) {
+                mem.grow(I->bx, I->c_bx, (size_t)R * I->nu * 4 * dyn.n, 0);
+                I->c_bx = (size_t)R * I->nu;
+            } else {
+                mem.grow(I->bxi, cxi, (size_t)R * I->nu, 0);
+                I->bx_n = (int32_t *)mem.alloc(sizeof(int32_t));
+                CK(cudaMemsetAsync(I->bx_n, 0, sizeof(int32_t), st));
+            }
             I->cap_pairs = (size_t)R * I->nu;
             std::vector<float> u32(I->u.begin(), I->u.end()), ur32(I->u.size());
             for (size_t j = 0; j < I->u.size(); j++) ur32[j] = radius_of(I->u[j], u32[j]);
@@ -720,10 +745,17 @@ struct Engine {
             alloc_nodes(I, target);
             const size_t n2 = (size_t)2 * I.dyn.n;
             const size_t keep = (size_t)I.n_nodes * I.nu;
-            size_t c32 = I.cap_pairs * 2 * n2, c64 = I.cap_pairs * 2 * n2, cex = I.cap_pairs;
+            size_t c32 = I.cap_pairs * 2 * n2, cex = I.cap_pairs;
             mem.grow(I.box32, c32, I.cap_nodes * I.nu * 2 * n2, keep * 2 * n2);
-            mem.grow(I.box64, c64, I.cap_nodes * I.nu * 2 * n2, keep * 2 * n2);
             mem.grow(I.exact, cex, I.cap_nodes * I.nu, keep);
+            if (I.bx_dense) {
+                size_t c64 = I.c_bx * 2 * n2;
+                mem.grow(I.bx, c64, I.cap_nodes * I.nu * 2 * n2, keep * 2 * n2);
+                I.c_bx = I.cap_nodes * I.nu;
+            } else {
+                size_t cxi = I.cap_pairs;
+                mem.grow(I.bxi, cxi, I.cap_nodes * I.nu, keep);
+            }
             I.cap_pairs = I.cap_nodes * I.nu;
         }
         const int nx = 1 - I.cur;
@@ -737,11 +769,13 @@ struct Engine {
         mem.free(I.lvl); mem.free(I.state); mem.free(I.child); mem.free(I.slot);
         for (int d = 0; d < MAXN; d++) { mem.free(I.idx[d]); I.idx[d] = nullptr; }
         mem.free(I.live[0]); mem.free(I.live[1]);
-        mem.free(I.box32); mem.free(I.box64); mem.free(I.exact);
+        mem.free(I.box32); mem.free(I.exact); mem.free(I.bx); mem.free(I.bxi); mem.free(I.bx_n);
         mem.free(I.u32); mem.free(I.ur32); mem.free(I.u64); mem.free(I.udd);
         I.lvl = I.state = nullptr;
         I.child = I.slot = I.live[0] = I.live[1] = nullptr;
-        I.box32 = nullptr; I.box64 = nullptr; I.exact = nullptr;
+        I.box32 = nullptr; I.exact = nullptr; I.bx = nullptr; I.bxi = I.bx_n = nullptr;
+        I.c_bx = 0;
+        I.bx_bound = 0;
         I.u32 = I.ur32 = I.udd = nullptr; I.u64 = nullptr;
         I.cap_nodes = I.cap_live[0] = I.cap_live[1] = I.cap_pairs = 0;
         I.active = false;
@@ -1024,6 +1058,23 @@ struct Engine {
                 nq = hq0;
             }
             if (nq > 0) {
+                // room in the compact enclosure stores: at most one new entry per
+                // rechecked pair of each problem
+                bool moved = false;
+                for (int i : ids) {
+                    Inst &I = *inst[i];
+                    if (I.precision != GIS_FP32_RECHECK || I.bx_dense) continue;
+                    const int64_t need = I.bx_bound + std::min<int64_t>(I.n_live * I.nu, nq);
+                    if ((size_t)need > I.c_bx) {
+                        size_t c = I.c_bx * 4 * I.dyn.n;
+                        const size_t cap = std::max<size_t>((size_t)need, I.c_bx + I.c_bx / 2);
+                        mem.grow(I.bx, c, cap * 4 * I.dyn.n, (size_t)I.bx_bound * 4 * I.dyn.n);
+                        I.c_bx = cap;
+                        moved = true;
+                    }
+                    I.bx_bound = need;
+                }
+                if (moved) upload_desc();
                 timer.begin(PH_RECHECK);
                 mem.ensure(rc_mnk, c_rc_mnk, (size_t)nq * MAXN);
                 mem.ensure(rc_mxk, c_rc_mxk, (size_t)nq * MAXN);
@@ -1035,7 +1086,7 @@ struct Engine {
                 CK(cudaMemsetAsync(ctl + 10, 0, 2 * sizeof(int32_t), st));
                 CK(cudaMemsetAsync(ctl + 16, 0, sizeof(int32_t), st));
                 RecheckArgs ra{d_desc, rq, ctl + 6, nq, rc_mnk, rc_mxk, rc_ddk, rc_need64, ctl + 11, rc_bad,
-                               rc_cand, ctl + 10, nq * Smax, rc_cand64, ctl + 16, Smax, rng, pflag};
+                               ctl + 7, rc_cand, ctl + 10, nq * Smax, rc_cand64, ctl + 16, Smax, rng, pflag};
                 // candidates; double-word enclosures and their decisions; FP64 for the rest
                 for (auto &k : kinds) CK(launch_recheck(RC_CAND, k.first.first, k.first.second, ra, st));
                 for (auto &k : kinds) CK(launch_recheck(RC_DD, k.first.first, k.first.second, ra, st));
@@ -1105,7 +1156,7 @@ struct Engine {
             cum.cum_recheck_samples += hq[4];
             cum.cum_recheck_fp64 += hq[5];
         }
-        if (hq[1] != 0) throw Error{GIS_EBOUNDS, "subdivision tree descent overflow"};
+        if (hq[1] != 0) throw Error{GIS_EBOUNDS, "descent stack, previous slot or enclosure store out of bounds"};
         unsigned long long hpe = 0;
         std::memcpy(&hpe, hq + 6, sizeof(hpe));
         E = (int64_t)hpe;

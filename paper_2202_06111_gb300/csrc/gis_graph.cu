@@ -533,7 +533,8 @@ __global__ void __launch_bounds__(256) k_export_boxes(const InstDesc *__restrict
         if (b32) b32[lp * 2 * N + e] = f;
         double v = (double)f;
         if ((x >> e) & 1) {
-            const double a = I.box64[q * 4 * N + 2 * e], b = I.box64[q * 4 * N + 2 * e + 1];
+            const double *bq = bx_get(I, q);
+            const double a = bq[2 * e], b = bq[2 * e + 1];
             v = a == b ? a : 0.5 * a + 0.5 * b;
             if (a == b) xb |= 1u << e;
         }

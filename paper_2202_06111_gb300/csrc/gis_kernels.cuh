@@ -55,6 +55,7 @@ struct RecheckArgs {
     int32_t *need64;             // [item] the pair is computed in FP64
     int32_t *n64;                // count of pairs computed in FP64
     int32_t *bad;                // [item] an FP64 sample was not finite
+    int32_t *err;                // GIS_EBOUNDS if an enclosure store is full
     int2 *cand;                  // (item, sample)
     int32_t *ncand;
     int64_t ccap;

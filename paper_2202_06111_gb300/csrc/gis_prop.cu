@@ -125,7 +125,10 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop32(const InstDesc *__restr
             I.box32[q * 4 * N + 2 * e] = a;
             I.box32[q * 4 * N + 2 * e + 1] = b;
         }
-        if (lane == 0) I.exact[q] = bad ? EX_NF32 : 0;
+        if (lane == 0) {
+            I.exact[q] = bad ? EX_NF32 : 0;
+            if (!I.bx_dense) I.bxi[q] = -1;     // compact store: no entry yet
+        }
     }
 }
 
@@ -249,6 +252,7 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop32_lat(const InstDesc *__r
             I.box32[q * 4 * N + 2 * (N + d) + 1] = himax[d];
         }
         I.exact[q] = bad ? EX_NF32 : 0;
+        if (!I.bx_dense) I.bxi[q] = -1;     // compact store: no entry yet
     }
 }
 
@@ -296,8 +300,9 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop64(const InstDesc *__restr
     const int64_t q = (int64_t)node * I.nu + u;
 #pragma unroll
     for (int d = 0; d < N; d++) {
-        I.box64[q * 4 * N + 2 * d] = I.box64[q * 4 * N + 2 * d + 1] = mn[d];
-        I.box64[q * 4 * N + 2 * (N + d)] = I.box64[q * 4 * N + 2 * (N + d) + 1] = mx[d];
+        double *b = I.bx + q * 4 * N;              // FP64 plain: dense store
+        b[2 * d] = b[2 * d + 1] = mn[d];
+        b[2 * (N + d)] = b[2 * (N + d) + 1] = mx[d];
         I.box32[q * 4 * N + 2 * d] = __double2float_rd(mn[d]);
         I.box32[q * 4 * N + 2 * d + 1] = __double2float_ru(mn[d]);
         I.box32[q * 4 * N + 2 * (N + d)] = __double2float_rd(mx[d]);
@@ -415,8 +420,8 @@ __global__ void __launch_bounds__(256) k_bin(const InstDesc *__restrict__ D, con
 #pragma unroll
         for (int e = 0; e < 2 * N; e++) {
             if ((ex >> e) & 1) {
-                if (!decide_enc<N>(I, e, I.box64[q * 4 * N + 2 * e], I.box64[q * 4 * N + 2 * e + 1], out[e], inx))
-                    m64 |= 1u << e;
+                const double *b = bx_get(I, q);
+                if (!decide_enc<N>(I, e, b[2 * e], b[2 * e + 1], out[e], inx)) m64 |= 1u << e;
             } else if (!decide_approx<N>(I, e, I.box32[q * 4 * N + 2 * e], I.box32[q * 4 * N + 2 * e + 1], out[e],
                                          inx)) {
                 mdd |= 1u << e;
@@ -608,7 +613,8 @@ template <int N>
 __global__ void __launch_bounds__(256) k_rc_mid(const InstDesc *__restrict__ D, const int2 *__restrict__ items,
                                                 const int32_t *__restrict__ count, int64_t qcap,
                                                 const long long *__restrict__ ddk, int32_t *__restrict__ need64,
-                                                int32_t *__restrict__ rng, uint8_t *__restrict__ pflag)
+                                                int32_t *__restrict__ rng, uint8_t *__restrict__ pflag,
+                                                int32_t *__restrict__ err)
 {
     constexpr unsigned FULL = (1u << (2 * N)) - 1u;
     const int total = (int)min((int64_t)*count, qcap);
@@ -622,13 +628,15 @@ __global__ void __launch_bounds__(256) k_rc_mid(const InstDesc *__restrict__ D, 
         const int ls = (int)(lp / I.nu);
         const int u = (int)(lp - (int64_t)ls * I.nu);
         const int64_t q = (int64_t)I.live[ls] * I.nu + u;
+        double *bq = bx_take(I, q, err);
+        if (!bq) continue;
         unsigned ex = I.exact[q];
 #pragma unroll
         for (int e = 0; e < 2 * N; e++) {
             if (!((mdd >> e) & 1)) continue;
             const long long *k = ddk + ((int64_t)it * MAXN + e % N) * 4 + (e < N ? 0 : 2);
-            I.box64[q * 4 * N + 2 * e] = dkey_inv(k[0]);
-            I.box64[q * 4 * N + 2 * e + 1] = dkey_inv(k[1]);
+            bq[2 * e] = dkey_inv(k[0]);
+            bq[2 * e + 1] = dkey_inv(k[1]);
             ex |= 1u << e;
         }
         I.exact[q] = (uint16_t)ex;
@@ -637,7 +645,7 @@ __global__ void __launch_bounds__(256) k_rc_mid(const InstDesc *__restrict__ D, 
 #pragma unroll
         for (int e = 0; e < 2 * N; e++) {
             if ((ex >> e) & 1)
-                done = done && decide_enc<N>(I, e, I.box64[q * 4 * N + 2 * e], I.box64[q * 4 * N + 2 * e + 1], out[e], inx);
+                done = done && decide_enc<N>(I, e, bq[2 * e], bq[2 * e + 1], out[e], inx);
             else
                 done = done && decide_approx<N>(I, e, I.box32[q * 4 * N + 2 * e], I.box32[q * 4 * N + 2 * e + 1], out[e], inx);
         }
@@ -729,7 +737,8 @@ __global__ void __launch_bounds__(256) k_rc_final(const InstDesc *__restrict__ D
                                                   const long long *__restrict__ mxk,
                                                   const int32_t *__restrict__ need64,
                                                   const int32_t *__restrict__ bad, int32_t *__restrict__ rng,
-                                                  uint8_t *__restrict__ pflag, int32_t *__restrict__ n64)
+                                                  uint8_t *__restrict__ pflag, int32_t *__restrict__ n64,
+                                                  int32_t *__restrict__ err)
 {
     constexpr unsigned FULL = (1u << (2 * N)) - 1u;
     const int total = (int)min((int64_t)*count, qcap);
@@ -753,12 +762,14 @@ __global__ void __launch_bounds__(256) k_rc_final(const InstDesc *__restrict__ D
         }
         const unsigned upd = all64 ? FULL : mask;
         unsigned ex = I.exact[q] & FULL;
+        double *bq = bx_take(I, q, err);
+        if (!bq) continue;
 #pragma unroll
         for (int e = 0; e < 2 * N; e++) {
             if (!((upd >> e) & 1)) continue;
             const int d = e % N;
             const double v = e < N ? dkey_inv(mnk[(int64_t)it * MAXN + d]) : dkey_inv(mxk[(int64_t)it * MAXN + d]);
-            I.box64[q * 4 * N + 2 * e] = I.box64[q * 4 * N + 2 * e + 1] = v;
+            bq[2 * e] = bq[2 * e + 1] = v;
             ex |= 1u << e;
         }
         I.exact[q] = (uint16_t)ex;
@@ -769,7 +780,7 @@ __global__ void __launch_bounds__(256) k_rc_final(const InstDesc *__restrict__ D
             // every extreme is decided: those in `upd` hold their FP64 value, the
             // others were decided before (FP32 or an enclosure)
             if ((ex >> e) & 1)
-                decide_enc<N>(I, e, I.box64[q * 4 * N + 2 * e], I.box64[q * 4 * N + 2 * e + 1], out[e], inx);
+                decide_enc<N>(I, e, bq[2 * e], bq[2 * e + 1], out[e], inx);
             else
                 decide_approx<N>(I, e, I.box32[q * 4 * N + 2 * e], I.box32[q * 4 * N + 2 * e + 1], out[e], inx);
         }
@@ -924,6 +935,7 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop32_sib(const InstDesc *__r
             I.box32[q * 4 * N + 2 * (N + d) + 1] = himax[d];
         }
         I.exact[q] = bad ? EX_NF32 : 0;
+        if (!I.bx_dense) I.bxi[q] = -1;     // compact store: no entry yet
     }
 }
 
@@ -1101,10 +1113,10 @@ static cudaError_t recheck_n(int phase, const RecheckArgs &a, cudaStream_t st)
 {
     const int g = sm_count() * 8;
     if (phase == RC_MID)
-        k_rc_mid<N><<<g, 256, 0, st>>>(a.D, a.items, a.count, a.qcap, a.ddk, a.need64, a.rng, a.pflag);
+        k_rc_mid<N><<<g, 256, 0, st>>>(a.D, a.items, a.count, a.qcap, a.ddk, a.need64, a.rng, a.pflag, a.err);
     else
         k_rc_final<N><<<g, 256, 0, st>>>(a.D, a.items, a.count, a.qcap, a.mnk, a.mxk, a.need64, a.bad, a.rng,
-                                         a.pflag, a.n64);
+                                         a.pflag, a.n64, a.err);
     note_launch();
     return cudaGetLastError();
 }

@@ -52,7 +52,7 @@ class gis_controls(C.Structure):
 class gis_options(C.Structure):
     _fields_ = [("rule", C.c_int32), ("precision", C.c_int32), ("band", C.c_double),
                 ("lanes_per_pair", C.c_int32), ("timing", C.c_int32), ("max_device_bytes", C.c_int64),
-                ("round_limit", C.c_int64)]
+                ("round_limit", C.c_int64), ("enclosure_store", C.c_int32), ("reserved", C.c_int32)]
 
 
 class gis_cell(C.Structure):

@@ -71,3 +71,17 @@ def test_doubling_map_ties_reach_fp64(gis):
     res = run_both(gis, prob, 1)
     rc, r64, _ = _totals(res)
     assert r64 > 0
+
+
+@pytest.mark.parametrize("store", [1, 2])
+def test_enclosure_store_dense_and_compact(gis, store):
+    """The FP64 enclosures of rechecked extremes, dense per (cell, control) or in
+    the compact store, give the same graphs (band widens the recheck)."""
+    res = run_both(gis, dict(W.cstr_256(levels=2, n0=23), rule="inner"), 2, band=0.2, enclosure_store=store)
+    rc, _, _ = _totals(res)
+    assert rc > 0
+
+
+def test_cartpole_compact_store(gis):
+    """4-D with the compact store (the default for large grids)."""
+    run_both(gis, dict(W.cartpole_48(levels=1, n0=6), rule="outer"), 1, band=0.1, enclosure_store=2)
