@@ -156,6 +156,47 @@ __device__ __forceinline__ uint32_t ctl_mask(const CtlBox<N> *__restrict__ box, 
     return m & mask;
 }
 
+// Children of a split node (level L, index idx; children at L + 1, shift sh
+// = Lf - L - 1): per dimension d and half b, the controls (bits of m) whose
+// range holds child index 2 idx_d + b. A child's mask is the AND over the
+// dimensions of its halves' masks: 2n range tests per control instead of 2^n n.
+template <int N>
+__device__ __forceinline__ void child_masks(const CtlBox<N> *__restrict__ box, int nu, uint32_t m, const int *idx,
+                                            int sh, uint32_t (*md)[2])
+{
+    int e0[N], e1[N], e2[N];                       // child corners at the finest level
+#pragma unroll
+    for (int d = 0; d < N; d++) {
+        e0[d] = (2 * idx[d]) << sh;
+        e1[d] = (2 * idx[d] + 1) << sh;
+        e2[d] = (2 * idx[d] + 2) << sh;
+        md[d][0] = md[d][1] = 0;
+    }
+    for (int u = 0; u < nu; u++) {
+        const CtlBox<N> b = box[u];
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            const int c = b.cf[2 * d], f = b.cf[2 * d + 1];
+            md[d][0] |= (uint32_t)(e1[d] >= c && e0[d] <= f) << u;
+            md[d][1] |= (uint32_t)(e2[d] >= c && e1[d] <= f) << u;
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < N; d++) {
+        md[d][0] &= m;
+        md[d][1] &= m;
+    }
+}
+
+template <int N>
+__device__ __forceinline__ uint32_t child_mask(const uint32_t (*md)[2], int cc)
+{
+    uint32_t r = 0xffffffffu;
+#pragma unroll
+    for (int d = 0; d < N; d++) r &= md[d][(cc >> (N - 1 - d)) & 1];
+    return r;
+}
+
 // k-th set bit (from 0) of m; m has more than k set bits.
 __device__ __forceinline__ int nth_set(uint32_t m, int k)
 {
@@ -335,6 +376,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cedges(const InstDesc *__rest
             }
             int node = -1, L = 0, idx[N];
             uint32_t pm = live;
+            bool tested = false;                   // stack entries carry their own mask
             if (sp != sb) {
                 const int q = (--sp) & (STACK - 1);
                 node = stn[q];
@@ -342,6 +384,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cedges(const InstDesc *__rest
 #pragma unroll
                 for (int d = 0; d < N; d++) idx[d] = sti[q][d];
                 pm = stm[q];
+                tested = true;
                 if (sp == sb) sb = sp = 0;
             } else if (next < r1) {
                 int r = 0;
@@ -373,26 +416,35 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cedges(const InstDesc *__rest
             uint8_t st = ST_DEAD;
             if (active) {
                 st = I.state[node];
-                const int sh = Lf - L;
-                int clo[N], chi[N];
+                if (tested) {
+                    m = pm;
+                } else {
+                    const int sh = Lf - L;
+                    int clo[N], chi[N];
 #pragma unroll
-                for (int d = 0; d < N; d++) {
-                    clo[d] = idx[d] << sh;
-                    chi[d] = (idx[d] + 1) << sh;
+                    for (int d = 0; d < N; d++) {
+                        clo[d] = idx[d] << sh;
+                        chi[d] = (idx[d] + 1) << sh;
+                    }
+                    m = ctl_mask<N>(box, nu, pm, clo, chi);
                 }
-                m = ctl_mask<N>(box, nu, pm, clo, chi);
                 if (m && st == ST_SPLIT) {
                     if (sp - sb + (1 << N) > STACK) {
                         atomicExch(err, GIS_EBOUNDS);
                     } else {
+                        // push the children that meet a control, with their masks
                         const int ch = I.child[node];
+                        uint32_t md[N][2];
+                        child_masks<N>(box, nu, m, idx, Lf - L - 1, md);
                         for (int cc = (1 << N) - 1; cc >= 0; cc--) {
+                            const uint32_t mc = child_mask<N>(md, cc);
+                            if (!mc) continue;
                             const int q = (sp++) & (STACK - 1);
                             stn[q] = ch + cc;
                             stl[q] = L + 1;
 #pragma unroll
                             for (int d = 0; d < N; d++) sti[q][d] = 2 * idx[d] + ((cc >> (N - 1 - d)) & 1);
-                            stm[q] = m;
+                            stm[q] = mc;
                         }
                     }
                 } else if (m && st == ST_DEAD) {
@@ -535,16 +587,11 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cinc(const InstDesc *__restri
                 int idx[N];
 #pragma unroll
                 for (int d = 0; d < N; d++) idx[d] = I.idx[d][node];
+                uint32_t md[N][2];
+                child_masks<N>(box, nu, m, idx, sh, md);
 #pragma unroll
                 for (int cc = 0; cc < NC; cc++) {
-                    int clo[N], chi[N];
-#pragma unroll
-                    for (int d = 0; d < N; d++) {
-                        const int ci = 2 * idx[d] + ((cc >> (N - 1 - d)) & 1);
-                        clo[d] = ci << sh;
-                        chi[d] = (ci + 1) << sh;
-                    }
-                    const uint32_t mc = ctl_mask<N>(box, nu, m, clo, chi);
+                    const uint32_t mc = child_mask<N>(md, cc);
                     if (mc) {
                         tn[ne] = ch + cc;
                         tm[ne] = mc;

@@ -682,7 +682,9 @@ struct Engine {
             I->n_fresh = R;
             alloc_nodes(*I, R);
             mem.grow(I->live[0], I->cap_live[0], R, 0);
-            mem.grow(I->box32, I->cap_pairs, (size_t)R * I->nu * 4 * dyn.n, 0);
+            size_t c32 = 0;
+            if (precision != GIS_FP64_PLAIN)        // FP64 plain keeps its extremes in bx only
+                mem.grow(I->box32, c32, (size_t)R * I->nu * 4 * dyn.n, 0);
             size_t cex = 0, cxi = 0;
             mem.grow(I->exact, cex, (size_t)R * I->nu, 0);
             // dense enclosures while they are small (no store to manage); a compact
@@ -746,7 +748,7 @@ struct Engine {
             const size_t n2 = (size_t)2 * I.dyn.n;
             const size_t keep = (size_t)I.n_nodes * I.nu;
             size_t c32 = I.cap_pairs * 2 * n2, cex = I.cap_pairs;
-            mem.grow(I.box32, c32, I.cap_nodes * I.nu * 2 * n2, keep * 2 * n2);
+            if (I.box32) mem.grow(I.box32, c32, I.cap_nodes * I.nu * 2 * n2, keep * 2 * n2);
             mem.grow(I.exact, cex, I.cap_nodes * I.nu, keep);
             if (I.bx_dense) {
                 size_t c64 = I.c_bx * 2 * n2;

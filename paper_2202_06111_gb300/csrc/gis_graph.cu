@@ -528,8 +528,9 @@ __global__ void __launch_bounds__(256) k_export_boxes(const InstDesc *__restrict
     const uint16_t x = I.exact[q];
     unsigned xb = 0;                                   // extremes whose FP64 value is known
     for (int e = 0; e < 2 * N; e++) {
-        const float lo = I.box32[q * 4 * N + 2 * e], hi = I.box32[q * 4 * N + 2 * e + 1];
-        const float f = 0.5f * lo + 0.5f * hi;
+        // FP64 plain keeps no FP32 intervals: its FP32 value is the FP64 one rounded
+        const float f = I.box32 ? 0.5f * I.box32[q * 4 * N + 2 * e] + 0.5f * I.box32[q * 4 * N + 2 * e + 1]
+                                : (float)bx_get(I, q)[2 * e];
         if (b32) b32[lp * 2 * N + e] = f;
         double v = (double)f;
         if ((x >> e) & 1) {

@@ -303,10 +303,6 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop64(const InstDesc *__restr
         double *b = I.bx + q * 4 * N;              // FP64 plain: dense store
         b[2 * d] = b[2 * d + 1] = mn[d];
         b[2 * (N + d)] = b[2 * (N + d) + 1] = mx[d];
-        I.box32[q * 4 * N + 2 * d] = __double2float_rd(mn[d]);
-        I.box32[q * 4 * N + 2 * d + 1] = __double2float_ru(mn[d]);
-        I.box32[q * 4 * N + 2 * (N + d)] = __double2float_rd(mx[d]);
-        I.box32[q * 4 * N + 2 * (N + d) + 1] = __double2float_ru(mx[d]);
     }
     I.exact[q] = (uint16_t)(((1u << (2 * N)) - 1u) | (bad ? EX_NF64 : 0));
 }
