@@ -385,6 +385,8 @@ def run_serving(a, reqs):
             "latency_ms": {"p50": lats[len(lats) // 2], "p99": lats[min(len(lats) - 1, int(0.99 * len(lats)))],
                            "max": lats[-1]},
             "cells_per_s": cells / wall, "engine_steps": st["steps"] - base["steps"], "clocks": clocks,
+            "oom_restarts": st["oom_restarts"] - base["oom_restarts"],
+            "peak_device_gb": st["peak_device_bytes"] / 2 ** 30, "budget_gb": st["budget_bytes"] / 2 ** 30,
             "offered_load_s": reqs[-1]["arrival_s"]}
     print(json.dumps(line), flush=True)
 

@@ -276,6 +276,9 @@ typedef struct {
     int64_t cells_built;       /* live cells graph-built, all requests                 */
     int64_t cell_edges;        /* cell -> cell edges built, all requests               */
     int64_t budget_bytes, admitted_bytes; /* admission budget, estimate in use         */
+    int64_t oom_restarts;      /* steps that ran out of device memory (their requests
+                                  were re-queued to run alone)                         */
+    int64_t peak_device_bytes; /* largest device memory the engine held after a step   */
 } gis_server_stats;
 
 typedef struct gis_server gis_server;

@@ -62,6 +62,7 @@ cudaError_t launch_cgather(const InstDesc *D, const WorkList &w, int32_t *cps, u
 }
 
 constexpr int CE_WARPS = 8;      // cells (warps) per block
+constexpr int CE_TAB = 224;      // per-warp table of root masks per dimension (entries)
 
 __device__ __forceinline__ int warp_min(int v)
 {
@@ -226,7 +227,7 @@ static_assert((STACK & (STACK - 1)) == 0, "descent stack is a ring of 2^k entrie
 // plus the edges its earlier chunks hold (cent, cmask), reverse edges at
 // rcur[target]++ (rsrc, rmask).
 template <int N, bool FILL>
-__global__ void __launch_bounds__(CE_WARPS * 32) k_cedges(const InstDesc *__restrict__ D, int64_t c0, int64_t c1,
+__global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__restrict__ D, int64_t c0, int64_t c1,
                                                          const int64_t *__restrict__ cbase,
                                                          const int32_t *__restrict__ cinst,
                                                          const int32_t *__restrict__ rng,
@@ -241,6 +242,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cedges(const InstDesc *__rest
 {
     constexpr uint32_t FULL = 0xffffffffu;
     __shared__ CtlBox<N> s_box[CE_WARPS][32];
+    __shared__ uint32_t s_tab[CE_WARPS][CE_TAB];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     const int64_t W = (int64_t)gridDim.x * CE_WARPS, w = (int64_t)blockIdx.x * CE_WARPS + warp;
@@ -325,6 +327,33 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cedges(const InstDesc *__rest
             nroots *= live ? ext[d] : 1;
         }
         __syncwarp();
+        // root cells' control masks per dimension: tab[off_d + x - ua_d] holds the
+        // controls whose level-0 range on d holds x; a root's mask is the AND over d
+        int toff[N];
+        int tsum = 0;
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            toff[d] = tsum;
+            tsum += live ? ext[d] : 0;
+        }
+        const bool use_tab = live && tsum <= CE_TAB;
+        if (use_tab) {
+            uint32_t *tab = s_tab[warp];
+            for (int j = lane; j < tsum; j += 32) {
+                int d = 0;
+#pragma unroll
+                for (int e = 1; e < N; e++) d += j >= toff[e];
+                const int x = ua[d] + j - toff[d];
+                const int lo = x << Lf, hi = (x + 1) << Lf;
+                uint32_t mk = 0;
+                for (int u = 0; u < nu; u++) {
+                    const CtlBox<N> bu = box[u];
+                    mk |= (uint32_t)(hi >= bu.cf[2 * d] && lo <= bu.cf[2 * d + 1]) << u;
+                }
+                tab[j] = mk & live;
+            }
+            __syncwarp();
+        }
         const int64_t cb = cbase[s], ce = cbase[s + 1], kend = min(ce, k1);
         const int64_t r1 = min(nroots, (kend - cb) * CE_CHUNK);
         const bool small = r1 < ((int64_t)1 << 31);
@@ -414,10 +443,19 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cedges(const InstDesc *__rest
             if (!__any_sync(FULL, active)) break;
             uint32_t m = 0;
             uint8_t st = ST_DEAD;
+            int tslot = 0, tchild = 0;
             if (active) {
+                // the node's state, slot and first child are read together: one
+                // memory latency instead of a chain
                 st = I.state[node];
+                tslot = I.slot[node];
+                tchild = I.child[node];
                 if (tested) {
                     m = pm;
+                } else if (use_tab) {               // a root cell
+                    m = pm;
+#pragma unroll
+                    for (int d = 0; d < N; d++) m &= s_tab[warp][toff[d] + idx[d] - ua[d]];
                 } else {
                     const int sh = Lf - L;
                     int clo[N], chi[N];
@@ -433,7 +471,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cedges(const InstDesc *__rest
                         atomicExch(err, GIS_EBOUNDS);
                     } else {
                         // push the children that meet a control, with their masks
-                        const int ch = I.child[node];
+                        const int ch = tchild;
                         uint32_t md[N][2];
                         child_masks<N>(box, nu, m, idx, Lf - L - 1, md);
                         for (int cc = (1 << N) - 1; cc >= 0; cc--) {
@@ -454,7 +492,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cedges(const InstDesc *__rest
             const bool emit = active && st == ST_ALIVE && m != 0;
             const uint32_t b = __ballot_sync(FULL, emit);
             if (emit) {
-                const int t = I.slot[node];
+                const int t = tslot;
                 if (FILL) {
                     const int64_t pos = wpos + __popc(b & lt);
                     cent[pos] = t;
@@ -575,8 +613,9 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cinc(const InstDesc *__restri
             const uint32_t m = prev.cmask[e] & live;
             const int node = prev.s2n[to];
             const uint8_t st = I.state[node];
+            const int slot_t = I.slot[node];         // read with the state (one latency)
             if (m && st == ST_ALIVE) {
-                tn[0] = node;
+                tn[0] = -1 - slot_t;                 // a slot, not a node
                 tm[0] = m;
                 ne = 1;
             } else if (m && st == ST_DEAD) {
@@ -610,7 +649,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cinc(const InstDesc *__restri
         const int tot = __shfl_sync(FULL, incl, 31);
         const int64_t base = wpos + (incl - ne);
         for (int j = 0; j < ne; j++) {
-            const int t = I.slot[tn[j]];
+            const int t = tn[j] < 0 ? -1 - tn[j] : I.slot[tn[j]];
             const uint32_t mm = tm[j];
             if (FILL) {
                 cent[base + j] = t;

@@ -216,6 +216,7 @@ void gis_server::run()
                     stats.admitted_bytes -= est_of[i];
                 }
                 stats.steps++;
+                stats.peak_device_bytes = std::max<int64_t>(stats.peak_device_bytes, E->mem.used);
                 stats.cells_built += cells;
                 stats.cell_edges += edges;
                 done_cv.notify_all();
@@ -232,6 +233,7 @@ void gis_server::run()
             if (e.st == GIS_ENOMEM && !solo_active) {
                 // out of device memory in a mix: retry each request alone, in order
                 std::lock_guard<std::mutex> lk(mu);
+                stats.oom_restarts++;
                 for (auto it = active.rbegin(); it != active.rend(); ++it) {
                     Pending pd = req_of[*it];
                     pd.solo = true;

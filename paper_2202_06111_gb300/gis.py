@@ -95,7 +95,8 @@ class gis_server_opts(C.Structure):
 
 
 _SERVER_STAT_FIELDS = [(k, C.c_int64) for k in ("submitted", "completed", "failed", "active", "queued", "steps",
-                                                "cells_built", "cell_edges", "budget_bytes", "admitted_bytes")]
+                                                "cells_built", "cell_edges", "budget_bytes", "admitted_bytes",
+                                                "oom_restarts", "peak_device_bytes")]
 
 
 class gis_server_stats(C.Structure):
