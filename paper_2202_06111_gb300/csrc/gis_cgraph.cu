@@ -63,6 +63,7 @@ cudaError_t launch_cgather(const InstDesc *D, const WorkList &w, int32_t *cps, u
 
 constexpr int CE_WARPS = 8;      // cells (warps) per block
 constexpr int CE_TAB = 224;      // per-warp table of root masks per dimension (entries)
+constexpr int CE_GRAB = 4;       // chunks a warp takes at a time
 
 __device__ __forceinline__ int warp_min(int v)
 {
@@ -210,87 +211,77 @@ __device__ __forceinline__ int nth_set(uint32_t m, int k)
 
 static_assert((STACK & (STACK - 1)) == 0, "descent stack is a ring of 2^k entries");
 
-// Edges of the cells c0 <= s < c1 (all of dimension N). The chunks
-// cbase[c0] .. cbase[c1] are split evenly over the grid's warps; a warp finds
-// the cell of its first chunk by a 32-way search of cbase, then walks its
-// chunks in order, one cell at a time. Lane u holds control u's box. The lanes
-// take the run's root cells 32 at a time; a split node's 2^n children go on
-// the lane's own stack (a ring: the lane pops the newest entry, and a lane
-// with no work left takes the oldest entry of another lane's stack, the
-// largest subtree still waiting). A node's control mask is the set of its
-// parent's controls whose box holds it; edges found in the same step are
-// compacted across the warp.
-// FILL = false: edges per cell (ccnt) and targets per pair (pcnt), added up
-// over the warps that share a cell (both zeroed beforehand), in-degrees
-// (rcnt), removed-leaf flags, the pair-edge total, and per warp the edges it
-// found in its last cell (wpart). FILL = true: a cell's edges at coff[cell]
-// plus the edges its earlier chunks hold (cent, cmask), reverse edges at
-// rcur[target]++ (rsrc, rmask).
+// Edges of the walked cells of dimension N (chunks cbase[c0] .. cbase[c1] of
+// the cells c0 <= s < c1; carried cells have none). Warps take CE_GRAB chunks
+// at a time from a counter, so cheap and deep chunks (a root with no subtree,
+// or one refined three levels down) balance out across the device; chk_cell
+// gives each chunk's cell. Lane u holds control u's box. The lanes take the
+// chunk's root cells 32 at a time; a split node pushes the children that meet
+// a control, with their masks, onto the lane's own stack (a ring: the lane
+// pops the newest entry, and a lane with no work left takes the oldest entry
+// of another lane's stack, the largest subtree still waiting); edges found in
+// the same step are compacted across the warp.
+// FILL = false: edges per chunk (chk_cnt), per cell (ccnt) and per pair (pcnt;
+// cells of several chunks add up, both zeroed beforehand), in-degrees (rcnt),
+// removed-leaf flags, the pair-edge total. FILL = true: a chunk's edges at
+// coff[cell] + chk_off[chunk] - chk_off[first chunk of the cell] (cent, cmask),
+// reverse edges at rcur[target]++ (rsrc, rmask). *stop (set when the chunk
+// arrays are too small) makes both passes return at once.
 template <int N, bool FILL>
 __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__restrict__ D, int64_t c0, int64_t c1,
-                                                         const int64_t *__restrict__ cbase,
-                                                         const int32_t *__restrict__ cinst,
-                                                         const int32_t *__restrict__ rng,
-                                                         uint8_t *__restrict__ pflag, int32_t *__restrict__ pcnt,
-                                                         int32_t *__restrict__ ccnt, int32_t *__restrict__ rcnt,
-                                                         const int64_t *__restrict__ coff, int32_t *__restrict__ cent,
-                                                         uint32_t *__restrict__ cmask,
-                                                         unsigned long long *__restrict__ rcur,
-                                                         int32_t *__restrict__ rsrc, uint32_t *__restrict__ rmask,
-                                                         unsigned long long *__restrict__ pair_edges,
-                                                         int32_t *__restrict__ wpart, int32_t *__restrict__ err)
+                                                            const int64_t *__restrict__ cbase,
+                                                            const int32_t *__restrict__ chk_cell,
+                                                            int32_t *__restrict__ chk_cnt,
+                                                            const int64_t *__restrict__ chk_off,
+                                                            unsigned long long *__restrict__ grab,
+                                                            const int32_t *__restrict__ stop,
+                                                            const int32_t *__restrict__ cinst,
+                                                            const int32_t *__restrict__ rng,
+                                                            uint8_t *__restrict__ pflag, int32_t *__restrict__ pcnt,
+                                                            int32_t *__restrict__ ccnt, int32_t *__restrict__ rcnt,
+                                                            const int64_t *__restrict__ coff,
+                                                            int32_t *__restrict__ cent, uint32_t *__restrict__ cmask,
+                                                            unsigned long long *__restrict__ rcur,
+                                                            int32_t *__restrict__ rsrc, uint32_t *__restrict__ rmask,
+                                                            unsigned long long *__restrict__ pair_edges,
+                                                            int32_t *__restrict__ err)
 {
     constexpr uint32_t FULL = 0xffffffffu;
     __shared__ CtlBox<N> s_box[CE_WARPS][32];
     __shared__ uint32_t s_tab[CE_WARPS][CE_TAB];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
-    const int64_t W = (int64_t)gridDim.x * CE_WARPS, w = (int64_t)blockIdx.x * CE_WARPS + warp;
-    const int64_t kb = cbase[c0], K = cbase[c1] - kb;
-    const int64_t k0 = kb + w * K / W, k1 = kb + (w + 1) * K / W;
-    if (k0 == k1) {
-        if (!FILL && lane == 0) wpart[w] = 0;
-        return;                                    // whole warp
-    }
-    // cell of chunk k0: cbase[lo] <= k0 < cbase[hi], 32 probes per round
-    int64_t lo = c0, hi = c1;
-    while (hi - lo > 1) {
-        const int64_t span = hi - lo;
-        const int64_t pos = span <= 32 ? lo + 1 + lane : lo + span * (lane + 1) / 33;
-        const bool valid = pos < hi;
-        const uint32_t le = __ballot_sync(FULL, valid && cbase[pos] <= k0);
-        const int nv = __popc(__ballot_sync(FULL, valid));
-        const int t = __popc(le);
-        const int64_t plo = __shfl_sync(FULL, pos, t > 0 ? t - 1 : 0);
-        const int64_t phi = __shfl_sync(FULL, pos, t < nv ? t : 0);
-        if (t > 0) lo = plo;
-        if (t < nv) hi = phi;
-    }
-    int64_t s = lo, k = k0;
-    int64_t wpos = 0;
-    if (FILL) {
-        const int64_t cb = cbase[s];
-        int64_t skip = 0;
-        if (k0 > cb)                               // the cell began in earlier warps' runs
-            for (int64_t j = w - 1; j >= 0; j--) {
-                skip += wpart[j];
-                if (kb + j * K / W <= cb) break;
-            }
-        wpos = coff[s] + skip;
-    }
+    if (*(volatile const int32_t *)stop) return;
+    const int64_t kb = cbase[c0], ke = cbase[c1];
     CtlBox<N> *box = s_box[warp];
     unsigned long long pe = 0;
-    while (k < k1) {
-        if (cbase[s + 1] == k) {                   // no chunks: a carried cell
-            s++;
-            continue;
-        }
-        if (FILL && cbase[s] == k) wpos = coff[s];  // the cell starts at its first chunk
-        const InstDesc &I = D[cinst[s]];
-        const int ls = (int)(s - I.slot_base);
-        const int nu = I.nu, Lf = I.Lf;
-        const int64_t p = I.pair_base + (int64_t)ls * nu + lane;
-        int n0[N];
+    // the cell set up in shared memory and registers (chunks of one cell are
+    // consecutive, so a warp often keeps its cell across chunks)
+    int64_t cur = -1;
+    const InstDesc *Ip = D;
+    int ls = 0, nu = 0, Lf = 0;
+    int64_t p = 0, nroots = 0, cb = 0, ce = 0;
+    int n0[N], ua[N], ext[N], toff[N];
+    uint32_t live = 0;
+    bool use_tab = false;
+#pragma unroll
+    for (int d = 0; d < N; d++) n0[d] = ua[d] = ext[d] = toff[d] = 0;
+    for (;;) {
+    unsigned long long g0 = 0;
+    if (lane == 0) g0 = atomicAdd(grab, (unsigned long long)CE_GRAB);
+    g0 = __shfl_sync(FULL, g0, 0);
+    if (kb + (int64_t)g0 >= ke) break;
+    const int64_t gend = min(kb + (int64_t)g0 + CE_GRAB, ke);
+    for (int64_t k = kb + (int64_t)g0; k < gend; k++) {
+        const int64_t s = chk_cell[k];
+        if (s != cur) {
+        cur = s;
+        Ip = D + cinst[s];
+        const InstDesc &I = *Ip;
+        ls = (int)(s - I.slot_base);
+        nu = I.nu;
+        Lf = I.Lf;
+        p = I.pair_base + (int64_t)ls * nu + lane;
 #pragma unroll
         for (int d = 0; d < N; d++) n0[d] = I.n0[d];
         // control `lane`: finest-level decisions, level-0 box
@@ -316,9 +307,8 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
                 box[lane] = cb_;
             }
         }
-        const uint32_t live = __ballot_sync(FULL, live_box);
-        int ua[N], ext[N];
-        int64_t nroots = live ? 1 : 0;
+        live = __ballot_sync(FULL, live_box);
+        nroots = live ? 1 : 0;
 #pragma unroll
         for (int d = 0; d < N; d++) {
             ua[d] = warp_min(live_box ? a0[d] : INT_MAX);
@@ -329,14 +319,13 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
         __syncwarp();
         // root cells' control masks per dimension: tab[off_d + x - ua_d] holds the
         // controls whose level-0 range on d holds x; a root's mask is the AND over d
-        int toff[N];
         int tsum = 0;
 #pragma unroll
         for (int d = 0; d < N; d++) {
             toff[d] = tsum;
             tsum += live ? ext[d] : 0;
         }
-        const bool use_tab = live && tsum <= CE_TAB;
+        use_tab = live && tsum <= CE_TAB;
         if (use_tab) {
             uint32_t *tab = s_tab[warp];
             for (int j = lane; j < tsum; j += 32) {
@@ -354,10 +343,14 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
             }
             __syncwarp();
         }
-        const int64_t cb = cbase[s], ce = cbase[s + 1], kend = min(ce, k1);
-        const int64_t r1 = min(nroots, (kend - cb) * CE_CHUNK);
+        cb = cbase[s];
+        ce = cbase[s + 1];
+        }
+        const InstDesc &I = *Ip;
+        const int64_t r1 = min(nroots, (k - cb + 1) * CE_CHUNK);
         const bool small = r1 < ((int64_t)1 << 31);
         int64_t next = (k - cb) * CE_CHUNK + lane;
+        int64_t wpos = FILL ? coff[s] + chk_off[k] - chk_off[cb] : 0;
         // per-lane ring stack of (node, level, index, parent's mask)
         int stn[STACK], stl[STACK], sti[STACK][N];
         uint32_t stm[STACK];
@@ -518,7 +511,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
         }
         if (!FILL) {
             const uint32_t touched = __reduce_or_sync(FULL, tch);
-            const bool whole = k == cb && ce <= k1;
+            const bool whole = ce - cb == 1;       // the cell's only chunk
             if (lane < nu) {
                 if (whole) pcnt[p] = myc;
                 else if (myc) atomicAdd(&pcnt[p], myc);
@@ -526,14 +519,13 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
             }
             pe += (unsigned long long)__reduce_add_sync(FULL, lane < nu ? (unsigned)myc : 0u);
             if (lane == 0) {
+                chk_cnt[k] = nent;
                 if (whole) ccnt[s] = nent;
                 else if (nent) atomicAdd(&ccnt[s], nent);
-                if (kend == k1) wpart[w] = nent;
             }
         }
         __syncwarp();
-        k = kend;
-        s++;
+    }
     }
     if (!FILL && lane == 0 && pe) atomicAdd(pair_edges, pe);
 }
@@ -707,26 +699,24 @@ cudaError_t launch_cinc(bool fill, int n, const InstDesc *D, const WorkList &w, 
     return cudaGetLastError();
 }
 
-// Persistent grid, the same for the count and the fill pass (the fill reads
-// the count's per-warp partials): as many blocks as fit on the device at once
-// for both.
-template <int N>
+// Persistent grid: as many blocks as fit on the device at once.
+template <int N, bool FILL>
 static int cedges_grid(int dev)
 {
     static int cached[64] = {};
     if (dev < 0 || dev >= 64) dev = 0;
     if (!cached[dev]) {
-        int a = 0, b = 0, sms = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_cedges<N, false>, CE_WARPS * 32, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cedges<N, true>, CE_WARPS * 32, 0);
+        int a = 0, sms = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_cedges<N, FILL>, CE_WARPS * 32, 0);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cached[dev] = std::max(1, std::min(a, b)) * std::max(1, sms);
+        cached[dev] = std::max(1, a) * std::max(1, sms);
     }
     return cached[dev];
 }
 
 cudaError_t launch_cedges(bool fill, int n, const InstDesc *D, int64_t c0, int64_t c1, const int64_t *cbase,
-                          const int32_t *cinst, const CellGraph &g, int32_t *wpart, cudaStream_t st)
+                          const ChunkWork &cw, unsigned long long *grab, const int32_t *cinst, const CellGraph &g,
+                          cudaStream_t st)
 {
     if (c1 <= c0) return cudaSuccess;
     int dev = 0;
@@ -735,13 +725,13 @@ cudaError_t launch_cedges(bool fill, int n, const InstDesc *D, int64_t c0, int64
 #define CE_CASE(NN)                                                                                        \
     case NN:                                                                                               \
         if (fill)                                                                                          \
-            k_cedges<NN, true><<<cedges_grid<NN>(dev), b, 0, st>>>(                                  \
-                D, c0, c1, cbase, cinst, g.rng, g.pflag, g.pcnt, g.ccnt, g.rcnt, g.coff, g.cent, g.cmask,  \
-                g.rcur, g.rsrc, g.rmask, g.pair_edges, wpart, g.err);                                      \
+            k_cedges<NN, true><<<cedges_grid<NN, true>(dev), b, 0, st>>>(                                   \
+                D, c0, c1, cbase, cw.cell, cw.cnt, cw.off, grab, cw.stop, cinst, g.rng, g.pflag, g.pcnt,    \
+                g.ccnt, g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rsrc, g.rmask, g.pair_edges, g.err);     \
         else                                                                                               \
-            k_cedges<NN, false><<<cedges_grid<NN>(dev), b, 0, st>>>(                                 \
-                D, c0, c1, cbase, cinst, g.rng, g.pflag, g.pcnt, g.ccnt, g.rcnt, g.coff, g.cent, g.cmask,  \
-                g.rcur, g.rsrc, g.rmask, g.pair_edges, wpart, g.err);                                      \
+            k_cedges<NN, false><<<cedges_grid<NN, false>(dev), b, 0, st>>>(                                 \
+                D, c0, c1, cbase, cw.cell, cw.cnt, cw.off, grab, cw.stop, cinst, g.rng, g.pflag, g.pcnt,    \
+                g.ccnt, g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rsrc, g.rmask, g.pair_edges, g.err);     \
         note_launch();                                                                                     \
         break;
     switch (n) {
@@ -752,18 +742,29 @@ cudaError_t launch_cedges(bool fill, int n, const InstDesc *D, int64_t c0, int64
     return cudaGetLastError();
 }
 
-int cedges_cells_per_block() { return CE_WARPS; }
-
-// Upper bound of the warps of one edge launch (size of wpart per dimension).
-int cedges_max_warps(int dev)
+// The cell of every chunk; *stop = 1 (and nothing written) if there are more
+// chunks than the arrays hold.
+__global__ void __launch_bounds__(256) k_cexpand(const int64_t *__restrict__ cbase, int64_t NL, int64_t cap,
+                                                 int32_t *__restrict__ cell, int32_t *__restrict__ stop)
 {
-    int m = 0;
-    m = std::max(m, cedges_grid<1>(dev));
-    m = std::max(m, cedges_grid<2>(dev));
-    m = std::max(m, cedges_grid<3>(dev));
-    m = std::max(m, cedges_grid<4>(dev));
-    return m * CE_WARPS;
+    if (cbase[NL] > cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) *stop = 1;
+        return;
+    }
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= NL) return;
+    for (int64_t k = cbase[s]; k < cbase[s + 1]; k++) cell[k] = (int32_t)s;
 }
+
+cudaError_t launch_cexpand(const int64_t *cbase, int64_t NL, const ChunkWork &cw, cudaStream_t st)
+{
+    if (NL == 0) return cudaSuccess;
+    k_cexpand<<<(unsigned)((NL + 255) / 256), 256, 0, st>>>(cbase, NL, cw.cap, cw.cell, cw.stop);
+    note_launch();
+    return cudaGetLastError();
+}
+
+int cedges_cells_per_block() { return CE_WARPS; }
 
 // ---------------------------------------------------------------------------
 // Prune on the cell graph. vmask[i] holds the controls of cell i that are

@@ -564,7 +564,9 @@ struct Engine {
     bool have_prev = false;     // the *_o arrays hold the previous build's complete graph
     int64_t prev_NL = 0;        // cells of that build
     int64_t *cbase = nullptr; size_t c_cbase = 0;
-    int32_t *wpart = nullptr; size_t c_wpart = 0;
+    int32_t *chk_cell = nullptr, *chk_cnt = nullptr; size_t c_chk_cell = 0, c_chk_cnt = 0;
+    int64_t *chk_off = nullptr; size_t c_chk_off = 0;
+    int64_t chunk_hint = 0;     // chunks of the previous build
     int32_t *rng = nullptr; size_t c_rng = 0;
     uint8_t *pflag = nullptr; size_t c_pflag = 0;
     int32_t *cnt = nullptr; size_t c_cnt = 0;
@@ -1108,51 +1110,74 @@ struct Engine {
         mem.ensure(rcnt, c_rcnt, NLs);
         mem.ensure(roff, c_roff, NLs + 1);
         mem.ensure(rcur, c_rcur, NLs);
-        CK(cudaMemsetAsync(rcnt, 0, NLs * sizeof(int32_t), st));
-        CK(cudaMemsetAsync(ctl + 12, 0, 2 * sizeof(int32_t), st));
-        CellGraph g{rng, pflag, pcnt, ccnt, rcnt, coff, nullptr, nullptr, (unsigned long long *)rcur, nullptr,
-                    nullptr, (unsigned long long *)(ctl + 12), ctl + 7};
-        timer.begin(PH_COUNT);
-        // work chunks of the cells' union boxes; cells of one dimension are
-        // contiguous (number() orders the problems by dimension)
         mem.ensure(cnch, c_cnch, NLs);
         mem.ensure(cbase, c_cbase, NLs + 1);
-        const int Wmax = cedges_max_warps(dev);
-        mem.ensure(wpart, c_wpart, (size_t)MAXN * Wmax);
-        CK(launch_cchunks(d_desc, NL, cinst, rng, pflag, cnch, st));
-        CK(launch_scan_i32(cnch, cbase, NL, scratch, st));
-        CK(cudaMemsetAsync(ccnt, 0, NLs * sizeof(int32_t), st));
-        CK(cudaMemsetAsync(pcnt, 0, Ps * sizeof(int32_t), st));
+        CellGraph g{rng, pflag, pcnt, ccnt, rcnt, coff, nullptr, nullptr, (unsigned long long *)rcur, nullptr,
+                    nullptr, (unsigned long long *)(ctl + 12), ctl + 7};
+        unsigned long long *grab = (unsigned long long *)(ctl + 24);   // 8 chunk counters
+        const CellPrev prev{oslot, coff_o, cent_o, cmask_o, s2n_o, cps_o, pflag_o, prev_NL};
         int64_t seg_base[MAXN + 2] = {0};
         for (int i : ids) seg_base[inst[i]->dyn.n + 1] += inst[i]->n_live;
         for (int n = 1; n <= MAXN; n++) seg_base[n + 1] += seg_base[n];
-        for (int n = 1; n <= MAXN; n++)
-            CK(launch_cedges(false, n, d_desc, seg_base[n], seg_base[n + 1], cbase, cinst, g,
-                             wpart + (size_t)(n - 1) * Wmax, st));
-        const CellPrev prev{oslot, coff_o, cent_o, cmask_o, s2n_o, cps_o, pflag_o, prev_NL};
-        WorkList wcar[MAXN + 1];
-        for (int n = 1; n <= MAXN; n++) {
+        auto carried = [&](int n) {
             std::vector<RangeSpec> r;
             for (int i : ids)
                 if (inst[i]->dyn.n == n && inst[i]->n_carry > 0)
                     r.push_back({inst[i]->tix, inst[i]->slot_base, inst[i]->n_carry});
-            if (r.empty()) continue;
-            wcar[n] = make_work(r, cedges_cells_per_block());
-            CK(launch_cinc(false, n, d_desc, wcar[n], g, prev, st));
+            return r;
+        };
+        // work chunks of the walked cells' union boxes (cells of one dimension
+        // are contiguous: number() orders the problems by dimension); the chunk
+        // arrays are sized from the previous build and grown if they overflow
+        timer.begin(PH_COUNT);
+        CK(launch_cchunks(d_desc, NL, cinst, rng, pflag, cnch, st));
+        CK(launch_scan_i32(cnch, cbase, NL, scratch, st));
+        timer.end();
+        int64_t hEc = 0, K = 0;
+        int32_t hq[8], hstop = 0;
+        int64_t cap = std::max<int64_t>(2 * NL + 4096, chunk_hint + chunk_hint / 4);
+        for (;;) {
+            mem.ensure(chk_cell, c_chk_cell, (size_t)cap);
+            mem.ensure(chk_cnt, c_chk_cnt, (size_t)cap);
+            mem.ensure(chk_off, c_chk_off, (size_t)cap + 1);
+            const ChunkWork cw{chk_cell, chk_cnt, chk_off, ctl + 18, cap};
+            mem.ensure(scratch, c_scratch, scan_scratch_bytes(std::max<int64_t>({P, NL, cap}) + 1));
+            timer.begin(PH_COUNT);
+            CK(cudaMemsetAsync(ctl + 18, 0, sizeof(int32_t), st));
+            CK(cudaMemsetAsync(ctl + 24, 0, 16 * sizeof(int32_t), st));
+            CK(cudaMemsetAsync(ctl + 12, 0, 2 * sizeof(int32_t), st));
+            CK(cudaMemsetAsync(rcnt, 0, NLs * sizeof(int32_t), st));
+            CK(cudaMemsetAsync(ccnt, 0, NLs * sizeof(int32_t), st));
+            CK(cudaMemsetAsync(pcnt, 0, Ps * sizeof(int32_t), st));
+            CK(cudaMemsetAsync(chk_cnt, 0, (size_t)cap * sizeof(int32_t), st));
+            CK(launch_cexpand(cbase, NL, cw, st));
+            for (int n = 1; n <= MAXN; n++)
+                CK(launch_cedges(false, n, d_desc, seg_base[n], seg_base[n + 1], cbase, cw, grab + (n - 1), cinst, g,
+                                 st));
+            for (int n = 1; n <= MAXN; n++) {
+                const auto r = carried(n);
+                if (!r.empty()) CK(launch_cinc(false, n, d_desc, make_work(r, cedges_cells_per_block()), g, prev, st));
+            }
+            timer.end();
+            timer.begin(PH_SCAN);
+            CK(launch_scan_i32(ccnt, coff, NL, scratch, st));
+            CK(launch_scan_i32(rcnt, roff, NL, scratch, st));
+            CK(launch_scan_i32(chk_cnt, chk_off, cap, scratch, st));
+            timer.end();
+            unsigned char *hp = pinned(256);
+            CK(cudaMemcpyAsync(hp, coff + NL, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(hp + 8, ctl + 6, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(hp + 40, cbase + NL, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(hp + 48, ctl + 18, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            sync();
+            std::memcpy(&hEc, hp, sizeof(hEc));
+            std::memcpy(hq, hp + 8, sizeof(hq));
+            std::memcpy(&K, hp + 40, sizeof(K));
+            std::memcpy(&hstop, hp + 48, sizeof(hstop));
+            if (!hstop) break;
+            cap = K + K / 8 + 1024;                // the chunk arrays were too small: again
         }
-        timer.end();
-        timer.begin(PH_SCAN);
-        CK(launch_scan_i32(ccnt, coff, NL, scratch, st));
-        CK(launch_scan_i32(rcnt, roff, NL, scratch, st));
-        timer.end();
-        unsigned char *hp = pinned(256);
-        CK(cudaMemcpyAsync(hp, coff + NL, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(hp + 8, ctl + 6, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        sync();
-        int64_t hEc = 0;
-        int32_t hq[8];
-        std::memcpy(&hEc, hp, sizeof(hEc));
-        std::memcpy(hq, hp + 8, sizeof(hq));
+        chunk_hint = K;
         last_recheck = hq[0];
         if (last_recheck > 0) {
             cum.cum_recheck_samples += hq[4];
@@ -1173,16 +1198,15 @@ struct Engine {
         g.rmask = rmask;
         timer.begin(PH_FILL);
         CK(cudaMemcpyAsync(rcur, roff, NLs * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
-        for (int n = 1; n <= MAXN; n++)
-            CK(launch_cedges(true, n, d_desc, seg_base[n], seg_base[n + 1], cbase, cinst, g,
-                             wpart + (size_t)(n - 1) * Wmax, st));
+        {
+            const ChunkWork cw{chk_cell, chk_cnt, chk_off, ctl + 18, cap};
+            for (int n = 1; n <= MAXN; n++)
+                CK(launch_cedges(true, n, d_desc, seg_base[n], seg_base[n + 1], cbase, cw, grab + 4 + (n - 1), cinst,
+                                 g, st));
+        }
         for (int n = 1; n <= MAXN; n++) {
-            if (!wcar[n].n_blocks) continue;
-            std::vector<RangeSpec> r;
-            for (int i : ids)
-                if (inst[i]->dyn.n == n && inst[i]->n_carry > 0)
-                    r.push_back({inst[i]->tix, inst[i]->slot_base, inst[i]->n_carry});
-            CK(launch_cinc(true, n, d_desc, make_work(r, cedges_cells_per_block()), g, prev, st));
+            const auto r = carried(n);
+            if (!r.empty()) CK(launch_cinc(true, n, d_desc, make_work(r, cedges_cells_per_block()), g, prev, st));
         }
         have_prev = true;
         prev_NL = NL;

@@ -133,12 +133,21 @@ cudaError_t launch_cinc(bool fill, int n, const InstDesc *D, const WorkList &wca
 // per cell the chunk count of its union box (the work unit of the edge kernels)
 cudaError_t launch_cchunks(const InstDesc *D, int64_t NL, const int32_t *cinst, const int32_t *rng,
                            const uint8_t *pflag, int32_t *nch, cudaStream_t st);
-// edges of the cells c0 <= s < c1, all of dimension n; cbase = exclusive scan
-// of the chunk counts; wpart holds cedges_max_warps() words, written by the
-// count pass and read by the fill pass of the same cells
+// chunks of the edge walk: the cell of each chunk, its edge count and the
+// exclusive scan of the counts; cap entries; *stop = 1 when cap is too small
+struct ChunkWork {
+    int32_t *cell;
+    int32_t *cnt;
+    int64_t *off;
+    int32_t *stop;
+    int64_t cap;
+};
+cudaError_t launch_cexpand(const int64_t *cbase, int64_t NL, const ChunkWork &cw, cudaStream_t st);
+// edges of the walked cells c0 <= s < c1, all of dimension n; cbase = exclusive
+// scan of the chunk counts; grab: the chunk counter of this launch (zeroed)
 cudaError_t launch_cedges(bool fill, int n, const InstDesc *D, int64_t c0, int64_t c1, const int64_t *cbase,
-                          const int32_t *cinst, const CellGraph &g, int32_t *wpart, cudaStream_t st);
-int cedges_max_warps(int dev);
+                          const ChunkWork &cw, unsigned long long *grab, const int32_t *cinst, const CellGraph &g,
+                          cudaStream_t st);
 int cedges_cells_per_block();     // cells per block of k_cinc
 cudaError_t launch_cprune_init(const InstDesc *D, const WorkList &wslots, const uint8_t *pflag, const int32_t *pcnt,
                                int32_t *pc, uint32_t *vmask, uint8_t *alive, int32_t *frontier0, uint32_t *sizes,
