@@ -63,7 +63,7 @@ cudaError_t launch_cgather(const InstDesc *D, const WorkList &w, int32_t *cps, u
 
 constexpr int CE_WARPS = 8;      // cells (warps) per block
 constexpr int CE_TAB = 224;      // per-warp table of root masks per dimension (entries)
-constexpr int CE_GRAB = 4;       // chunks a warp takes at a time
+constexpr int CE_GRAB = 4;       // fewest chunks a warp takes at a time
 
 __device__ __forceinline__ int warp_min(int v)
 {
@@ -90,12 +90,14 @@ constexpr int64_t CE_CHUNK = 64;
 // One warp per cell (lane = control), as the edge kernels read the boxes.
 __global__ void __launch_bounds__(256) k_cchunks(const InstDesc *__restrict__ D, int64_t NL,
                                                  const int32_t *__restrict__ cinst, const int32_t *__restrict__ rng,
-                                                 const uint8_t *__restrict__ pflag, int32_t *__restrict__ nch)
+                                                 const uint8_t *__restrict__ pflag, int32_t *__restrict__ nch,
+                                                 int32_t *__restrict__ pcnt)
 {
     const int lane = threadIdx.x & 31;
     const int64_t s = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (s >= NL) return;                           // whole warp
     const InstDesc &I = D[cinst[s]];
+    if (lane < I.nu) pcnt[I.pair_base + (s - I.slot_base) * I.nu + lane] = 0;
     if (s - I.slot_base < I.n_carry) {             // edges from the previous level's
         if (lane == 0) nch[s] = 0;
         return;
@@ -123,10 +125,10 @@ __global__ void __launch_bounds__(256) k_cchunks(const InstDesc *__restrict__ D,
 }
 
 cudaError_t launch_cchunks(const InstDesc *D, int64_t NL, const int32_t *cinst, const int32_t *rng,
-                           const uint8_t *pflag, int32_t *nch, cudaStream_t st)
+                           const uint8_t *pflag, int32_t *nch, int32_t *pcnt, cudaStream_t st)
 {
     if (NL == 0) return cudaSuccess;
-    k_cchunks<<<(unsigned)((NL + 7) / 8), 256, 0, st>>>(D, NL, cinst, rng, pflag, nch);
+    k_cchunks<<<(unsigned)((NL + 7) / 8), 256, 0, st>>>(D, NL, cinst, rng, pflag, nch, pcnt);
     note_launch();
     return cudaGetLastError();
 }
@@ -209,22 +211,33 @@ __device__ __forceinline__ int nth_set(uint32_t m, int k)
     return pos;
 }
 
-static_assert((STACK & (STACK - 1)) == 0, "descent stack is a ring of 2^k entries");
+// Warp-shared descent stack of the edge walk (dynamic shared memory, S
+// entries per warp, structure of arrays): an entry is a split node whose
+// children still wait -- its first child, the bitmap of its children that
+// meet a control with their level (meta = bitmap | level << 16), its index,
+// and per dimension and half the controls meeting the children (child_masks;
+// a child's mask is the AND of its halves'). A step takes up to 32 children,
+// lowest bits first, from the entries of the top level only, so the entries
+// of one level form one run of at most 32 (one step's pushes) and S = 32 x
+// the levels below the roots always suffices.
+__host__ __device__ constexpr int walk_words(int n) { return 2 + 3 * n; }
 
 // Edges of the walked cells of dimension N (chunks cbase[c0] .. cbase[c1] of
-// the cells c0 <= s < c1; carried cells have none). Warps take CE_GRAB chunks
-// at a time from a counter, so cheap and deep chunks (a root with no subtree,
-// or one refined three levels down) balance out across the device; chk_cell
-// gives each chunk's cell. Lane u holds control u's box. The lanes take the
-// chunk's root cells 32 at a time; a split node pushes the children that meet
-// a control, with their masks, onto the lane's own stack (a ring: the lane
-// pops the newest entry, and a lane with no work left takes the oldest entry
-// of another lane's stack, the largest subtree still waiting); edges found in
-// the same step are compacted across the warp.
+// the cells c0 <= s < c1; carried cells have none). Warps take runs of chunks
+// from a counter, an eighth of the remaining work's share per warp (4 to 16
+// chunks), so cheap and deep chunks (a root with no subtree, or one refined
+// three levels down) balance out across the device while the warps stay on
+// neighbouring cells (whose targets share cache lines); chk_cell gives each
+// chunk's cell. Lane u holds control u's box. A step gives every lane one
+// node: the waiting children of the stack's top level, else the chunk's next
+// root cells; a split node meeting a control becomes a stack entry. Edges
+// found in the same step are compacted across the warp.
 // FILL = false: edges per chunk (chk_cnt), per cell (ccnt) and per pair (pcnt;
 // cells of several chunks add up, both zeroed beforehand), in-degrees (rcnt),
 // removed-leaf flags, the pair-edge total. FILL = true: a chunk's edges at
-// coff[cell] + chk_off[chunk] - chk_off[first chunk of the cell] (cent, cmask),
+// coff[cell] + the edges of the cell's earlier chunks (cent, cmask; carried
+// from chunk to chunk within a run, from chk_off = the exclusive scan of
+// chk_cnt at a run's start; no scan is needed when every cell has one chunk),
 // reverse edges at rcur[target]++ (rsrc, rmask). *stop (set when the chunk
 // arrays are too small) makes both passes return at once.
 template <int N, bool FILL>
@@ -234,7 +247,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
                                                             int32_t *__restrict__ chk_cnt,
                                                             const int64_t *__restrict__ chk_off,
                                                             unsigned long long *__restrict__ grab,
-                                                            const int32_t *__restrict__ stop,
+                                                            const int32_t *__restrict__ stop, int S,
                                                             const int32_t *__restrict__ cinst,
                                                             const int32_t *__restrict__ rng,
                                                             uint8_t *__restrict__ pflag, int32_t *__restrict__ pcnt,
@@ -249,11 +262,17 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
     constexpr uint32_t FULL = 0xffffffffu;
     __shared__ CtlBox<N> s_box[CE_WARPS][32];
     __shared__ uint32_t s_tab[CE_WARPS][CE_TAB];
+    extern __shared__ uint32_t s_walk[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     if (*(volatile const int32_t *)stop) return;
     const int64_t kb = cbase[c0], ke = cbase[c1];
     CtlBox<N> *box = s_box[warp];
+    uint32_t *const ws = s_walk + (size_t)warp * S * walk_words(N);
+    int32_t *const e_ch = (int32_t *)ws;           // [e]
+    uint32_t *const e_meta = ws + S;               // [e]
+    int32_t *const e_idx = (int32_t *)(ws + 2 * S);   // [d S + e]
+    uint32_t *const e_md = ws + (2 + N) * S;       // [(2 d + h) S + e]
     unsigned long long pe = 0;
     // the cell set up in shared memory and registers (chunks of one cell are
     // consecutive, so a warp often keeps its cell across chunks)
@@ -266,12 +285,20 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
     bool use_tab = false;
 #pragma unroll
     for (int d = 0; d < N; d++) n0[d] = ua[d] = ext[d] = toff[d] = 0;
+    const int64_t nw8 = 8 * (int64_t)gridDim.x * CE_WARPS;
+    int64_t seen = 0;                              // lane 0: the counter as last seen
     for (;;) {
-    unsigned long long g0 = 0;
-    if (lane == 0) g0 = atomicAdd(grab, (unsigned long long)CE_GRAB);
+    long long g0 = 0, gn = 0;
+    if (lane == 0) {
+        gn = min((int64_t)16, max((int64_t)CE_GRAB, (ke - kb - seen) / nw8));
+        g0 = (long long)atomicAdd(grab, (unsigned long long)gn);
+        seen = g0 + gn;
+    }
     g0 = __shfl_sync(FULL, g0, 0);
+    gn = __shfl_sync(FULL, gn, 0);
     if (kb + (int64_t)g0 >= ke) break;
-    const int64_t gend = min(kb + (int64_t)g0 + CE_GRAB, ke);
+    const int64_t gend = min(kb + (int64_t)(g0 + gn), ke);
+    int64_t wpos = 0;                              // FILL: where the chunk's edges go
     for (int64_t k = kb + (int64_t)g0; k < gend; k++) {
         const int64_t s = chk_cell[k];
         if (s != cur) {
@@ -349,138 +376,146 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
         const InstDesc &I = *Ip;
         const int64_t r1 = min(nroots, (k - cb + 1) * CE_CHUNK);
         const bool small = r1 < ((int64_t)1 << 31);
-        int64_t next = (k - cb) * CE_CHUNK + lane;
-        int64_t wpos = FILL ? coff[s] + chk_off[k] - chk_off[cb] : 0;
-        // per-lane ring stack of (node, level, index, parent's mask)
-        int stn[STACK], stl[STACK], sti[STACK][N];
-        uint32_t stm[STACK];
-        int sb = 0, sp = 0;                        // entries sb .. sp-1 (mod STACK)
+        int64_t nbase = (k - cb) * CE_CHUNK;       // the chunk's next root (lane 0)
+        if (FILL && (k == cb || k == kb + (int64_t)g0))   // a run's first chunk
+            wpos = coff[s] + (k == cb ? 0 : chk_off[k] - chk_off[cb]);
+        int sp = 0;                                // stack entries
         int32_t nent = 0, myc = 0;
         uint32_t tch = 0;
         for (;;) {
-            // lanes with nothing left take the oldest entry of a lane holding two or more
-            const uint32_t idle = __ballot_sync(FULL, sp == sb && next >= r1);
-            if (idle) {
-                const uint32_t rich = __ballot_sync(FULL, sp - sb >= 2);
-                if (rich && idle != FULL) {
-                    const int nt = min(__popc(idle), __popc(rich));
-                    const bool donor = ((rich >> lane) & 1u) && __popc(rich & lt) < nt;
-                    const bool recv = ((idle >> lane) & 1u) && __popc(idle & lt) < nt;
-                    int gn = 0, gl = 0, gi[N];
-                    uint32_t gm = 0;
-#pragma unroll
-                    for (int d = 0; d < N; d++) gi[d] = 0;
-                    if (donor) {
-                        const int q = sb & (STACK - 1);
-                        gn = stn[q];
-                        gl = stl[q];
-#pragma unroll
-                        for (int d = 0; d < N; d++) gi[d] = sti[q][d];
-                        gm = stm[q];
-                        sb++;
-                    }
-                    const int src = recv ? nth_set(rich, __popc(idle & lt)) : lane;
-                    gn = __shfl_sync(FULL, gn, src);
-                    gl = __shfl_sync(FULL, gl, src);
-#pragma unroll
-                    for (int d = 0; d < N; d++) gi[d] = __shfl_sync(FULL, gi[d], src);
-                    gm = __shfl_sync(FULL, gm, src);
-                    if (recv) {
-                        sb = 0;
-                        sp = 1;
-                        stn[0] = gn;
-                        stl[0] = gl;
-#pragma unroll
-                        for (int d = 0; d < N; d++) sti[0][d] = gi[d];
-                        stm[0] = gm;
-                    }
-                }
-            }
             int node = -1, L = 0, idx[N];
-            uint32_t pm = live;
-            bool tested = false;                   // stack entries carry their own mask
-            if (sp != sb) {
-                const int q = (--sp) & (STACK - 1);
-                node = stn[q];
-                L = stl[q];
+            uint32_t m = 0;
+            bool root = false;
 #pragma unroll
-                for (int d = 0; d < N; d++) idx[d] = sti[q][d];
-                pm = stm[q];
-                tested = true;
-                if (sp == sb) sb = sp = 0;
-            } else if (next < r1) {
-                int r = 0;
-                if (small) {
-                    uint32_t q = (uint32_t)next;
+            for (int d = 0; d < N; d++) idx[d] = 0;
+            if (sp > 0) {
+                // lane j looks at entry sp-1-j; the top level's entries are a run
+                const int Lt = (int)(e_meta[sp - 1] >> 16);
+                const int e = sp - 1 - lane;
+                const uint32_t me = e >= 0 ? e_meta[e] : 0u;
+                const uint32_t gb = __ballot_sync(FULL, e >= 0 && (int)(me >> 16) == Lt);
+                const int ng = gb == FULL ? 32 : __ffs(~gb) - 1;
+                const bool mine = lane < ng;
+                const int cnt = mine ? __popc(me & 0xffffu) : 0;
+                int pre = cnt;
 #pragma unroll
-                    for (int d = N - 1; d > 0; d--) {
-                        const uint32_t qq = q / (uint32_t)ext[d];
-                        idx[d] = ua[d] + (int)(q - qq * (uint32_t)ext[d]);
-                        q = qq;
-                    }
-                    idx[0] = ua[0] + (int)q;
-                } else {
-                    int64_t q = next;
-#pragma unroll
-                    for (int d = N - 1; d >= 0; d--) {
-                        idx[d] = ua[d] + (int)(q % ext[d]);
-                        q /= ext[d];
-                    }
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(FULL, pre, o);
+                    if (lane >= o) pre += t;
                 }
+                const int start = pre - cnt;
+                const uint32_t B = __reduce_or_sync(FULL, (mine && start < 32) ? 1u << start : 0u);
+                const int total = __shfl_sync(FULL, pre, 31);
+                if (lane < total) {                // item `lane`: of the entry starting at or below it
+                    const uint32_t Bi = B & (FULL >> (31 - lane));
+                    const int q = sp - __popc(Bi);
+                    const int cc = nth_set(e_meta[q] & 0xffffu, lane - (31 - __clz(Bi)));
+                    node = e_ch[q] + cc;
+                    L = Lt;
+                    uint32_t mm = FULL;
 #pragma unroll
-                for (int d = 0; d < N; d++) r = r * n0[d] + idx[d];
-                node = r;
-                next += 32;
+                    for (int d = 0; d < N; d++) {
+                        const int h = (cc >> (N - 1 - d)) & 1;
+                        idx[d] = 2 * e_idx[d * S + q] + h;
+                        mm &= e_md[(2 * d + h) * S + q];
+                    }
+                    m = mm;
+                }
+                // pop the spent entries; the deepest one taken may keep children
+                const int nfull = __popc(__ballot_sync(FULL, mine && pre <= 32));
+                __syncwarp();
+                if (mine && lane == nfull && start < 32) {
+                    uint32_t rest = me & 0xffffu;
+                    for (int t = start; t < 32; t++) rest &= rest - 1u;
+                    e_meta[e] = (me & 0xffff0000u) | rest;
+                }
+                sp -= nfull;
+                __syncwarp();
+            } else if (nbase < r1) {
+                const int64_t rr = nbase + lane;
+                if (rr < r1) {
+                    if (small) {
+                        uint32_t q = (uint32_t)rr;
+#pragma unroll
+                        for (int d = N - 1; d > 0; d--) {
+                            const uint32_t qq = q / (uint32_t)ext[d];
+                            idx[d] = ua[d] + (int)(q - qq * (uint32_t)ext[d]);
+                            q = qq;
+                        }
+                        idx[0] = ua[0] + (int)q;
+                    } else {
+                        int64_t q = rr;
+#pragma unroll
+                        for (int d = N - 1; d >= 0; d--) {
+                            idx[d] = ua[d] + (int)(q % ext[d]);
+                            q /= ext[d];
+                        }
+                    }
+                    int r = 0;
+#pragma unroll
+                    for (int d = 0; d < N; d++) r = r * n0[d] + idx[d];
+                    node = r;
+                    root = true;
+                }
+                nbase += 32;
+            } else {
+                break;
             }
             const bool active = node >= 0;
-            if (!__any_sync(FULL, active)) break;
-            uint32_t m = 0;
             uint8_t st = ST_DEAD;
             int tslot = 0, tchild = 0;
+            bool push = false;
+            uint32_t md[N][2], cmap = 0;
             if (active) {
                 // the node's state, slot and first child are read together: one
                 // memory latency instead of a chain
                 st = I.state[node];
                 tslot = I.slot[node];
                 tchild = I.child[node];
-                if (tested) {
-                    m = pm;
-                } else if (use_tab) {               // a root cell
-                    m = pm;
+                if (root) {
+                    m = live;
+                    if (use_tab) {
 #pragma unroll
-                    for (int d = 0; d < N; d++) m &= s_tab[warp][toff[d] + idx[d] - ua[d]];
-                } else {
-                    const int sh = Lf - L;
-                    int clo[N], chi[N];
+                        for (int d = 0; d < N; d++) m &= s_tab[warp][toff[d] + idx[d] - ua[d]];
+                    } else {
+                        int clo[N], chi[N];
 #pragma unroll
-                    for (int d = 0; d < N; d++) {
-                        clo[d] = idx[d] << sh;
-                        chi[d] = (idx[d] + 1) << sh;
+                        for (int d = 0; d < N; d++) {
+                            clo[d] = idx[d] << Lf;
+                            chi[d] = (idx[d] + 1) << Lf;
+                        }
+                        m = ctl_mask<N>(box, nu, m, clo, chi);
                     }
-                    m = ctl_mask<N>(box, nu, pm, clo, chi);
                 }
                 if (m && st == ST_SPLIT) {
-                    if (sp - sb + (1 << N) > STACK) {
-                        atomicExch(err, GIS_EBOUNDS);
-                    } else {
-                        // push the children that meet a control, with their masks
-                        const int ch = tchild;
-                        uint32_t md[N][2];
-                        child_masks<N>(box, nu, m, idx, Lf - L - 1, md);
-                        for (int cc = (1 << N) - 1; cc >= 0; cc--) {
-                            const uint32_t mc = child_mask<N>(md, cc);
-                            if (!mc) continue;
-                            const int q = (sp++) & (STACK - 1);
-                            stn[q] = ch + cc;
-                            stl[q] = L + 1;
+                    child_masks<N>(box, nu, m, idx, Lf - L - 1, md);
 #pragma unroll
-                            for (int d = 0; d < N; d++) sti[q][d] = 2 * idx[d] + ((cc >> (N - 1 - d)) & 1);
-                            stm[q] = mc;
-                        }
-                    }
+                    for (int cc = 0; cc < (1 << N); cc++) cmap |= (uint32_t)(child_mask<N>(md, cc) != 0u) << cc;
+                    push = cmap != 0;
                 } else if (m && st == ST_DEAD) {
                     tch |= m;
                 }
+            }
+            const uint32_t pb = __ballot_sync(FULL, push);
+            if (pb) {
+                const int np = __popc(pb);
+                if (sp + np > S) {                 // not reached: S = 32 x the levels below the roots
+                    if (lane == 0) atomicExch(err, GIS_EBOUNDS);
+                } else {
+                    if (push) {
+                        const int q = sp + __popc(pb & lt);
+                        e_ch[q] = tchild;
+                        e_meta[q] = cmap | (uint32_t)(L + 1) << 16;
+#pragma unroll
+                        for (int d = 0; d < N; d++) {
+                            e_idx[d * S + q] = idx[d];
+                            e_md[2 * d * S + q] = md[d][0];
+                            e_md[(2 * d + 1) * S + q] = md[d][1];
+                        }
+                    }
+                    sp += np;
+                }
+                __syncwarp();
             }
             const bool emit = active && st == ST_ALIVE && m != 0;
             const uint32_t b = __ballot_sync(FULL, emit);
@@ -699,41 +734,56 @@ cudaError_t launch_cinc(bool fill, int n, const InstDesc *D, const WorkList &w, 
     return cudaGetLastError();
 }
 
-// Persistent grid: as many blocks as fit on the device at once.
+// Persistent grid: as many blocks as fit on the device at once, with `smem`
+// bytes of walk stacks per block (cached per device and depth).
 template <int N, bool FILL>
-static int cedges_grid(int dev)
+static int cedges_grid(int dev, int depth, size_t smem)
 {
-    static int cached[64] = {};
+    static int cached[64][MAXL + 2] = {};
+    static bool attr[64] = {};
     if (dev < 0 || dev >= 64) dev = 0;
-    if (!cached[dev]) {
-        int a = 0, sms = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_cedges<N, FILL>, CE_WARPS * 32, 0);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cached[dev] = std::max(1, a) * std::max(1, sms);
+    if (!attr[dev]) {
+        // the deepest subdivision a problem of dimension N may reach (the
+        // bound of check_depth), so that no later launch needs more
+        const int dmax = std::min(MAXL, (STACK - 1) / ((1 << N) - 1));
+        const size_t most = (size_t)CE_WARPS * 32 * std::max(dmax, 1) * walk_words(N) * sizeof(uint32_t);
+        cudaFuncSetAttribute(k_cedges<N, FILL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(most, smem));
+        attr[dev] = true;
     }
-    return cached[dev];
+    int &c = cached[dev][depth];
+    if (!c) {
+        int a = 0, sms = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_cedges<N, FILL>, CE_WARPS * 32, smem);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        c = std::max(1, a) * std::max(1, sms);
+    }
+    return c;
 }
 
-cudaError_t launch_cedges(bool fill, int n, const InstDesc *D, int64_t c0, int64_t c1, const int64_t *cbase,
-                          const ChunkWork &cw, unsigned long long *grab, const int32_t *cinst, const CellGraph &g,
-                          cudaStream_t st)
+cudaError_t launch_cedges(bool fill, int n, int depth, const InstDesc *D, int64_t c0, int64_t c1,
+                          const int64_t *cbase, const ChunkWork &cw, unsigned long long *grab, const int32_t *cinst,
+                          const CellGraph &g, cudaStream_t st)
 {
     if (c1 <= c0) return cudaSuccess;
+    if (depth < 0 || depth > MAXL) return cudaErrorInvalidValue;
     int dev = 0;
     cudaGetDevice(&dev);
     dim3 b(CE_WARPS * 32);
+    const int S = 32 * std::max(depth, 1);
 #define CE_CASE(NN)                                                                                        \
-    case NN:                                                                                               \
+    case NN: {                                                                                             \
+        const size_t smem = (size_t)CE_WARPS * S * walk_words(NN) * sizeof(uint32_t);                     \
         if (fill)                                                                                          \
-            k_cedges<NN, true><<<cedges_grid<NN, true>(dev), b, 0, st>>>(                                   \
-                D, c0, c1, cbase, cw.cell, cw.cnt, cw.off, grab, cw.stop, cinst, g.rng, g.pflag, g.pcnt,    \
+            k_cedges<NN, true><<<cedges_grid<NN, true>(dev, depth, smem), b, smem, st>>>(                   \
+                D, c0, c1, cbase, cw.cell, cw.cnt, cw.off, grab, cw.stop, S, cinst, g.rng, g.pflag, g.pcnt, \
                 g.ccnt, g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rsrc, g.rmask, g.pair_edges, g.err);     \
         else                                                                                               \
-            k_cedges<NN, false><<<cedges_grid<NN, false>(dev), b, 0, st>>>(                                 \
-                D, c0, c1, cbase, cw.cell, cw.cnt, cw.off, grab, cw.stop, cinst, g.rng, g.pflag, g.pcnt,    \
+            k_cedges<NN, false><<<cedges_grid<NN, false>(dev, depth, smem), b, smem, st>>>(                 \
+                D, c0, c1, cbase, cw.cell, cw.cnt, cw.off, grab, cw.stop, S, cinst, g.rng, g.pflag, g.pcnt, \
                 g.ccnt, g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rsrc, g.rmask, g.pair_edges, g.err);     \
         note_launch();                                                                                     \
-        break;
+        break;                                                                                             \
+    }
     switch (n) {
         CE_CASE(1) CE_CASE(2) CE_CASE(3) CE_CASE(4)
     default: return cudaErrorInvalidValue;
@@ -742,24 +792,30 @@ cudaError_t launch_cedges(bool fill, int n, const InstDesc *D, int64_t c0, int64
     return cudaGetLastError();
 }
 
-// The cell of every chunk; *stop = 1 (and nothing written) if there are more
-// chunks than the arrays hold.
+// The cell of every chunk; *stop = 1 (and no cell written) if there are more
+// chunks than the arrays hold. Zeroes the per-cell edge and in-degree counts.
 __global__ void __launch_bounds__(256) k_cexpand(const int64_t *__restrict__ cbase, int64_t NL, int64_t cap,
-                                                 int32_t *__restrict__ cell, int32_t *__restrict__ stop)
+                                                 int32_t *__restrict__ cell, int32_t *__restrict__ stop,
+                                                 int32_t *__restrict__ ccnt, int32_t *__restrict__ rcnt)
 {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < NL) {
+        ccnt[s] = 0;
+        rcnt[s] = 0;
+    }
     if (cbase[NL] > cap) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) *stop = 1;
+        if (s == 0) *stop = 1;
         return;
     }
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= NL) return;
     for (int64_t k = cbase[s]; k < cbase[s + 1]; k++) cell[k] = (int32_t)s;
 }
 
-cudaError_t launch_cexpand(const int64_t *cbase, int64_t NL, const ChunkWork &cw, cudaStream_t st)
+cudaError_t launch_cexpand(const int64_t *cbase, int64_t NL, const ChunkWork &cw, int32_t *ccnt, int32_t *rcnt,
+                           cudaStream_t st)
 {
     if (NL == 0) return cudaSuccess;
-    k_cexpand<<<(unsigned)((NL + 255) / 256), 256, 0, st>>>(cbase, NL, cw.cap, cw.cell, cw.stop);
+    k_cexpand<<<(unsigned)((NL + 255) / 256), 256, 0, st>>>(cbase, NL, cw.cap, cw.cell, cw.stop, ccnt, rcnt);
     note_launch();
     return cudaGetLastError();
 }

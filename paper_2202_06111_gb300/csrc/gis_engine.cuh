@@ -567,6 +567,7 @@ struct Engine {
     int32_t *chk_cell = nullptr, *chk_cnt = nullptr; size_t c_chk_cell = 0, c_chk_cnt = 0;
     int64_t *chk_off = nullptr; size_t c_chk_off = 0;
     int64_t chunk_hint = 0;     // chunks of the previous build
+    int64_t chunk_cells = 0;    // and its cells
     int32_t *rng = nullptr; size_t c_rng = 0;
     uint8_t *pflag = nullptr; size_t c_pflag = 0;
     int32_t *cnt = nullptr; size_t c_cnt = 0;
@@ -1119,6 +1120,8 @@ struct Engine {
         int64_t seg_base[MAXN + 2] = {0};
         for (int i : ids) seg_base[inst[i]->dyn.n + 1] += inst[i]->n_live;
         for (int n = 1; n <= MAXN; n++) seg_base[n + 1] += seg_base[n];
+        int seg_depth[MAXN + 1] = {0};             // deepest finest level per dimension
+        for (int i : ids) seg_depth[inst[i]->dyn.n] = std::max(seg_depth[inst[i]->dyn.n], inst[i]->Lf);
         auto carried = [&](int n) {
             std::vector<RangeSpec> r;
             for (int i : ids)
@@ -1130,30 +1133,28 @@ struct Engine {
         // are contiguous: number() orders the problems by dimension); the chunk
         // arrays are sized from the previous build and grown if they overflow
         timer.begin(PH_COUNT);
-        CK(launch_cchunks(d_desc, NL, cinst, rng, pflag, cnch, st));
+        CK(launch_cchunks(d_desc, NL, cinst, rng, pflag, cnch, pcnt, st));
         CK(launch_scan_i32(cnch, cbase, NL, scratch, st));
         timer.end();
         int64_t hEc = 0, K = 0;
         int32_t hq[8], hstop = 0;
-        int64_t cap = std::max<int64_t>(2 * NL + 4096, chunk_hint + chunk_hint / 4);
-        for (;;) {
+        // chunks per cell as in the previous build, with a margin
+        int64_t cap = 2 * NL + 4096;
+        if (chunk_hint > 0 && chunk_cells > 0)
+            cap = std::max<int64_t>(cap, (int64_t)((double)chunk_hint / (double)chunk_cells * 1.25 * (double)NL) + 4096);
+        for (int attempt = 0;; attempt++) {
             mem.ensure(chk_cell, c_chk_cell, (size_t)cap);
             mem.ensure(chk_cnt, c_chk_cnt, (size_t)cap);
-            mem.ensure(chk_off, c_chk_off, (size_t)cap + 1);
-            const ChunkWork cw{chk_cell, chk_cnt, chk_off, ctl + 18, cap};
-            mem.ensure(scratch, c_scratch, scan_scratch_bytes(std::max<int64_t>({P, NL, cap}) + 1));
+            const ChunkWork cw{chk_cell, chk_cnt, nullptr, ctl + 18, cap};
+            mem.ensure(scratch, c_scratch, scan_scratch_bytes(std::max<int64_t>(P, NL) + 1));
             timer.begin(PH_COUNT);
-            CK(cudaMemsetAsync(ctl + 18, 0, sizeof(int32_t), st));
-            CK(cudaMemsetAsync(ctl + 24, 0, 16 * sizeof(int32_t), st));
-            CK(cudaMemsetAsync(ctl + 12, 0, 2 * sizeof(int32_t), st));
-            CK(cudaMemsetAsync(rcnt, 0, NLs * sizeof(int32_t), st));
-            CK(cudaMemsetAsync(ccnt, 0, NLs * sizeof(int32_t), st));
-            CK(cudaMemsetAsync(pcnt, 0, Ps * sizeof(int32_t), st));
-            CK(cudaMemsetAsync(chk_cnt, 0, (size_t)cap * sizeof(int32_t), st));
-            CK(launch_cexpand(cbase, NL, cw, st));
+            // pair-edge total (12, 13), chunk-overflow flag (18), chunk counters (24 .. 39)
+            CK(cudaMemsetAsync(ctl + 12, 0, 28 * sizeof(int32_t), st));
+            if (attempt > 0) CK(cudaMemsetAsync(pcnt, 0, Ps * sizeof(int32_t), st));   // k_cinc ran
+            CK(launch_cexpand(cbase, NL, cw, ccnt, rcnt, st));
             for (int n = 1; n <= MAXN; n++)
-                CK(launch_cedges(false, n, d_desc, seg_base[n], seg_base[n + 1], cbase, cw, grab + (n - 1), cinst, g,
-                                 st));
+                CK(launch_cedges(false, n, seg_depth[n], d_desc, seg_base[n], seg_base[n + 1], cbase, cw,
+                                 grab + (n - 1), cinst, g, st));
             for (int n = 1; n <= MAXN; n++) {
                 const auto r = carried(n);
                 if (!r.empty()) CK(launch_cinc(false, n, d_desc, make_work(r, cedges_cells_per_block()), g, prev, st));
@@ -1162,7 +1163,6 @@ struct Engine {
             timer.begin(PH_SCAN);
             CK(launch_scan_i32(ccnt, coff, NL, scratch, st));
             CK(launch_scan_i32(rcnt, roff, NL, scratch, st));
-            CK(launch_scan_i32(chk_cnt, chk_off, cap, scratch, st));
             timer.end();
             unsigned char *hp = pinned(256);
             CK(cudaMemcpyAsync(hp, coff + NL, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -1178,6 +1178,7 @@ struct Engine {
             cap = K + K / 8 + 1024;                // the chunk arrays were too small: again
         }
         chunk_hint = K;
+        chunk_cells = NL;
         last_recheck = hq[0];
         if (last_recheck > 0) {
             cum.cum_recheck_samples += hq[4];
@@ -1196,13 +1197,25 @@ struct Engine {
         g.cmask = cmask;
         g.rsrc = rsrc;
         g.rmask = rmask;
+        // a cell of several chunks writes each chunk after the earlier ones
+        int64_t walked = NL;
+        for (int i : ids) walked -= inst[i]->n_carry;
+        int64_t *koff = nullptr;
+        if (K > walked) {
+            mem.ensure(chk_off, c_chk_off, (size_t)K + 1);
+            mem.ensure(scratch, c_scratch, scan_scratch_bytes(std::max<int64_t>({P, NL, K}) + 1));
+            timer.begin(PH_SCAN);
+            CK(launch_scan_i32(chk_cnt, chk_off, K, scratch, st));
+            timer.end();
+            koff = chk_off;
+        }
         timer.begin(PH_FILL);
         CK(cudaMemcpyAsync(rcur, roff, NLs * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
         {
-            const ChunkWork cw{chk_cell, chk_cnt, chk_off, ctl + 18, cap};
+            const ChunkWork cw{chk_cell, chk_cnt, koff, ctl + 18, cap};
             for (int n = 1; n <= MAXN; n++)
-                CK(launch_cedges(true, n, d_desc, seg_base[n], seg_base[n + 1], cbase, cw, grab + 4 + (n - 1), cinst,
-                                 g, st));
+                CK(launch_cedges(true, n, seg_depth[n], d_desc, seg_base[n], seg_base[n + 1], cbase, cw,
+                                 grab + 4 + (n - 1), cinst, g, st));
         }
         for (int n = 1; n <= MAXN; n++) {
             const auto r = carried(n);

@@ -130,11 +130,13 @@ struct CellPrev {
 };
 cudaError_t launch_cinc(bool fill, int n, const InstDesc *D, const WorkList &wcarried, const CellGraph &g,
                         const CellPrev &prev, cudaStream_t st);
-// per cell the chunk count of its union box (the work unit of the edge kernels)
+// per cell the chunk count of its union box (the work unit of the edge
+// kernels); zeroes the per-pair target counts pcnt
 cudaError_t launch_cchunks(const InstDesc *D, int64_t NL, const int32_t *cinst, const int32_t *rng,
-                           const uint8_t *pflag, int32_t *nch, cudaStream_t st);
-// chunks of the edge walk: the cell of each chunk, its edge count and the
-// exclusive scan of the counts; cap entries; *stop = 1 when cap is too small
+                           const uint8_t *pflag, int32_t *nch, int32_t *pcnt, cudaStream_t st);
+// chunks of the edge walk: the cell of each chunk, its edge count and (for
+// the fill, where a cell has several chunks) the exclusive scan of the counts;
+// cap entries; *stop = 1 when cap is too small
 struct ChunkWork {
     int32_t *cell;
     int32_t *cnt;
@@ -142,12 +144,15 @@ struct ChunkWork {
     int32_t *stop;
     int64_t cap;
 };
-cudaError_t launch_cexpand(const int64_t *cbase, int64_t NL, const ChunkWork &cw, cudaStream_t st);
-// edges of the walked cells c0 <= s < c1, all of dimension n; cbase = exclusive
-// scan of the chunk counts; grab: the chunk counter of this launch (zeroed)
-cudaError_t launch_cedges(bool fill, int n, const InstDesc *D, int64_t c0, int64_t c1, const int64_t *cbase,
-                          const ChunkWork &cw, unsigned long long *grab, const int32_t *cinst, const CellGraph &g,
-                          cudaStream_t st);
+// the cell of each chunk; zeroes the per-cell counts ccnt and rcnt
+cudaError_t launch_cexpand(const int64_t *cbase, int64_t NL, const ChunkWork &cw, int32_t *ccnt, int32_t *rcnt,
+                           cudaStream_t st);
+// edges of the walked cells c0 <= s < c1, all of dimension n and at most
+// `depth` levels below their roots; cbase = exclusive scan of the chunk
+// counts; grab: the chunk counter of this launch (zeroed)
+cudaError_t launch_cedges(bool fill, int n, int depth, const InstDesc *D, int64_t c0, int64_t c1,
+                          const int64_t *cbase, const ChunkWork &cw, unsigned long long *grab, const int32_t *cinst,
+                          const CellGraph &g, cudaStream_t st);
 int cedges_cells_per_block();     // cells per block of k_cinc
 cudaError_t launch_cprune_init(const InstDesc *D, const WorkList &wslots, const uint8_t *pflag, const int32_t *pcnt,
                                int32_t *pc, uint32_t *vmask, uint8_t *alive, int32_t *frontier0, uint32_t *sizes,
