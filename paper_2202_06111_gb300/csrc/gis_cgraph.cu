@@ -62,7 +62,7 @@ cudaError_t launch_cgather(const InstDesc *D, const WorkList &w, int32_t *cps, u
 }
 
 constexpr int CE_WARPS = 8;      // cells (warps) per block
-constexpr int CE_TAB = 224;      // per-warp table of root masks per dimension (entries)
+constexpr int CE_TAB = 512;      // per-warp tables of control sets per dimension (entries)
 constexpr int CE_GRAB = 4;       // fewest chunks a warp takes at a time
 
 __device__ __forceinline__ int warp_min(int v)
@@ -344,13 +344,17 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
             nroots *= live ? ext[d] : 1;
         }
         __syncwarp();
-        // root cells' control masks per dimension: tab[off_d + x - ua_d] holds the
-        // controls whose level-0 range on d holds x; a root's mask is the AND over d
+        // per dimension and finest-level coordinate x of the union box (x0 =
+        // ua << Lf <= x <= (ub + 1) << Lf): tab[off_d + 2 (x - x0)] holds the
+        // controls with c <= x, tab[off_d + 2 (x - x0) + 1] those with f >= x. A
+        // node spanning [lo, hi] at the finest level meets control u iff
+        // hi >= c_u and lo <= f_u, so its mask is the AND over d of
+        // tab[.. hi ..] & tab[.. lo .. + 1]: two loads per dimension
         int tsum = 0;
 #pragma unroll
         for (int d = 0; d < N; d++) {
             toff[d] = tsum;
-            tsum += live ? ext[d] : 0;
+            tsum += live ? 2 * ((ext[d] << Lf) + 1) : 0;
         }
         use_tab = live && tsum <= CE_TAB;
         if (use_tab) {
@@ -359,12 +363,13 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
                 int d = 0;
 #pragma unroll
                 for (int e = 1; e < N; e++) d += j >= toff[e];
-                const int x = ua[d] + j - toff[d];
-                const int lo = x << Lf, hi = (x + 1) << Lf;
+                const int r = j - toff[d];
+                const int x = (ua[d] << Lf) + (r >> 1);
                 uint32_t mk = 0;
-                for (int u = 0; u < nu; u++) {
-                    const CtlBox<N> bu = box[u];
-                    mk |= (uint32_t)(hi >= bu.cf[2 * d] && lo <= bu.cf[2 * d + 1]) << u;
+                if (r & 1) {
+                    for (int u = 0; u < nu; u++) mk |= (uint32_t)(box[u].cf[2 * d + 1] >= x) << u;
+                } else {
+                    for (int u = 0; u < nu; u++) mk |= (uint32_t)(box[u].cf[2 * d] <= x) << u;
                 }
                 tab[j] = mk & live;
             }
@@ -475,8 +480,12 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
                 if (root) {
                     m = live;
                     if (use_tab) {
+                        const uint32_t *tab = s_tab[warp];
 #pragma unroll
-                        for (int d = 0; d < N; d++) m &= s_tab[warp][toff[d] + idx[d] - ua[d]];
+                        for (int d = 0; d < N; d++) {
+                            const int r = 2 * ((idx[d] - ua[d]) << Lf) + toff[d];
+                            m &= tab[r + (2 << Lf)] & tab[r + 1];
+                        }
                     } else {
                         int clo[N], chi[N];
 #pragma unroll
@@ -488,7 +497,20 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
                     }
                 }
                 if (m && st == ST_SPLIT) {
-                    child_masks<N>(box, nu, m, idx, Lf - L - 1, md);
+                    if (use_tab) {
+                        // halves [e0, e1] and [e1, e2] of the node on each dimension
+                        const uint32_t *tab = s_tab[warp];
+                        const int sh = Lf - L - 1;
+#pragma unroll
+                        for (int d = 0; d < N; d++) {
+                            const int r = toff[d] + 2 * ((2 * idx[d] - (ua[d] << (L + 1))) << sh);
+                            const int w = 2 << sh;
+                            md[d][0] = tab[r + w] & tab[r + 1] & m;
+                            md[d][1] = tab[r + 2 * w] & tab[r + w + 1] & m;
+                        }
+                    } else {
+                        child_masks<N>(box, nu, m, idx, Lf - L - 1, md);
+                    }
 #pragma unroll
                     for (int cc = 0; cc < (1 << N); cc++) cmap |= (uint32_t)(child_mask<N>(md, cc) != 0u) << cc;
                     push = cmap != 0;
