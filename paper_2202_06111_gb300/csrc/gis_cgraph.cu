@@ -31,11 +31,10 @@ namespace gis {
     const InstDesc &I = D[rg.inst];
 
 // Global slot of every live node; per cell the index of its first pair, its
-// control count / rule (cinfo = n_controls | rule << 6), its problem, its node
-// and the slot the node had at the previous level (meaningful for carried cells).
+// problem, its node and the slot the node had at the previous level
+// (meaningful for carried cells).
 __global__ void __launch_bounds__(256) k_cgather(const InstDesc *__restrict__ D, const Range *__restrict__ R, int nr,
-                                                 int32_t *__restrict__ cps, uint8_t *__restrict__ cinfo,
-                                                 int32_t *__restrict__ cinst, int32_t *__restrict__ s2n,
+                                                 int32_t *__restrict__ cps, int32_t *__restrict__ cinst, int32_t *__restrict__ s2n,
                                                  int32_t *__restrict__ oslot)
 {
     CRANGE_HEAD(256)
@@ -47,16 +46,15 @@ __global__ void __launch_bounds__(256) k_cgather(const InstDesc *__restrict__ D,
     if (ls < I.n_carry) oslot[s] = I.slot[node];
     I.slot[node] = (int32_t)s;
     cps[s] = (int32_t)(I.pair_base + (int64_t)ls * I.nu);
-    cinfo[s] = (uint8_t)(I.nu | (I.rule << 6));
     cinst[s] = rg.inst;
     s2n[s] = node;
 }
 
-cudaError_t launch_cgather(const InstDesc *D, const WorkList &w, int32_t *cps, uint8_t *cinfo, int32_t *cinst,
-                           int32_t *s2n, int32_t *oslot, cudaStream_t st)
+cudaError_t launch_cgather(const InstDesc *D, const WorkList &w, int32_t *cps, int32_t *cinst, int32_t *s2n,
+                           int32_t *oslot, cudaStream_t st)
 {
     if (w.n_blocks == 0) return cudaSuccess;
-    k_cgather<<<(unsigned)w.n_blocks, 256, 0, st>>>(D, w.d_ranges, w.n_ranges, cps, cinfo, cinst, s2n, oslot);
+    k_cgather<<<(unsigned)w.n_blocks, 256, 0, st>>>(D, w.d_ranges, w.n_ranges, cps, cinst, s2n, oslot);
     note_launch();
     return cudaGetLastError();
 }
@@ -845,16 +843,26 @@ cudaError_t launch_cexpand(const int64_t *cbase, int64_t NL, const ChunkWork &cw
 int cedges_cells_per_block() { return CE_WARPS; }
 
 // ---------------------------------------------------------------------------
-// Prune on the cell graph. vmask[i] holds the controls of cell i that are
-// still viable: INNER -- image in X, no removed cell touched, every target
-// kept; OUTER -- some target kept (pc[pair] counts its kept targets). A cell
-// dies when its mask empties; dying cells form the next frontier.
+// Prune on the cell graph. A cell dies when no control is left viable:
+// INNER -- image in X, no removed cell touched, every target kept (vmask[i],
+// the viable controls, loses an edge's controls when its target dies); OUTER
+// -- some target kept. OUTER counts the kept targets of each (cell, control);
+// when the counts fit, a cell keeps them in bit fields of one 64-bit word pk
+// (64 / n_controls bits each), so that a dying target takes one atomic per
+// reverse edge and the cell dies exactly when its word reaches 0 (no borrow:
+// a field is decremented once per kept target it counts). Otherwise the
+// counts are per pair (pc) beside vmask. pinfo[i]: bit 7 packed, bit 6 OUTER,
+// bits 0-5 the field width - 1.
 // ---------------------------------------------------------------------------
+constexpr uint8_t PI_PACKED = 0x80, PI_OUTER = 0x40;
+
 __global__ void __launch_bounds__(256) k_cprune_init(const InstDesc *__restrict__ D, const Range *__restrict__ R,
                                                      int nr, const uint8_t *__restrict__ pflag,
                                                      const int32_t *__restrict__ pcnt, int32_t *__restrict__ pc,
-                                                     uint32_t *__restrict__ vmask, uint8_t *__restrict__ alive,
-                                                     int32_t *__restrict__ frontier0, uint32_t *__restrict__ sizes)
+                                                     unsigned long long *__restrict__ pk,
+                                                     uint8_t *__restrict__ pinfo, uint32_t *__restrict__ vmask,
+                                                     uint8_t *__restrict__ alive, int32_t *__restrict__ frontier0,
+                                                     uint32_t *__restrict__ sizes)
 {
     CRANGE_HEAD(256)
     const int64_t local = (int64_t)(blockIdx.x - rg.block_start) * 256 + threadIdx.x;
@@ -862,43 +870,89 @@ __global__ void __launch_bounds__(256) k_cprune_init(const InstDesc *__restrict_
     const int64_t s = rg.first + local;
     const int64_t p0 = I.pair_base + (s - I.slot_base) * I.nu;
     uint32_t m = 0;
-    for (int u = 0; u < I.nu; u++) {
-        const int64_t p = p0 + u;
-        bool v;
-        if (I.rule == GIS_RULE_OUTER) {
-            const int32_t c = pcnt[p];
-            pc[p] = c;
-            v = c > 0;
-        } else {
-            const uint8_t f = pflag[p];
-            v = (f & PF_INX) && !(f & (PF_TOUCH_DEAD | PF_NONFINITE));
+    uint8_t info = 0;
+    if (I.rule == GIS_RULE_OUTER) {
+        const int w = 64 / I.nu;
+        const int64_t cmax = w >= 32 ? (int64_t)INT_MAX : ((int64_t)1 << w) - 2;
+        unsigned long long word = 0;
+        bool fits = true;
+        for (int u = 0; u < I.nu; u++) {
+            const int32_t c = pcnt[p0 + u];
+            m |= (uint32_t)(c > 0) << u;
+            fits = fits && c <= cmax;
+            word += (unsigned long long)c << (w * u);
         }
-        m |= (uint32_t)v << u;
+        if (fits) {
+            pk[s] = word;
+            info = PI_PACKED | PI_OUTER | (uint8_t)(w - 1);
+        } else {
+            for (int u = 0; u < I.nu; u++) pc[p0 + u] = pcnt[p0 + u];
+            info = PI_OUTER;
+        }
+    } else {
+        for (int u = 0; u < I.nu; u++) {
+            const uint8_t f = pflag[p0 + u];
+            m |= (uint32_t)((f & PF_INX) && !(f & (PF_TOUCH_DEAD | PF_NONFINITE))) << u;
+        }
     }
+    pinfo[s] = info;
     vmask[s] = m;
     alive[s] = m != 0;
     if (m == 0) frontier0[atomicAdd(&sizes[0], 1u)] = (int32_t)s;
 }
 
 cudaError_t launch_cprune_init(const InstDesc *D, const WorkList &w, const uint8_t *pflag, const int32_t *pcnt,
-                               int32_t *pc, uint32_t *vmask, uint8_t *alive, int32_t *frontier0, uint32_t *sizes,
-                               cudaStream_t st)
+                               int32_t *pc, unsigned long long *pk, uint8_t *pinfo, uint32_t *vmask, uint8_t *alive,
+                               int32_t *frontier0, uint32_t *sizes, cudaStream_t st)
 {
     if (w.n_blocks == 0) return cudaSuccess;
-    k_cprune_init<<<(unsigned)w.n_blocks, 256, 0, st>>>(D, w.d_ranges, w.n_ranges, pflag, pcnt, pc, vmask, alive,
-                                                        frontier0, sizes);
+    k_cprune_init<<<(unsigned)w.n_blocks, 256, 0, st>>>(D, w.d_ranges, w.n_ranges, pflag, pcnt, pc, pk, pinfo, vmask,
+                                                        alive, frontier0, sizes);
     note_launch();
     return cudaGetLastError();
 }
 
+// The controls of cell i that lose their last kept target when a target
+// reached by the controls m dies; true when the cell dies with them.
+__device__ __forceinline__ bool cprune_visit(const CPruneArgs &a, int i, uint32_t m)
+{
+    const uint8_t info = a.pinfo[i];
+    if (info & PI_PACKED) {
+        const int w = (info & 63) + 1;
+        unsigned long long sub = 0;
+        for (uint32_t mm = m; mm; mm &= mm - 1) sub += 1ull << (w * (__ffs(mm) - 1));
+        return atomicAdd(&a.pk[i], 0ull - sub) == sub;
+    }
+    if (info & PI_OUTER) {
+        const int32_t p0 = a.cps[i];
+        bool died = false;
+        for (uint32_t mm = m; mm; mm &= mm - 1) {
+            const int u = __ffs(mm) - 1;
+            if (atomicSub(&a.pc[p0 + u], 1) == 1) {
+                const uint32_t bit = 1u << u;
+                died = died || atomicAnd(&a.vmask[i], ~bit) == bit;
+            }
+        }
+        return died;
+    }
+    const uint32_t old = atomicAnd(&a.vmask[i], ~m);
+    return old != 0 && (old & ~m) == 0;
+}
+
+// The frontier rounds in one cooperative launch: a warp takes a dying cell and
+// walks its reverse edges, two per lane at a time (more gathers in flight);
+// cells dying in a round are appended, a warp at a time, to the next frontier.
 __global__ void __launch_bounds__(256) k_cprune(CPruneArgs a)
 {
+    constexpr uint32_t FULL = 0xffffffffu;
     __shared__ uint32_t s_nf;
     const int wpb = blockDim.x / 32;
     const int nwarps = gridDim.x * wpb;
     const int gw = blockIdx.x * wpb + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
     uint32_t target = 0;
+    unsigned long long walked = 0;
     int round = 0;
     for (;; round++) {
         target += gridDim.x;
@@ -920,33 +974,36 @@ __global__ void __launch_bounds__(256) k_cprune(CPruneArgs a)
             const int j = __ldcg(&F[it]);
             const int64_t e1 = a.roff[j + 1];
             const int64_t e0 = a.roff[j];
-            if (lane == 0) atomicAdd(a.scanned, (unsigned long long)(e1 - e0));
-            for (int64_t e = e0 + lane; e < e1; e += 32) {
-                const int i = a.rsrc[e];
-                const uint32_t m = a.rmask[e];
-                const uint8_t info = a.cinfo[i];
-                bool died = false;
-                if ((info >> 6) == GIS_RULE_INNER) {
-                    const uint32_t old = atomicAnd(&a.vmask[i], ~m);
-                    died = old != 0 && (old & ~m) == 0;
-                } else {
-                    const int32_t p0 = a.cps[i];
-                    for (uint32_t mm = m; mm; mm &= mm - 1) {
-                        const int u = __ffs(mm) - 1;
-                        if (atomicSub(&a.pc[p0 + u], 1) == 1) {
-                            const uint32_t bit = 1u << u;
-                            const uint32_t old = atomicAnd(&a.vmask[i], ~bit);
-                            died = died || old == bit;
-                        }
-                    }
+            walked += (unsigned long long)(e1 - e0);
+            for (int64_t eb = e0; eb < e1; eb += 64) {
+                const int64_t e = eb + lane;
+                const bool h0 = e < e1, h1 = e + 32 < e1;
+                int i0 = 0, i1 = 0;
+                uint32_t m0 = 0, m1 = 0;
+                if (h0) {
+                    i0 = __ldcs(&a.rsrc[e]);
+                    m0 = __ldcs(&a.rmask[e]);
                 }
-                if (died) {
-                    a.alive[i] = 0;
-                    Fn[atomicAdd(nsz, 1u)] = i;
+                if (h1) {
+                    i1 = __ldcs(&a.rsrc[e + 32]);
+                    m1 = __ldcs(&a.rmask[e + 32]);
+                }
+                const bool d0 = h0 && cprune_visit(a, i0, m0);
+                const bool d1 = h1 && cprune_visit(a, i1, m1);
+                if (d0) a.alive[i0] = 0;
+                if (d1) a.alive[i1] = 0;
+                const uint32_t b0 = __ballot_sync(FULL, d0), b1 = __ballot_sync(FULL, d1);
+                if (b0 | b1) {
+                    uint32_t base = 0;
+                    if (lane == 0) base = atomicAdd(nsz, (uint32_t)(__popc(b0) + __popc(b1)));
+                    base = __shfl_sync(FULL, base, 0);
+                    if (d0) Fn[base + __popc(b0 & lt)] = i0;
+                    if (d1) Fn[base + __popc(b0) + __popc(b1 & lt)] = i1;
                 }
             }
         }
     }
+    if (lane == 0 && walked) atomicAdd(a.scanned, walked);
     if (blockIdx.x == 0 && threadIdx.x == 0) *a.rounds = round;
 }
 
@@ -958,8 +1015,11 @@ cudaError_t launch_cprune(const CPruneArgs &a, int64_t n_slots, cudaStream_t st)
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cprune, 256, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int64_t want = (n_slots + 7) / 8;
-    const int64_t cap = (int64_t)sms * (per_sm < 2 ? per_sm : 2);
+    // a block per 256 cells, up to every block that fits (a cooperative launch
+    // needs them all resident): large graphs get the most gathers in flight,
+    // small ones cheaper grid barriers
+    const int64_t want = (n_slots + 255) / 256;
+    const int64_t cap = (int64_t)sms * per_sm;
     const int blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
     CPruneArgs args = a;
     void *params[] = {&args};

@@ -542,7 +542,8 @@ struct Engine {
     int32_t *pair_slot = nullptr; size_t c_pair_slot = 0;
     int64_t Ecell = 0;
     int32_t *cps = nullptr; size_t c_cps = 0;
-    uint8_t *cinfo = nullptr; size_t c_cinfo = 0;
+    uint8_t *pinfo = nullptr; size_t c_pinfo = 0;
+    unsigned long long *pk = nullptr; size_t c_pk = 0;
     int32_t *pcnt = nullptr; size_t c_pcnt = 0;
     int32_t *ccnt = nullptr; size_t c_ccnt = 0;
     int64_t *coff = nullptr; size_t c_coff = 0;
@@ -961,11 +962,10 @@ struct Engine {
         timer.begin(PH_OTHER);
         WorkList ws = make_work(slot_ranges(ids), 256);
         mem.ensure(cps, c_cps, NLs);
-        mem.ensure(cinfo, c_cinfo, NLs);
         mem.ensure(cinst, c_cinst, NLs);
         mem.ensure(s2n, c_s2n, NLs);
         mem.ensure(oslot, c_oslot, NLs);
-        CK(launch_cgather(d_desc, ws, cps, cinfo, cinst, s2n, oslot, st));
+        CK(launch_cgather(d_desc, ws, cps, cinst, s2n, oslot, st));
         timer.end();
 
         // propagation of new cells, grouped by (dynamics, n, precision, lanes)
@@ -1263,17 +1263,21 @@ struct Engine {
         mem.ensure(alive, c_alive, NLs);
         mem.ensure(front[0], c_front[0], NLs);
         mem.ensure(front[1], c_front[1], NLs);
+        mem.ensure(pinfo, c_pinfo, NLs);
+        mem.ensure(pk, c_pk, NLs);
         timer.begin(PH_PRUNE);
         CK(cudaMemsetAsync(ctl, 0, 6 * sizeof(int32_t), st));
         CK(cudaMemsetAsync(ctl + 8, 0, 2 * sizeof(int32_t), st));
         WorkList ws = make_work(slot_ranges(step), 256);
-        CK(launch_cprune_init(d_desc, ws, pflag, pcnt, pstate, vmask, alive, front[0], (uint32_t *)ctl, st));
+        CK(launch_cprune_init(d_desc, ws, pflag, pcnt, pstate, pk, pinfo, vmask, alive, front[0], (uint32_t *)ctl,
+                              st));
         CPruneArgs a{};
         a.roff = roff;
         a.rsrc = rsrc;
         a.rmask = rmask;
         a.cps = cps;
-        a.cinfo = cinfo;
+        a.pinfo = pinfo;
+        a.pk = pk;
         a.pc = pstate;
         a.vmask = vmask;
         a.alive = alive;

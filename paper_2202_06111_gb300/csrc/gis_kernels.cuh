@@ -115,7 +115,7 @@ struct CellGraph {
     unsigned long long *pair_edges;  // total (cell, control) -> cell edges
     int32_t *err;
 };
-cudaError_t launch_cgather(const InstDesc *D, const WorkList &wslots, int32_t *cps, uint8_t *cinfo, int32_t *cinst,
+cudaError_t launch_cgather(const InstDesc *D, const WorkList &wslots, int32_t *cps, int32_t *cinst,
                            int32_t *s2n, int32_t *oslot, cudaStream_t st);
 // the previous level's graph, for cells carried over
 struct CellPrev {
@@ -155,15 +155,16 @@ cudaError_t launch_cedges(bool fill, int n, int depth, const InstDesc *D, int64_
                           const CellGraph &g, cudaStream_t st);
 int cedges_cells_per_block();     // cells per block of k_cinc
 cudaError_t launch_cprune_init(const InstDesc *D, const WorkList &wslots, const uint8_t *pflag, const int32_t *pcnt,
-                               int32_t *pc, uint32_t *vmask, uint8_t *alive, int32_t *frontier0, uint32_t *sizes,
-                               cudaStream_t st);
+                               int32_t *pc, unsigned long long *pk, uint8_t *pinfo, uint32_t *vmask, uint8_t *alive,
+                               int32_t *frontier0, uint32_t *sizes, cudaStream_t st);
 struct CPruneArgs {
     const int64_t *roff;
     const int32_t *rsrc;
     const uint32_t *rmask;
     const int32_t *cps;          // first pair of each cell
-    const uint8_t *cinfo;        // n_controls | rule << 6
-    int32_t *pc;                 // OUTER: kept targets per pair
+    const uint8_t *pinfo;        // per cell: packed OUTER counts, OUTER, field width - 1
+    int32_t *pc;                 // OUTER, unpacked: kept targets per pair
+    unsigned long long *pk;      // OUTER, packed: kept targets per control in bit fields
     uint32_t *vmask;             // viable controls per cell
     uint8_t *alive;
     int32_t *frontier[2];

@@ -103,6 +103,17 @@ def test_closed_form_doubling_map(gis, n0, rule):
     run_both(gis, prob, 2)
 
 
+@pytest.mark.parametrize("nu", [1, 3, 32])
+def test_outer_prune_count_words(gis, nu):
+    """OUTER counts kept targets per (cell, control): packed into 64 / nu bit
+    fields of one word when they fit (nu = 1: one 64-bit field; nu = 3: 21
+    bits), per pair otherwise (nu = 32: 2-bit fields hold at most 2 targets,
+    and these images meet up to 9 cells)."""
+    prob = W.problem(W.linmap([[1.3, 0.2], [-0.1, 1.25]], [[0.6], [0.3]]), [-1.0, -1.0], [1.0, 1.0], [12, 10], 3,
+                     W.controls_grid(-0.5, 0.5, nu), 1.0, 0, rule="outer", precision="fp32")
+    run_both(gis, prob, 2)
+
+
 def test_everything_leaves(gis):
     """x+ = 2x + 3: every image leaves X, nothing is kept, no split."""
     prob = W.problem(W.linmap([[2.0]], [[1.0]]), [-1.0], [1.0], 16, 2, [[3.0]], 1.0, 0, precision="fp32")
