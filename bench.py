@@ -315,6 +315,11 @@ def run_gis(a, prob):
             "recheck_fp64_pairs_per_step": agg["cum_recheck_fp64"] / len(stats),
             "pairs_propagated_per_step": agg["cum_pairs_propagated"] / len(stats),
             "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
+            "shapes": {"lattice_tile_cells": stats[-1]["lattice_tile_cells"],
+                       "sibling_parents": stats[-1]["sibling_parents"],
+                       "lanes_per_pair": stats[-1]["lanes_per_pair"],
+                       "picked_by": "autotuner, timed during the warm-up solves",
+                       "tune_launches_timed": agg["cum_tune_launches"]},
             "fp64_plain": {"ms_per_step": statistics.mean(fp64_ms),
                            "speedup_of_fp32_recheck": statistics.mean(fp64_ms) / (total_ms / len(per_step)),
                            "same_cells_built": same},

@@ -112,7 +112,12 @@ typedef struct {
     int32_t enclosure_store; /* FP64 enclosures of rechecked extremes: 0 = auto
                                 (dense while the roots' store is under 1 GB),
                                 1 = dense per (cell, control), 2 = compact      */
-    int32_t reserved;
+    int32_t fixed_shapes;   /* 0: propagation shapes (lattice tile, sibling-lattice
+                               parents per block, lanes per pair) picked by the
+                               autotuner, which times the candidates on a prefix of
+                               the first work of each kind (per dynamics, n, samples
+                               per dimension, controls; cached for the process);
+                               1: the built-in choices. Results do not depend on it */
 } gis_options;
 
 /* One live cell: box = prod [lo + idx w_level, lo + (idx+1) w_level],
@@ -166,6 +171,10 @@ typedef struct {
                                (cell, control) -> cell edges                       */
     int64_t cum_cell_edges;
     int64_t cum_recheck_fp64; /* rechecked pairs that needed FP64 samples          */
+    int32_t lattice_tile_cells; /* root cells per lattice block of the first build
+                                   (0: no lattice kernel)                          */
+    int32_t sibling_parents;  /* parents per sibling-lattice block (0: none)        */
+    int64_t cum_tune_launches; /* launches the autotuner timed                      */
 } gis_stats;
 
 typedef struct gis_ctx gis_ctx;

@@ -190,15 +190,34 @@ __device__ __forceinline__ Ball bfma(Ball a, Ball b, Ball c)
 // |a/b - am/bm| <= (|am| rb + |bm| ra) / (|bm| (|bm| - rb)) when |bm| > rb;
 // the quotient of the bound is rounded to nearest (within 2^-24 of itself) and
 // raised by 2^-23 upward. |bm| <= rb gives the non-finite ball.
+// FAST: both quotients by __fdividef, within 2 ulp (so 2^-22 relative) for
+// divisors in [2^-126, 2^126] (CUDA's documented bound): the bound's quotient
+// raised by 2^-21, the midpoint's error counted as 2 ulp. Cheaper and fewer
+// registers; the balls are a little wider, which costs rechecks on some
+// models and not on others, so each model picks.
+__device__ __forceinline__ bool fdiv_ok(float y)
+{
+    const float a = fabsf(y);
+    return a >= 1.17549435e-38f && a <= 8.50705917e37f;
+}
+template <bool FAST = false>
 __device__ __forceinline__ Ball bdiv(Ball a, Ball b)
 {
     const float ab = fabsf(b.m);
-    const float m = a.m / b.m;
     const float num = __fmaf_ru(fabsf(a.m), b.r, __fmul_ru(ab, a.r));
     const float den = __fmul_rd(ab, __fsub_rd(ab, b.r));
-    const float q = __fmul_ru(num / den, 1.00000012f);
     const bool ok = ab > b.r;
-    return {ok ? m : NAN, ok ? __fadd_ru(q, b_rerr(m)) : INFINITY};
+    float q, m, em;
+    if (FAST && fdiv_ok(den)) q = __fmul_ru(__fdividef(num, den), 1.00000048f);
+    else q = __fmul_ru(num / den, 1.00000012f);
+    if (FAST && fdiv_ok(b.m)) {
+        m = __fdividef(a.m, b.m);
+        em = __fmaf_ru(fabsf(m), B_F, B_ETA);
+    } else {
+        m = a.m / b.m;
+        em = b_rerr(m);
+    }
+    return {ok ? m : NAN, ok ? __fadd_ru(q, em) : INFINITY};
 }
 // exp is increasing and e^r - 1 <= r + r^2 for r <= 1: over [m - r, m + r]
 // the ball is expf(m) with radius e^m (r + r^2) plus the library error
@@ -213,10 +232,19 @@ __device__ __forceinline__ Ball bexp(Ball a)
     return {ok ? e : NAN, ok ? __fmaf_ru(eup, grow, __fmaf_ru(e, B_F, B_ETA)) : INFINITY};
 }
 
-// sin and cos are 1-Lipschitz
+// sin and cos are 1-Lipschitz. On [-pi, pi] the hardware approximations,
+// within 2^-21.41 < 3.6e-7 absolute there (CUDA's documented bound for
+// __sinf / __cosf / __sincosf); elsewhere sincosf, within 2 ulp.
 __device__ __forceinline__ void bsincos(Ball a, Ball *s, Ball *c)
 {
     float sm, cm;
+    if (fabsf(a.m) <= 3.14159f) {
+        __sincosf(a.m, &sm, &cm);
+        s->m = sm;
+        c->m = cm;
+        s->r = c->r = __fadd_ru(a.r, 3.6e-7f);
+        return;
+    }
     sincosf(a.m, &sm, &cm);
     s->m = sm;
     s->r = __fadd_ru(a.r, __fmaf_ru(fabsf(sm), B_F, B_ETA));
@@ -278,7 +306,7 @@ struct DynCartpole {  // p32: g, 1/tot, pml, l, mp, 4/3    p64: mc, mp, l, g, to
         bsincos(x[2], &s, &c);
         const Ball temp = bmul(bfma(bmul(bmul(M.P(2), x[3]), x[3]), s, u[0]), M.P(1));
         const Ball den = bmul(M.P(3), bfma(bmul(bmul(bneg(M.P(4)), c), c), M.P(1), M.P(5)));
-        const Ball thacc = bdiv(bfma(M.P(0), s, bneg(bmul(c, temp))), den);
+        const Ball thacc = bdiv<true>(bfma(M.P(0), s, bneg(bmul(c, temp))), den);
         dx[0] = x[1];
         dx[1] = bfma(bmul(bmul(bneg(M.P(2)), thacc), c), M.P(1), temp);
         dx[2] = x[3];

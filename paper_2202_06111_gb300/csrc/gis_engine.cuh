@@ -20,6 +20,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "gis.h"
@@ -235,8 +236,32 @@ struct Inst {
     float *u32 = nullptr, *ur32 = nullptr, *udd = nullptr;
     double *u64 = nullptr;
     bool udd_ok = true;
+    // propagation shapes (0: built-in): root cells per lattice block, parents
+    // per sibling-lattice block, lanes per pair
+    int lat_cells = 0, sib_cap = 0, lanes = 0;
     InstDesc desc{};
 };
+
+// Propagation shapes picked by the autotuner, per kind of work (lattice,
+// sibling lattice, per pair) and problem shape; shared by every engine of the
+// process.
+struct ShapeKey {
+    int kind, dyn, n, k, nu, S;
+    bool operator<(const ShapeKey &o) const
+    {
+        return std::tie(kind, dyn, n, k, nu, S) < std::tie(o.kind, o.dyn, o.n, o.k, o.nu, o.S);
+    }
+};
+inline std::mutex &shape_mu()
+{
+    static std::mutex m;
+    return m;
+}
+inline std::map<ShapeKey, int> &shape_cache()
+{
+    static std::map<ShapeKey, int> c;
+    return c;
+}
 
 inline double model_flops_rhs(const Inst &I)
 {
@@ -477,7 +502,8 @@ inline void fill_desc(Inst &I)
     }
     D.fresh0 = I.n_live - I.n_fresh;
     D.sib_groups = sibling_groups(n, I.grid.k_samples);
-    const bool lat = lattice_tile(n, I.grid.k_samples, D.n0, D.tile);
+    if (I.sib_cap > 0) D.sib_groups = std::min(D.sib_groups, I.sib_cap);
+    const bool lat = lattice_tile(n, I.grid.k_samples, D.n0, D.tile, I.lat_cells);
     for (int d = 0; d < MAXN; d++) D.ntile[d] = !lat ? 0 : d < n ? (D.n0[d] + D.tile[d] - 1) / D.tile[d] : 1;
     const int k = I.grid.k_samples;
     for (int j = 0; j < MAXK; j++) {
@@ -613,6 +639,7 @@ struct Engine {
         if (o) opt = *o;
         else gis_default_options(&opt);
         if (opt.enclosure_store < 0 || opt.enclosure_store > 2) throw Error{GIS_EINVAL, "enclosure_store: 0, 1 or 2"};
+        if (opt.fixed_shapes != 0 && opt.fixed_shapes != 1) throw Error{GIS_EINVAL, "fixed_shapes: 0 or 1"};
         if (opt.lanes_per_pair != 0 && opt.lanes_per_pair != 1 && opt.lanes_per_pair != 2 && opt.lanes_per_pair != 4 &&
             opt.lanes_per_pair != 8 && opt.lanes_per_pair != 16)
             throw Error{GIS_EINVAL, "lanes_per_pair: 0 (auto), 1, 2, 4, 8 or 16"};
@@ -902,6 +929,7 @@ struct Engine {
     int lanes_for(const Inst &I)
     {
         if (opt.lanes_per_pair > 0) return opt.lanes_per_pair;
+        if (I.lanes > 0) return I.lanes;
         int g = 4;
         while (g > 1 && g > I.S) g >>= 1;
         return g;
@@ -930,6 +958,139 @@ struct Engine {
         if (NL >= ((int64_t)1 << 31) - 1 || P >= ((int64_t)1 << 31) - 1)
             throw Error{GIS_EUNSUPPORTED, "more than 2^31 cells or pairs in one level"};
         upload_desc();
+    }
+
+    // ---- propagation shapes and their autotuner -----------------------------
+    enum { PK_LATTICE = 0, PK_SIBLING = 1, PK_PAIR = 2 };
+    // which propagation kernel takes I's fresh cells (-1: FP64 plain): the
+    // first build of an FP32 problem with boundary samples shares lattice
+    // points across tiles of root cells; fresh children of split cells share
+    // their sibling lattice; the rest propagate per pair
+    int prop_kind(const Inst &I) const
+    {
+        if (I.precision != GIS_FP32_RECHECK) return -1;
+        if (I.desc.ntile[0] > 0 && I.level == 0 && I.n_fresh == I.n_live && I.n_live == I.n_nodes &&
+            opt.lanes_per_pair == 0)
+            return PK_LATTICE;
+        if (I.desc.sib_groups > 0 && I.n_fresh < I.n_nodes && I.n_fresh % (1 << I.dyn.n) == 0 &&
+            opt.lanes_per_pair == 0)
+            return PK_SIBLING;
+        return PK_PAIR;
+    }
+    static void set_shape(Inst &I, int kind, int v)
+    {
+        if (kind == PK_LATTICE) I.lat_cells = v;
+        else if (kind == PK_SIBLING) I.sib_cap = v;
+        else I.lanes = v;
+    }
+    std::vector<int> shape_candidates(const Inst &I, int kind) const
+    {
+        std::vector<int> c;
+        if (kind == PK_LATTICE) {
+            const int t = prop_block_threads();
+            c = {t, t / 2, t / 4};
+        } else if (kind == PK_SIBLING) {
+            const int g = sibling_groups(I.dyn.n, I.grid.k_samples);
+            for (int v : {g, g / 2, g / 4})
+                if (v >= 1 && (c.empty() || c.back() != v)) c.push_back(v);
+        } else if (opt.lanes_per_pair == 0) {
+            for (int v : {1, 2, 4, 8, 16})
+                if (v == 1 || v <= I.S) c.push_back(v);
+        }
+        return c;
+    }
+    // device time per unit of work (root cell x control for the lattice,
+    // parent x control for siblings, pair otherwise) of shape v, on a prefix
+    // of I's work of about eight blocks per SM; the launch is repeated (the
+    // first loads the kernel), and its results are rewritten by the real one
+    double time_shape(Inst &I, int kind, int v)
+    {
+        set_shape(I, kind, v);
+        upload_desc();
+        const InstDesc &D = I.desc;
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        RangeSpec r{I.tix, 0, 0};
+        int per_block = 1;
+        double units = 1;
+        if (kind == PK_LATTICE) {
+            int64_t tiles = 1;
+            for (int d = 0; d < I.dyn.n; d++) {
+                tiles *= D.ntile[d];
+                units *= D.tile[d];
+            }
+            r.count = std::min<int64_t>(tiles * I.nu, 8LL * sms);
+        } else if (kind == PK_SIBLING) {
+            const int64_t ng = I.n_fresh >> I.dyn.n;
+            r.count = std::min<int64_t>((ng + D.sib_groups - 1) / D.sib_groups * I.nu, 8LL * sms);
+            units = D.sib_groups;
+        } else {
+            per_block = prop_pairs_per_block(v);
+            r.first = I.pair_base + (I.n_live - I.n_fresh) * I.nu;
+            r.count = std::min<int64_t>(I.n_fresh * I.nu, 8LL * sms * per_block);
+        }
+        if (r.count <= 0) return 0;
+        const WorkList w = make_work({r}, per_block);
+        auto launch = [&]() {
+            if (kind == PK_LATTICE) CK(launch_prop32_lattice(I.dyn.dyn_id, I.dyn.n, d_desc, w, st));
+            else if (kind == PK_SIBLING) CK(launch_prop32_siblings(I.dyn.dyn_id, I.dyn.n, d_desc, w, st));
+            else CK(launch_prop32(I.dyn.dyn_id, I.dyn.n, v, d_desc, w, st));
+            cum.cum_tune_launches++;
+        };
+        launch();
+        cudaEvent_t a, b;
+        CK(cudaEventCreate(&a));
+        CK(cudaEventCreate(&b));
+        CK(cudaEventRecord(a, st));
+        launch();
+        CK(cudaEventRecord(b, st));
+        CK(cudaEventSynchronize(b));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, a, b));
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return (double)ms / ((double)r.count * units);
+    }
+    // every fresh FP32 problem takes its kind's shape from the cache, timing
+    // the candidates on the first problem of a kind not seen before
+    void tune_shapes(const std::vector<int> &ids)
+    {
+        bool changed = false;
+        for (int i : ids) {
+            Inst &I = *inst[i];
+            if (I.n_fresh == 0) continue;
+            const int kind = prop_kind(I);
+            if (kind < 0) continue;
+            const ShapeKey key{kind, I.dyn.dyn_id, I.dyn.n, I.grid.k_samples, I.nu, I.S};
+            int v = 0;
+            {
+                std::lock_guard<std::mutex> g(shape_mu());
+                auto it = shape_cache().find(key);
+                if (it != shape_cache().end()) v = it->second;
+            }
+            if (v == 0) {
+                const std::vector<int> c = shape_candidates(I, kind);
+                if (c.empty()) continue;
+                double best = 0;
+                for (int cand : c) {
+                    const double t = c.size() > 1 ? time_shape(I, kind, cand) : 0;
+                    if (v == 0 || t < best) {
+                        v = cand;
+                        best = t;
+                    }
+                }
+                std::lock_guard<std::mutex> g(shape_mu());
+                shape_cache()[key] = v;
+                changed = true;
+            }
+            int &cur = kind == PK_LATTICE ? I.lat_cells : kind == PK_SIBLING ? I.sib_cap : I.lanes;
+            if (cur != v) {
+                set_shape(I, kind, v);
+                changed = true;
+            }
+        }
+        if (changed) upload_desc();
     }
 
     void build_graph(const std::vector<int> &ids)
@@ -968,6 +1129,8 @@ struct Engine {
         CK(launch_cgather(d_desc, ws, cps, cinst, s2n, oslot, st));
         timer.end();
 
+        if (!opt.fixed_shapes) tune_shapes(ids);
+
         // propagation of new cells, grouped by (dynamics, n, precision, lanes)
         timer.begin(PH_PROP);
         last_new_pairs = 0;
@@ -979,8 +1142,8 @@ struct Engine {
             // first build of an FP32 problem with boundary samples: shared
             // lattice points (lanes = 0 marks the lattice kernel; items are
             // tiles x controls)
-            if (I.precision == GIS_FP32_RECHECK && I.desc.ntile[0] > 0 && I.level == 0 &&
-                I.n_fresh == I.n_live && I.n_live == I.n_nodes && opt.lanes_per_pair == 0) {
+            const int kind = prop_kind(I);
+            if (kind == PK_LATTICE) {
                 int64_t tiles = 1;
                 double points = 1;             // lattice points propagated, summed over tiles
                 const int k1 = I.grid.k_samples - 1;
@@ -992,8 +1155,7 @@ struct Engine {
                 }
                 groups[{I.dyn.dyn_id, I.dyn.n, I.precision, 0}].push_back({I.tix, 0, tiles * I.nu});
                 cum.prop_flops += sample_ball_flops(I) * points * I.nu;
-            } else if (I.precision == GIS_FP32_RECHECK && I.desc.sib_groups > 0 && I.n_fresh < I.n_nodes &&
-                       I.n_fresh % (1 << I.dyn.n) == 0 && opt.lanes_per_pair == 0) {
+            } else if (kind == PK_SIBLING) {
                 // fresh children of split cells: shared points among siblings
                 // (lanes = -1 marks the sibling kernel; items are runs of
                 // parents x controls)
@@ -1459,6 +1621,16 @@ struct Engine {
         s->n_recheck = last_recheck;
         s->prune_rounds = last_rounds;
         s->lanes_per_pair = inst.empty() ? 0 : const_cast<Engine *>(this)->lanes_for(*inst[0]);
+        if (!inst.empty()) {
+            const Inst &I = *inst[0];
+            int cells = 0;
+            if (I.desc.ntile[0] > 0) {
+                cells = 1;
+                for (int d = 0; d < I.dyn.n; d++) cells *= I.desc.tile[d];
+            }
+            s->lattice_tile_cells = cells;
+            s->sibling_parents = I.desc.sib_groups;
+        }
     }
 };
 

@@ -34,12 +34,13 @@ struct RecheckQueue {            // per dynamics: (global pair, inst | mask << 1
 cudaError_t launch_prop32(int dyn, int n, int lanes, const InstDesc *D, const WorkList &w, cudaStream_t st);
 // first build: one block per (tile of root cells, control), items = tiles x controls
 cudaError_t launch_prop32_lattice(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st);
-bool lattice_tile(int n, int k, const int32_t *n0, int32_t *tile);
+bool lattice_tile(int n, int k, const int32_t *n0, int32_t *tile, int max_cells = 0);
 // fresh children: one block per (run of sib_groups parents, control)
 cudaError_t launch_prop32_siblings(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st);
 int sibling_groups(int n, int k);
 cudaError_t launch_prop64(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st);
 int prop_pairs_per_block(int lanes);
+int prop_block_threads();
 // binning: decisions at the finest level, band check, recheck queue
 cudaError_t launch_bin(int n, const InstDesc *D, const WorkList &w, int32_t *rng, uint8_t *pflag,
                        int2 *queue_items, int32_t *queue_counts, int64_t queue_cap, cudaStream_t st);

@@ -790,6 +790,7 @@ __global__ void __launch_bounds__(256) k_rc_final(const InstDesc *__restrict__ D
 // dispatch
 // ---------------------------------------------------------------------------
 int prop_pairs_per_block(int lanes) { return PROP_THREADS / lanes; }
+int prop_block_threads() { return PROP_THREADS; }
 
 template <class DY>
 static cudaError_t prop32_g(int lanes, const InstDesc *D, const WorkList &w, cudaStream_t st)
@@ -1000,10 +1001,11 @@ cudaError_t launch_prop32_lattice(int dyn, int n, const InstDesc *D, const WorkL
 }
 
 // Tile of root cells for the lattice kernel: grow the extents in turn while
-// the tile's lattice points fit a block and its cells fit one pass; false if
-// one cell's k^n points do not fit.
-bool lattice_tile(int n, int k, const int32_t *n0, int32_t *tile)
+// the tile's lattice points fit a block and its cells fit one pass (and at most
+// max_cells, if > 0); false if one cell's k^n points do not fit.
+bool lattice_tile(int n, int k, const int32_t *n0, int32_t *tile, int max_cells)
 {
+    const int64_t cmax = max_cells > 0 ? std::min(max_cells, PROP_THREADS) : PROP_THREADS;
     const int pmax = LAT_POINTS / n;
     int64_t one = 1;
     for (int d = 0; d < n; d++) {
@@ -1021,7 +1023,7 @@ bool lattice_tile(int n, int k, const int32_t *n0, int32_t *tile)
                 pts *= (int64_t)te * (k - 1) + 1;
                 cells *= te;
             }
-            if (pts > pmax || cells > PROP_THREADS) continue;
+            if (pts > pmax || cells > cmax) continue;
             tile[d] = std::min(2 * tile[d], (int)n0[d]);
             grew = true;
         }

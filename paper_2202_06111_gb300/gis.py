@@ -52,7 +52,7 @@ class gis_controls(C.Structure):
 class gis_options(C.Structure):
     _fields_ = [("rule", C.c_int32), ("precision", C.c_int32), ("band", C.c_double),
                 ("lanes_per_pair", C.c_int32), ("timing", C.c_int32), ("max_device_bytes", C.c_int64),
-                ("round_limit", C.c_int64), ("enclosure_store", C.c_int32), ("reserved", C.c_int32)]
+                ("round_limit", C.c_int64), ("enclosure_store", C.c_int32), ("fixed_shapes", C.c_int32)]
 
 
 class gis_cell(C.Structure):
@@ -71,7 +71,8 @@ _STAT_FIELDS = [("finest_level", C.c_int32), ("level", C.c_int32), ("n_nodes", C
                 ("graph_bytes", C.c_double), ("prune_bytes", C.c_double), ("count_bytes", C.c_double),
                 ("fill_bytes", C.c_double), ("transpose_bytes", C.c_double), ("cum_launches", C.c_int64),
                 ("cum_recheck_samples", C.c_int64), ("n_cell_edges", C.c_int64), ("cum_cell_edges", C.c_int64),
-                ("cum_recheck_fp64", C.c_int64)]
+                ("cum_recheck_fp64", C.c_int64), ("lattice_tile_cells", C.c_int32),
+                ("sibling_parents", C.c_int32), ("cum_tune_launches", C.c_int64)]
 
 
 class gis_stats(C.Structure):

@@ -114,6 +114,23 @@ def test_outer_prune_count_words(gis, nu):
     run_both(gis, prob, 2)
 
 
+def test_autotuned_shapes_same_result(gis):
+    """The autotuner times candidate propagation shapes (lattice tile, sibling
+    lattice, lanes per pair) on the first work of a kind; the graphs and kept
+    sets must not depend on the shapes it picks. The shapes are cached per
+    process; thirteen controls (the random batch and serving problems draw 5
+    to 11) make a key no other test uses, so the candidates are timed here."""
+    prob = dict(W.problem(W.cstr_dl(0.072), [0, 0], [1, 8], [37, 41], 3, W.controls_grid(-2, 2, 13), 0.05, 4,
+                          rule="inner", precision="fp32"))
+    tuned = run_both(gis, prob, 2)
+    st = tuned[-1][1]
+    assert st["cum_tune_launches"] > 0
+    assert st["lattice_tile_cells"] > 0 and st["sibling_parents"] > 0
+    fixed = run_both(gis, prob, 2, fixed_shapes=1)
+    assert [k for k, _ in tuned] == [k for k, _ in fixed]
+    assert fixed[-1][1]["cum_tune_launches"] == 0
+
+
 def test_everything_leaves(gis):
     """x+ = 2x + 3: every image leaves X, nothing is kept, no split."""
     prob = W.problem(W.linmap([[2.0]], [[1.0]]), [-1.0], [1.0], 16, 2, [[3.0]], 1.0, 0, precision="fp32")
