@@ -62,6 +62,7 @@ cudaError_t launch_cgather(const InstDesc *D, const WorkList &w, int32_t *cps, i
 constexpr int CE_WARPS = 8;      // cells (warps) per block
 constexpr int CE_TAB = 512;      // per-warp tables of control sets per dimension (entries)
 constexpr int CE_GRAB = 4;       // fewest chunks a warp takes at a time
+constexpr int CE_EB = CE_EB_HOST;   // staged edges a warp buffers in shared memory
 
 __device__ __forceinline__ int warp_min(int v)
 {
@@ -237,13 +238,16 @@ __host__ __device__ constexpr int walk_words(int n) { return 2 + 3 * n; }
 // from chunk to chunk within a run, from chk_off = the exclusive scan of
 // chk_cnt at a run's start; no scan is needed when every cell has one chunk),
 // reverse edges at rcur[target]++ (rsrc, rmask). *stop (set when the chunk
-// arrays are too small) makes both passes return at once.
+// arrays are too small) makes both passes return at once. With sa.stg the
+// count pass also stages its edges (StageArgs), in a buffer of CE_EB per warp
+// after the stacks in dynamic shared memory.
 template <int N, bool FILL>
 __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__restrict__ D, int64_t c0, int64_t c1,
                                                             const int64_t *__restrict__ cbase,
                                                             const int32_t *__restrict__ chk_cell,
                                                             int32_t *__restrict__ chk_cnt,
                                                             const int64_t *__restrict__ chk_off,
+                                                            const uint8_t *__restrict__ only,
                                                             unsigned long long *__restrict__ grab,
                                                             const int32_t *__restrict__ stop, int S,
                                                             const int32_t *__restrict__ cinst,
@@ -255,12 +259,14 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
                                                             unsigned long long *__restrict__ rcur,
                                                             int32_t *__restrict__ rsrc, uint32_t *__restrict__ rmask,
                                                             unsigned long long *__restrict__ pair_edges,
-                                                            int32_t *__restrict__ err)
+                                                            int32_t *__restrict__ err, int64_t ecap,
+                                                            const StageArgs sa)
 {
     constexpr uint32_t FULL = 0xffffffffu;
     __shared__ CtlBox<N> s_box[CE_WARPS][32];
     __shared__ uint32_t s_tab[CE_WARPS][CE_TAB];
     extern __shared__ uint32_t s_walk[];
+    uint2 *const eb = (uint2 *)(s_walk + (size_t)CE_WARPS * S * walk_words(N)) + (threadIdx.x >> 5) * CE_EB;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     if (*(volatile const int32_t *)stop) return;
@@ -298,6 +304,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
     const int64_t gend = min(kb + (int64_t)(g0 + gn), ke);
     int64_t wpos = 0;                              // FILL: where the chunk's edges go
     for (int64_t k = kb + (int64_t)g0; k < gend; k++) {
+        if (FILL && only && !only[k]) continue;    // placed from the staged edges
         const int64_t s = chk_cell[k];
         if (s != cur) {
         cur = s;
@@ -380,11 +387,39 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
         const int64_t r1 = min(nroots, (k - cb + 1) * CE_CHUNK);
         const bool small = r1 < ((int64_t)1 << 31);
         int64_t nbase = (k - cb) * CE_CHUNK;       // the chunk's next root (lane 0)
-        if (FILL && (k == cb || k == kb + (int64_t)g0))   // a run's first chunk
+        if (FILL && (k == cb || k == kb + (int64_t)g0 || only))   // a run's first chunk
             wpos = coff[s] + (k == cb ? 0 : chk_off[k] - chk_off[cb]);
         int sp = 0;                                // stack entries
         int32_t nent = 0, myc = 0;
         uint32_t tch = 0;
+        int nbuf = 0, soff = 0;                    // staged edges: buffered, flushed of this chunk
+        auto stage_flush = [&]() {
+            __syncwarp();
+            unsigned long long base = 0;
+            unsigned int sidx = 0;
+            if (lane == 0) {
+                base = atomicAdd(sa.top, (unsigned long long)nbuf);
+                sidx = atomicAdd(sa.seg_top, 1u);
+            }
+            base = __shfl_sync(FULL, base, 0);
+            sidx = __shfl_sync(FULL, sidx, 0);
+            if (base + (unsigned long long)nbuf <= (unsigned long long)sa.cap && (int64_t)sidx < sa.seg_cap) {
+                for (int j = lane; j < nbuf; j += 32) {
+                    const uint2 v = eb[j];
+                    sa.stg[base + j] = (unsigned long long)v.y << 32 | v.x;
+                }
+                if (lane == 0) sa.seg[sidx] = SegRec{(long long)base, (int32_t)k, soff, nbuf, 0};
+            } else if (lane == 0) {
+                // out of room: the chunk is walked again by the fill (its record,
+                // if it has a slot, is written empty)
+                if ((int64_t)sidx < sa.seg_cap) sa.seg[sidx] = SegRec{0, (int32_t)k, soff, 0, 0};
+                *sa.over = 1;
+                sa.lost[k] = 1;
+            }
+            soff += nbuf;
+            nbuf = 0;
+            __syncwarp();
+        };
         for (;;) {
             int node = -1, L = 0, idx[N];
             uint32_t m = 0;
@@ -543,14 +578,23 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
                 const int t = tslot;
                 if (FILL) {
                     const int64_t pos = wpos + __popc(b & lt);
-                    cent[pos] = t;
-                    cmask[pos] = m;
                     const unsigned long long r = atomicAdd(&rcur[t], 1ull);
-                    rsrc[r] = (int32_t)s;
-                    rmask[r] = m;
+                    if (pos < ecap && r < (unsigned long long)ecap) {
+                        cent[pos] = t;
+                        cmask[pos] = m;
+                        rsrc[r] = (int32_t)s;
+                        rmask[r] = m;
+                    } else {
+                        atomicExch(err, GIS_EBOUNDS);
+                    }
                 } else {
                     atomicAdd(&rcnt[t], 1);
                 }
+            }
+            if (!FILL && sa.stg && b) {
+                if (nbuf + __popc(b) > CE_EB) stage_flush();
+                if (emit) eb[nbuf + __popc(b & lt)] = make_uint2((uint32_t)tslot, m);
+                nbuf += __popc(b);
             }
             if (!FILL && b) {
                 // targets per control: one ballot per control present in the step
@@ -565,6 +609,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
             nent += __popc(b);
         }
         if (!FILL) {
+            if (sa.stg && nbuf > 0) stage_flush();
             const uint32_t touched = __reduce_or_sync(FULL, tch);
             const bool whole = ce - cb == 1;       // the cell's only chunk
             if (lane < nu) {
@@ -606,7 +651,8 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cinc(const InstDesc *__restri
                                                        unsigned long long *__restrict__ rcur,
                                                        int32_t *__restrict__ rsrc, uint32_t *__restrict__ rmask,
                                                        unsigned long long *__restrict__ pair_edges,
-                                                       int32_t *__restrict__ err, const CellPrev prev)
+                                                       int32_t *__restrict__ err, int64_t ecap,
+                                                       const CellPrev prev)
 {
     constexpr uint32_t FULL = 0xffffffffu;
     constexpr int NC = 1 << N;
@@ -699,11 +745,15 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cinc(const InstDesc *__restri
             const int t = tn[j] < 0 ? -1 - tn[j] : I.slot[tn[j]];
             const uint32_t mm = tm[j];
             if (FILL) {
-                cent[base + j] = t;
-                cmask[base + j] = mm;
                 const unsigned long long r = atomicAdd(&rcur[t], 1ull);
-                rsrc[r] = (int32_t)s;
-                rmask[r] = mm;
+                if (base + j < ecap && r < (unsigned long long)ecap) {
+                    cent[base + j] = t;
+                    cmask[base + j] = mm;
+                    rsrc[r] = (int32_t)s;
+                    rmask[r] = mm;
+                } else {
+                    atomicExch(err, GIS_EBOUNDS);
+                }
             } else {
                 atomicAdd(&rcnt[t], 1);
                 for (uint32_t b = mm; b; b &= b - 1) atomicAdd(&s_cnt[warp][__ffs(b) - 1], 1);
@@ -739,11 +789,11 @@ cudaError_t launch_cinc(bool fill, int n, const InstDesc *D, const WorkList &w, 
         if (fill)                                                                                            \
             k_cinc<NN, true><<<gr, b, 0, st>>>(D, w.d_ranges, w.n_ranges, g.rng, g.pflag, g.pcnt, g.ccnt,    \
                                                g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rsrc, g.rmask,     \
-                                               g.pair_edges, g.err, prev);                                   \
+                                               g.pair_edges, g.err, g.ecap, prev);                           \
         else                                                                                                 \
             k_cinc<NN, false><<<gr, b, 0, st>>>(D, w.d_ranges, w.n_ranges, g.rng, g.pflag, g.pcnt, g.ccnt,   \
                                                 g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rsrc, g.rmask,    \
-                                                g.pair_edges, g.err, prev);                                  \
+                                                g.pair_edges, g.err, g.ecap, prev);                          \
         note_launch();                                                                                       \
         break;
     switch (n) {
@@ -766,7 +816,8 @@ static int cedges_grid(int dev, int depth, size_t smem)
         // the deepest subdivision a problem of dimension N may reach (the
         // bound of check_depth), so that no later launch needs more
         const int dmax = std::min(MAXL, (STACK - 1) / ((1 << N) - 1));
-        const size_t most = (size_t)CE_WARPS * 32 * std::max(dmax, 1) * walk_words(N) * sizeof(uint32_t);
+        const size_t most = (size_t)CE_WARPS * 32 * std::max(dmax, 1) * walk_words(N) * sizeof(uint32_t) +
+                            (FILL ? 0 : (size_t)CE_WARPS * CE_EB * sizeof(uint2));
         cudaFuncSetAttribute(k_cedges<N, FILL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(most, smem));
         attr[dev] = true;
     }
@@ -782,7 +833,7 @@ static int cedges_grid(int dev, int depth, size_t smem)
 
 cudaError_t launch_cedges(bool fill, int n, int depth, const InstDesc *D, int64_t c0, int64_t c1,
                           const int64_t *cbase, const ChunkWork &cw, unsigned long long *grab, const int32_t *cinst,
-                          const CellGraph &g, cudaStream_t st)
+                          const CellGraph &g, const StageArgs &sa, cudaStream_t st)
 {
     if (c1 <= c0) return cudaSuccess;
     if (depth < 0 || depth > MAXL) return cudaErrorInvalidValue;
@@ -792,15 +843,18 @@ cudaError_t launch_cedges(bool fill, int n, int depth, const InstDesc *D, int64_
     const int S = 32 * std::max(depth, 1);
 #define CE_CASE(NN)                                                                                        \
     case NN: {                                                                                             \
-        const size_t smem = (size_t)CE_WARPS * S * walk_words(NN) * sizeof(uint32_t);                     \
+        const size_t smem = (size_t)CE_WARPS * S * walk_words(NN) * sizeof(uint32_t) +                     \
+                            (fill ? 0 : (size_t)CE_WARPS * CE_EB * sizeof(uint2));                         \
         if (fill)                                                                                          \
             k_cedges<NN, true><<<cedges_grid<NN, true>(dev, depth, smem), b, smem, st>>>(                   \
-                D, c0, c1, cbase, cw.cell, cw.cnt, cw.off, grab, cw.stop, S, cinst, g.rng, g.pflag, g.pcnt, \
-                g.ccnt, g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rsrc, g.rmask, g.pair_edges, g.err);     \
+                D, c0, c1, cbase, cw.cell, cw.cnt, cw.off, cw.only, grab, cw.stop, S, cinst, g.rng, g.pflag, g.pcnt, \
+                g.ccnt, g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rsrc, g.rmask, g.pair_edges, g.err,      \
+                g.ecap, StageArgs{});                                                                              \
         else                                                                                               \
             k_cedges<NN, false><<<cedges_grid<NN, false>(dev, depth, smem), b, smem, st>>>(                 \
-                D, c0, c1, cbase, cw.cell, cw.cnt, cw.off, grab, cw.stop, S, cinst, g.rng, g.pflag, g.pcnt, \
-                g.ccnt, g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rsrc, g.rmask, g.pair_edges, g.err);     \
+                D, c0, c1, cbase, cw.cell, cw.cnt, cw.off, cw.only, grab, cw.stop, S, cinst, g.rng, g.pflag, g.pcnt, \
+                g.ccnt, g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rsrc, g.rmask, g.pair_edges, g.err,      \
+                g.ecap, sa);                                                                               \
         note_launch();                                                                                     \
         break;                                                                                             \
     }
@@ -809,6 +863,65 @@ cudaError_t launch_cedges(bool fill, int n, int depth, const InstDesc *D, int64_
     default: return cudaErrorInvalidValue;
     }
 #undef CE_CASE
+    return cudaGetLastError();
+}
+
+// The place pass: a warp per staged segment copies its edges to their CSR
+// position (the cell's offset, plus the edges of the cell's earlier chunks,
+// plus the segment's offset in its chunk) and scatters the reverse edges at
+// rcur[target]++.
+__global__ void __launch_bounds__(256) k_place(const int64_t *__restrict__ cbase,
+                                               const int32_t *__restrict__ chk_cell,
+                                               const int64_t *__restrict__ chk_off,
+                                               const unsigned long long *__restrict__ stg,
+                                               int64_t nchunks, const SegRec *__restrict__ seg, int64_t nseg,
+                                               const uint8_t *__restrict__ lost, int64_t ecap,
+                                               int32_t *__restrict__ err,
+                                               const int64_t *__restrict__ coff, int32_t *__restrict__ cent,
+                                               uint32_t *__restrict__ cmask, unsigned long long *__restrict__ rcur,
+                                               int32_t *__restrict__ rsrc, uint32_t *__restrict__ rmask)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (w >= nseg) return;
+    const SegRec r = seg[w];
+    if (r.chunk < 0 || r.chunk >= nchunks || r.len < 0 || r.len > CE_EB) {
+        if (lane == 0) atomicExch(err, GIS_EBOUNDS);
+        return;
+    }
+    if (lost && lost[r.chunk]) return;            // the fill walks this chunk
+    const int32_t s = chk_cell[r.chunk];
+    int64_t dst = coff[s] + r.soff;
+    if (chk_off) dst += chk_off[r.chunk] - chk_off[cbase[s]];
+    if (dst < coff[s] || dst + r.len > coff[s + 1]) {
+        if (lane == 0) atomicExch(err, GIS_EBOUNDS);
+        return;
+    }
+    for (int j = lane; j < r.len; j += 32) {
+        const unsigned long long e = __ldcs(&stg[r.pos + j]);
+        const int32_t t = (int32_t)(uint32_t)e;
+        const uint32_t m = (uint32_t)(e >> 32);
+        cent[dst + j] = t;
+        cmask[dst + j] = m;
+        const unsigned long long q = atomicAdd(&rcur[t], 1ull);
+        if (q < (unsigned long long)ecap) {
+            rsrc[q] = s;
+            rmask[q] = m;
+        } else {
+            atomicExch(err, GIS_EBOUNDS);
+        }
+    }
+}
+
+cudaError_t launch_place(const int64_t *cbase, const int32_t *chk_cell, const int64_t *chk_off, int64_t nchunks,
+                         const StageArgs &sa, bool any_lost, int64_t nseg, const CellGraph &g, cudaStream_t st)
+{
+    nseg = std::min(nseg, sa.seg_cap);            // the counter also counts records that found no slot
+    if (nseg <= 0) return cudaSuccess;
+    k_place<<<(unsigned)((nseg + 7) / 8), 256, 0, st>>>(cbase, chk_cell, chk_off, sa.stg, nchunks, sa.seg, nseg,
+                                                        any_lost ? sa.lost : nullptr, g.ecap, g.err, g.coff, g.cent,
+                                                        g.cmask, g.rcur, g.rsrc, g.rmask);
+    note_launch();
     return cudaGetLastError();
 }
 

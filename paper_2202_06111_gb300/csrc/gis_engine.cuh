@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -593,7 +594,11 @@ struct Engine {
     int64_t *cbase = nullptr; size_t c_cbase = 0;
     int32_t *chk_cell = nullptr, *chk_cnt = nullptr; size_t c_chk_cell = 0, c_chk_cnt = 0;
     int64_t *chk_off = nullptr; size_t c_chk_off = 0;
+    uint8_t *chk_lost = nullptr; size_t c_chk_lost = 0;
     int64_t chunk_hint = 0;     // chunks of the previous build
+    unsigned long long *stg = nullptr; size_t c_stg = 0;   // staged edges of the count pass
+    SegRec *seg = nullptr; size_t c_seg = 0;
+    double stage_per_cell = 0;  // walked edges per walked cell of the previous staged build
     int64_t chunk_cells = 0;    // and its cells
     int32_t *rng = nullptr; size_t c_rng = 0;
     uint8_t *pflag = nullptr; size_t c_pflag = 0;
@@ -1304,19 +1309,67 @@ struct Engine {
         int64_t cap = 2 * NL + 4096;
         if (chunk_hint > 0 && chunk_cells > 0)
             cap = std::max<int64_t>(cap, (int64_t)((double)chunk_hint / (double)chunk_cells * 1.25 * (double)NL) + 4096);
+        // staging of the walk's edges (one walk for count and fill), sized from
+        // the previous build's edges per walked cell (64 before any), unless the
+        // device or the memory budget is short; else the fill walks again.
+        // GIS_STAGE_PER_CELL (tests) fixes the edges per walked cell, with no
+        // slack (0: no staging)
+        int64_t walked = NL;
+        for (int i : ids) walked -= inst[i]->n_carry;
+        StageArgs sa{};
+        const char *fixed_per = std::getenv("GIS_STAGE_PER_CELL");
+        const double fper = fixed_per ? std::atof(fixed_per) : -1.0;
+        if (walked > 0 && fper != 0.0) {
+            const double per = fper > 0 ? fper : stage_per_cell > 0 ? 1.25 * stage_per_cell : 64.0;
+            const int64_t scap = (int64_t)(per * (double)walked) + (fper > 0 ? 1 : 65536);
+            const int64_t gcap = cap + scap / (CE_EB_HOST - 32) + 4096;
+            auto grown = [](size_t have, int64_t need, size_t el) {
+                return (size_t)need <= have ? 0.0 : (double)std::max<size_t>((size_t)need, have + have / 2) * el;
+            };
+            const double extra = grown(c_stg, scap, sizeof(unsigned long long)) + grown(c_seg, gcap, sizeof(SegRec));
+            // a large growth must also leave room for the edge arrays that follow
+            // (forward and reverse, 16 bytes an edge); small ones skip the query
+            bool room = extra <= 256.0 * (1 << 20);
+            if (!room) {
+                size_t fr = 0, tot = 0;
+                cudaMemGetInfo(&fr, &tot);
+                room = extra + 16.0 * (double)scap <= 0.8 * (double)fr;
+            }
+            if (room && (mem.limit == 0 || (double)mem.used + extra <= 0.8 * (double)mem.limit)) {
+                mem.ensure(stg, c_stg, (size_t)scap);
+                mem.ensure(seg, c_seg, (size_t)gcap);
+                sa.stg = stg;
+                sa.cap = (int64_t)c_stg;
+                sa.top = (unsigned long long *)(ctl + 40);
+                sa.seg = seg;
+                sa.seg_cap = (int64_t)c_seg;
+                sa.seg_top = (unsigned int *)(ctl + 42);
+                sa.over = ctl + 43;
+            }
+        }
         for (int attempt = 0;; attempt++) {
             mem.ensure(chk_cell, c_chk_cell, (size_t)cap);
             mem.ensure(chk_cnt, c_chk_cnt, (size_t)cap);
+            if (sa.stg) {
+                // a segment per chunk and per full buffer
+                mem.ensure(seg, c_seg, (size_t)(cap + sa.cap / (CE_EB_HOST - 32) + 4096));
+                sa.seg = seg;
+                sa.seg_cap = (int64_t)c_seg;
+                mem.ensure(chk_lost, c_chk_lost, (size_t)cap);
+                sa.lost = chk_lost;
+                CK(cudaMemsetAsync(chk_lost, 0, (size_t)cap, st));
+            }
             const ChunkWork cw{chk_cell, chk_cnt, nullptr, ctl + 18, cap};
             mem.ensure(scratch, c_scratch, scan_scratch_bytes(std::max<int64_t>(P, NL) + 1));
             timer.begin(PH_COUNT);
-            // pair-edge total (12, 13), chunk-overflow flag (18), chunk counters (24 .. 39)
-            CK(cudaMemsetAsync(ctl + 12, 0, 28 * sizeof(int32_t), st));
+            // pair-edge total (12, 13), chunk-overflow flag (18), chunk counters (24 .. 39),
+            // staged edges (40, 41), segments (42), staging overflow (43)
+            CK(cudaMemsetAsync(ctl + 12, 0, 32 * sizeof(int32_t), st));
             if (attempt > 0) CK(cudaMemsetAsync(pcnt, 0, Ps * sizeof(int32_t), st));   // k_cinc ran
             CK(launch_cexpand(cbase, NL, cw, ccnt, rcnt, st));
             for (int n = 1; n <= MAXN; n++)
                 CK(launch_cedges(false, n, seg_depth[n], d_desc, seg_base[n], seg_base[n + 1], cbase, cw,
-                                 grab + (n - 1), cinst, g, st));
+                                 grab + (n - 1), cinst, g, sa, st));
             for (int n = 1; n <= MAXN; n++) {
                 const auto r = carried(n);
                 if (!r.empty()) CK(launch_cinc(false, n, d_desc, make_work(r, cedges_cells_per_block()), g, prev, st));
@@ -1331,6 +1384,7 @@ struct Engine {
             CK(cudaMemcpyAsync(hp + 8, ctl + 6, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
             CK(cudaMemcpyAsync(hp + 40, cbase + NL, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
             CK(cudaMemcpyAsync(hp + 48, ctl + 18, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(hp + 56, ctl + 40, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
             sync();
             std::memcpy(&hEc, hp, sizeof(hEc));
             std::memcpy(hq, hp + 8, sizeof(hq));
@@ -1341,6 +1395,17 @@ struct Engine {
         }
         chunk_hint = K;
         chunk_cells = NL;
+        unsigned long long staged = 0;
+        uint32_t nseg = 0;
+        int32_t sover = 0;
+        {
+            const unsigned char *hp = pin;
+            std::memcpy(&staged, hp + 56, sizeof(staged));
+            std::memcpy(&nseg, hp + 64, sizeof(nseg));
+            std::memcpy(&sover, hp + 68, sizeof(sover));
+        }
+        if (sa.stg && walked > 0) stage_per_cell = (double)staged / (double)walked;
+        const bool placed = sa.stg != nullptr;   // chunks that lost a flush are walked again
         last_recheck = hq[0];
         if (last_recheck > 0) {
             cum.cum_recheck_samples += hq[4];
@@ -1359,9 +1424,8 @@ struct Engine {
         g.cmask = cmask;
         g.rsrc = rsrc;
         g.rmask = rmask;
+        g.ecap = Ecell;
         // a cell of several chunks writes each chunk after the earlier ones
-        int64_t walked = NL;
-        for (int i : ids) walked -= inst[i]->n_carry;
         int64_t *koff = nullptr;
         if (K > walked) {
             mem.ensure(chk_off, c_chk_off, (size_t)K + 1);
@@ -1373,11 +1437,13 @@ struct Engine {
         }
         timer.begin(PH_FILL);
         CK(cudaMemcpyAsync(rcur, roff, NLs * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
-        {
-            const ChunkWork cw{chk_cell, chk_cnt, koff, ctl + 18, cap};
+        if (placed) CK(launch_place(cbase, chk_cell, koff, K, sa, sover != 0, (int64_t)nseg, g, st));
+        if (!placed || sover) {
+            ChunkWork cw{chk_cell, chk_cnt, koff, ctl + 18, cap};
+            cw.only = placed ? chk_lost : nullptr;
             for (int n = 1; n <= MAXN; n++)
                 CK(launch_cedges(true, n, seg_depth[n], d_desc, seg_base[n], seg_base[n + 1], cbase, cw,
-                                 grab + 4 + (n - 1), cinst, g, st));
+                                 grab + 4 + (n - 1), cinst, g, StageArgs{}, st));
         }
         for (int n = 1; n <= MAXN; n++) {
             const auto r = carried(n);
@@ -1395,18 +1461,21 @@ struct Engine {
         cum.cum_recheck += last_recheck;
         // algorithmic bytes. count: per pair the decisions (8n), the flag (read and
         // write) and the target count; per cell the edge count; per cell edge the
-        // in-degree update (8). fill: per pair decisions and flag, per cell the
-        // offset; per cell edge the edge (8), the reverse cursor update (16) and
-        // the reverse edge (8).
+        // in-degree update (8); per staged edge its write (8). fill: per cell
+        // edge the edge (8), the reverse cursor update (16) and the reverse edge
+        // (8); a staged edge is read back (8), else the walk reads per pair the
+        // decisions and flag and per cell the offset again.
         double cb = 0, fb = 0;
         for (int i : ids) {
             const Inst &I = *inst[i];
             const double pairs = (double)I.n_live * I.nu;
             cb += pairs * (8.0 * I.dyn.n + 1 + 4 + 1) + 4.0 * (double)I.n_live;
-            fb += pairs * (8.0 * I.dyn.n + 1) + 8.0 * (double)I.n_live;
+            if (!placed) fb += pairs * (8.0 * I.dyn.n + 1) + 8.0 * (double)I.n_live;
         }
         cb += 8.0 * (double)Ecell;
         fb += 32.0 * (double)Ecell;
+        if (sa.stg) cb += 8.0 * (double)staged;
+        if (placed) fb += 8.0 * (double)staged;
         cum.count_bytes += cb;
         cum.fill_bytes += fb;
         cum.graph_bytes += cb + fb;
@@ -1487,6 +1556,7 @@ struct Engine {
         std::memcpy(kept.data(), pin + 256, step.size() * sizeof(int64_t));
         prune_pending = false;
         if (hc[4] != 0) throw Error{(gis_status)hc[4], "prune: round or wait limit reached"};
+        if (hc[7] != 0) throw Error{GIS_EBOUNDS, "edge fill out of bounds"};
         last_rounds = hc[5];
         unsigned long long scanned = 0;
         std::memcpy(&scanned, hc + 8, sizeof(scanned));

@@ -115,6 +115,8 @@ struct CellGraph {
     uint32_t *rmask;             // reverse edge control mask
     unsigned long long *pair_edges;  // total (cell, control) -> cell edges
     int32_t *err;
+    int64_t ecap = 0;            // fill: edges allocated (cent, cmask, rsrc, rmask); a write
+                                 // beyond sets *err = GIS_EBOUNDS and is skipped
 };
 cudaError_t launch_cgather(const InstDesc *D, const WorkList &wslots, int32_t *cps, int32_t *cinst,
                            int32_t *s2n, int32_t *oslot, cudaStream_t st);
@@ -144,7 +146,32 @@ struct ChunkWork {
     int64_t *off;
     int32_t *stop;
     int64_t cap;
+    uint8_t *only = nullptr;     // fill: walk only the chunks marked here (null: all)
 };
+// Edges staged by the count pass, so that one walk serves both passes: a
+// warp collects its chunk's edges in shared memory and flushes them to stg
+// (target | mask << 32) as a segment (chunk, offset in the chunk, position,
+// length); the place pass then copies every segment to its CSR position and
+// scatters the reverse edges. *top counts every edge (also past cap); when
+// stg or seg runs out, *over is set and the chunk is marked in lost[] (its
+// segments are skipped and the fill walks it again).
+constexpr int CE_EB_HOST = 256;  // edges a warp buffers before a flush (CE_EB)
+struct SegRec {
+    long long pos;
+    int32_t chunk, soff, len, pad;
+};
+struct StageArgs {
+    unsigned long long *stg = nullptr;   // null: no staging
+    int64_t cap = 0;
+    unsigned long long *top = nullptr;
+    SegRec *seg = nullptr;
+    int64_t seg_cap = 0;
+    unsigned int *seg_top = nullptr;
+    int32_t *over = nullptr;
+    uint8_t *lost = nullptr;     // per chunk, zeroed
+};
+cudaError_t launch_place(const int64_t *cbase, const int32_t *chk_cell, const int64_t *chk_off, int64_t nchunks,
+                         const StageArgs &sa, bool any_lost, int64_t nseg, const CellGraph &g, cudaStream_t st);
 // the cell of each chunk; zeroes the per-cell counts ccnt and rcnt
 cudaError_t launch_cexpand(const int64_t *cbase, int64_t NL, const ChunkWork &cw, int32_t *ccnt, int32_t *rcnt,
                            cudaStream_t st);
@@ -153,7 +180,7 @@ cudaError_t launch_cexpand(const int64_t *cbase, int64_t NL, const ChunkWork &cw
 // counts; grab: the chunk counter of this launch (zeroed)
 cudaError_t launch_cedges(bool fill, int n, int depth, const InstDesc *D, int64_t c0, int64_t c1,
                           const int64_t *cbase, const ChunkWork &cw, unsigned long long *grab, const int32_t *cinst,
-                          const CellGraph &g, cudaStream_t st);
+                          const CellGraph &g, const StageArgs &sa, cudaStream_t st);
 int cedges_cells_per_block();     // cells per block of k_cinc
 cudaError_t launch_cprune_init(const InstDesc *D, const WorkList &wslots, const uint8_t *pflag, const int32_t *pcnt,
                                int32_t *pc, unsigned long long *pk, uint8_t *pinfo, uint32_t *vmask, uint8_t *alive,

@@ -131,6 +131,17 @@ def test_autotuned_shapes_same_result(gis):
     assert fixed[-1][1]["cum_tune_launches"] == 0
 
 
+@pytest.mark.parametrize("per_cell", ["0", "0.4", "3"])
+def test_staged_edges_and_fallbacks(gis, monkeypatch, per_cell):
+    """The count pass stages the walk's edges and a place pass puts them in
+    CSR order. Forced staging sizes: none (the fill walks again), far too
+    small (most chunks lose a flush and are walked again, the rest placed),
+    a little small (a few chunks walked again)."""
+    monkeypatch.setenv("GIS_STAGE_PER_CELL", per_cell)
+    run_both(gis, dict(W.cstr_256(levels=2, n0=23), rule="inner"), 2)
+    run_both(gis, dict(W.cartpole_48(levels=1, n0=5), rule="outer"), 1)
+
+
 def test_everything_leaves(gis):
     """x+ = 2x + 3: every image leaves X, nothing is kept, no split."""
     prob = W.problem(W.linmap([[2.0]], [[1.0]]), [-1.0], [1.0], 16, 2, [[3.0]], 1.0, 0, precision="fp32")
