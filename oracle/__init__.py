@@ -9,7 +9,9 @@ compiled without FMA contraction.
 
 Problems are plain dicts (see ``paper_2202_06111_gb300.workloads``):
 ``dyn`` (name), ``n``, ``m``, ``params``, ``dt``, ``substeps``, ``lo``, ``hi``,
-``n0``, ``k``, ``controls`` (n_u x m), ``rule`` ("inner" | "outer").
+``n0``, ``k``, ``controls`` (n_u x m), ``rule`` ("inner" | "outer"), optionally
+``split_ring`` (cells split besides the boundary cells: those within this many
+rings of them, -1 every kept cell; default 0).
 """
 from __future__ import annotations
 
@@ -69,6 +71,7 @@ def lib():
         L.orc_classify.argtypes = [vp, vp, C.POINTER(i64)]
         L.orc_solve.argtypes = [vp, i32]
         L.orc_set_kept.argtypes = [vp, vp]
+        L.orc_set_ring.argtypes = [vp, i32]
         for name in ("orc_num_live", "orc_num_edges", "orc_num_nodes"):
             getattr(L, name).restype = i64
             getattr(L, name).argtypes = [vp]
@@ -185,6 +188,9 @@ class Solver:
         self._h = lib().orc_create(C.byref(self._s), ctrl.ctypes.data_as(C.POINTER(C.c_double)), self.n_u)
         if not self._h:
             raise ValueError("oracle: invalid problem")
+        ring = int(prob.get("split_ring", 0))
+        if ring:
+            _check(lib().orc_set_ring(self._h, ring))
 
     def __del__(self):
         h = getattr(self, "_h", None)

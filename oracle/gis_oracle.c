@@ -23,8 +23,10 @@
  *     control maps it inside X with every image cell kept;
  *   - boundary classification (Sec. 3.1.1, Alg. 1, Remark 1) in its exact form:
  *     a kept cell is a boundary cell iff its closed box touches the faces of X
- *     or a removed cell;
- *   - subdivision of the boundary cells into 2^n children (Sec. 2.1, Sec. 3.1).
+ *     or a removed cell; optionally the kept cells within a number of rings
+ *     of touching cells around them, standing in for the N nearest neighbours
+ *     of Sec. 3.1.2 (or every kept cell: the all-split scheme);
+ *   - subdivision of the marked cells into 2^n children (Sec. 2.1, Sec. 3.1).
  *
  * Compiled with -O2 -ffp-contract=off and without fast-math, so every
  * floating-point expression rounds after each operation, in C's left-to-right
@@ -87,7 +89,8 @@ typedef struct {
     uint8_t *flag;
     double *bbox;       /* per pair: ymin[0..n-1], ymax[0..n-1] */
     uint8_t *kept;      /* per slot, after prune */
-    uint8_t *bnd;       /* per slot, after classify */
+    uint8_t *bnd;       /* per slot, after classify: the cells to split */
+    int32_t ring;       /* split rings around the boundary cells (-1: every kept cell) */
 } orc_solver;
 
 static int orc_threads = 1;
@@ -319,6 +322,8 @@ typedef struct {
     int32_t *out;       /* NULL: count only */
     int64_t count;
     int touch_dead;
+    const uint8_t *mark; /* if not NULL: hit = some live leaf met has its slot marked */
+    int hit;
 } orc_acc;
 
 static void orc_visit(const orc_solver *S, int64_t node, const orc_ranges *R, orc_acc *acc)
@@ -332,6 +337,7 @@ static void orc_visit(const orc_solver *S, int64_t node, const orc_ranges *R, or
         for (int64_t c = 0; c < nc; c++) orc_visit(S, nd->child + c, R, acc);
     } else if (nd->state == ORC_ALIVE) {
         if (acc->out) acc->out[acc->count] = (int32_t)S->slot_of[node];
+        if (acc->mark && acc->mark[S->slot_of[node]]) acc->hit = 1;
         acc->count++;
     } else {
         acc->touch_dead = 1;
@@ -646,18 +652,13 @@ int orc_set_kept(orc_solver *S, const uint8_t *kept)
     return ORC_OK;
 }
 
-/* Exact boundary rule (Sec. 3.1.1, Alg. 1 with Remark 1's edge points, as the
- * enlargement delta goes to 0): a kept cell is a boundary cell iff its closed
- * box touches a face of X, or some leaf whose closed box meets it is removed.
- * Neighbour ranges are exact integer arithmetic: a level-L' cell j meets the
- * level-L cell i iff ceil(idx_i / 2^(L-L')) - 1 <= j <= floor((idx_i+1) / 2^(L-L'))
- * for L' <= L, and idx_i 2^(L'-L) - 1 <= j <= (idx_i+1) 2^(L'-L) for L' > L. */
-static int orc_is_boundary(const orc_solver *S, const orc_node *nd)
+/* Per-level index ranges of the leaves whose closed boxes meet the closed box
+ * of node nd: exact integer arithmetic, a level-L' cell j meets the level-L
+ * cell i iff ceil(idx_i / 2^(L-L')) - 1 <= j <= floor((idx_i+1) / 2^(L-L')) for
+ * L' <= L, and idx_i 2^(L'-L) - 1 <= j <= (idx_i+1) 2^(L'-L) for L' > L. */
+static void orc_touch_ranges(const orc_solver *S, const orc_node *nd, orc_ranges *R)
 {
     int n = S->P.n, L = nd->level;
-    for (int d = 0; d < n; d++)
-        if (nd->idx[d] == 0 || nd->idx[d] == orc_cells(&S->P, L, d) - 1) return 1;
-    orc_ranges R;
     for (int Lp = 0; Lp <= S->max_level; Lp++) {
         for (int d = 0; d < n; d++) {
             int64_t a, b, i = nd->idx[d];
@@ -673,16 +674,64 @@ static int orc_is_boundary(const orc_solver *S, const orc_node *nd)
             int64_t last = orc_cells(&S->P, Lp, d) - 1;
             if (a < 0) a = 0;
             if (b > last) b = last;
-            R.rng[Lp][d][0] = a;
-            R.rng[Lp][d][1] = b;
+            R->rng[Lp][d][0] = a;
+            R->rng[Lp][d][1] = b;
         }
     }
-    orc_acc acc = {NULL, 0, 0};
+}
+
+/* Exact boundary rule (Sec. 3.1.1, Alg. 1 with Remark 1's edge points, as the
+ * enlargement delta goes to 0): a kept cell is a boundary cell iff its closed
+ * box touches a face of X, or some leaf whose closed box meets it is removed. */
+static int orc_is_boundary(const orc_solver *S, const orc_node *nd)
+{
+    int n = S->P.n, L = nd->level;
+    for (int d = 0; d < n; d++)
+        if (nd->idx[d] == 0 || nd->idx[d] == orc_cells(&S->P, L, d) - 1) return 1;
+    orc_ranges R;
+    orc_touch_ranges(S, nd, &R);
+    orc_acc acc = {NULL, 0, 0, NULL, 0};
     orc_descend(S, &R, &acc);
     return acc.touch_dead;
 }
 
-/* Remove the cells the prune dropped, classify the kept ones. */
+/* The neighbourhood that stands in for the paper's N nearest neighbours (Sec.
+ * 3.1.2): ring r adds the kept cells whose closed boxes meet a cell of ring
+ * r - 1, ring 0 being the boundary cells; ring = -1 marks every kept cell
+ * (the all-split scheme the adaptive one is compared with). */
+int orc_set_ring(orc_solver *S, int32_t ring)
+{
+    if (!S || ring < -1 || ring > 64) return ORC_EINVAL;
+    S->ring = ring;
+    return ORC_OK;
+}
+
+static int orc_grow_rings(orc_solver *S)
+{
+    if (S->ring == -1) {
+        for (int64_t s = 0; s < S->n_live; s++) S->bnd[s] = S->kept[s];
+        return ORC_OK;
+    }
+    uint8_t *next = (uint8_t *)malloc((size_t)(S->n_live ? S->n_live : 1));
+    if (!next) return ORC_ENOMEM;
+    for (int r = 0; r < S->ring; r++) {
+        for (int64_t s = 0; s < S->n_live; s++) {
+            next[s] = S->bnd[s];
+            if (next[s] || !S->kept[s]) continue;
+            orc_ranges R;
+            orc_touch_ranges(S, &S->nodes[S->live[s]], &R);
+            orc_acc acc = {NULL, 0, 0, S->bnd, 0};
+            orc_descend(S, &R, &acc);
+            next[s] = (uint8_t)acc.hit;
+        }
+        memcpy(S->bnd, next, (size_t)S->n_live);
+    }
+    free(next);
+    return ORC_OK;
+}
+
+/* Remove the cells the prune dropped, classify the kept ones, and add the
+ * rings around the boundary cells. */
 int orc_classify(orc_solver *S, uint8_t *bnd_out, int64_t *n_bnd)
 {
     if (!S || !S->have_prune) return ORC_ESTATE;
@@ -691,12 +740,12 @@ int orc_classify(orc_solver *S, uint8_t *bnd_out, int64_t *n_bnd)
     free(S->bnd);
     S->bnd = (uint8_t *)calloc((size_t)(S->n_live ? S->n_live : 1), 1);
     if (!S->bnd) return ORC_ENOMEM;
+    for (int64_t s = 0; s < S->n_live; s++)
+        if (S->kept[s]) S->bnd[s] = (uint8_t)orc_is_boundary(S, &S->nodes[S->live[s]]);
+    int rc = orc_grow_rings(S);
+    if (rc != ORC_OK) return rc;
     int64_t nb = 0;
-    for (int64_t s = 0; s < S->n_live; s++) {
-        if (!S->kept[s]) continue;
-        S->bnd[s] = (uint8_t)orc_is_boundary(S, &S->nodes[S->live[s]]);
-        nb += S->bnd[s];
-    }
+    for (int64_t s = 0; s < S->n_live; s++) nb += S->bnd[s];
     if (bnd_out) memcpy(bnd_out, S->bnd, (size_t)S->n_live);
     if (n_bnd) *n_bnd = nb;
     return ORC_OK;

@@ -98,3 +98,55 @@ def test_subdivision_children_and_union(orc):
         F = s.max_level()
         area = sum(4 ** (F - int(l)) for l, t in zip(lv, st) if t != 2)
         assert area == (8 << F) ** 2
+
+
+def _touch(a_lo, a_hi, b_lo, b_hi):
+    """Closed boxes (per-dimension integer bounds at the finest level) meet."""
+    return bool(np.all(a_lo <= b_hi) and np.all(b_lo <= a_hi))
+
+
+@pytest.mark.parametrize("ring", [1, 2, -1])
+def test_split_rings_brute_force(orc, ring):
+    """The rings that stand in for the N nearest neighbours (Sec. 3.1.2): ring r
+    adds the kept cells whose closed boxes meet a cell of ring r - 1, ring 0
+    being the exact boundary cells; -1 splits every kept cell. Checked at a
+    refined level (leaves of two levels) against brute force over closed boxes
+    in integer coordinates of the finest level."""
+    base = W.problem(W.vdp(1.0), [-3, -3], [3, 3], 8, 3, W.controls_grid(-1, 1, 3), 0.25, 2, rule="outer",
+                     precision="fp64")
+    s = orc.Solver(dict(base, split_ring=ring))
+    s.build_graph()
+    s.prune()
+    s.subdivide()
+    s.build_graph()
+    s.prune()
+    lv, idx = s.live()
+    kept = s.kept()
+    F = int(lv.max())
+    lo = idx.astype(np.int64) << (F - lv[:, None])
+    hi = (idx.astype(np.int64) + 1) << (F - lv[:, None])
+    top = np.array(base["n0"], np.int64) << F
+    # removed leaves: the removed cells of this level and the removed leaves of the tree
+    nl, nst, nidx, _ = s.nodes()
+    dead = [(nidx[j].astype(np.int64) << (F - nl[j]), (nidx[j].astype(np.int64) + 1) << (F - nl[j]))
+            for j in range(len(nl)) if nst[j] == orc.DEAD]
+    dead += [(lo[c], hi[c]) for c in range(len(lv)) if not kept[c]]
+    mark = np.zeros(len(lv), bool)
+    for c in range(len(lv)):
+        if kept[c]:
+            mark[c] = bool(np.any(lo[c] == 0) or np.any(hi[c] == top)) or \
+                any(_touch(lo[c], hi[c], a, b) for a, b in dead)
+    want0 = mark.copy()
+    if ring == -1:
+        mark = kept.copy()
+    for _ in range(max(ring, 0)):
+        nxt = mark.copy()
+        for c in range(len(lv)):
+            if kept[c] and not mark[c]:
+                nxt[c] = any(mark[o] and _touch(lo[c], hi[c], lo[o], hi[o]) for o in range(len(lv)))
+        mark = nxt
+    got = s.classify()
+    # (all-split leaves one live level; the removed root cells stay as leaves)
+    assert len(set(lv.tolist())) == (1 if ring == -1 else 2)
+    assert 0 < want0.sum() < mark.sum() <= kept.sum()
+    assert np.array_equal(got, mark)
