@@ -55,6 +55,8 @@ def _workload(name):
         return {"serving": W.serving_2000()}
     if name == "batch_512":
         return {"batch": W.batch_512()}
+    if name == "cstr_paper_rings":
+        return {"rings": dict(W.cstr_paper_problem(n0=(16, 16), levels=6), rule="outer")}
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -451,9 +453,67 @@ def run_batch(a, probs):
     print(json.dumps(line), flush=True)
 
 
+def run_rings(a, prob):
+    """The paper's own CSTR (Eq. 4, Table 2) refined six times, splitting the
+    boundary cells only (ring 0, the exact rule) or also the kept cells within
+    1, 3, 5 rings of them (the neighbourhood that stands in for the N nearest
+    neighbours of Sec. 3.1.2), against splitting every kept cell (-1): solve
+    time, cells built, and the kept volume (the outer approximation's size,
+    smaller is tighter)."""
+    import numpy as np
+    import torch
+    from paper_2202_06111_gb300 import build, gis
+
+    build.build()
+    gis.load()
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    n = prob["n"]
+    roots = float(np.prod(prob["n0"]))
+    clk = Clocks(dev)
+    rings = {}
+    for ring in (0, 1, 3, 5, -1):
+        p = dict(prob, split_ring=ring)
+        ms, st, vol = [], None, 0.0
+        for it in range(max(1, a.warmup) + max(1, a.steps)):
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                c = gis.Context(p, stream=stream.cuda_stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c.solve()
+            e1.record(stream)
+            e1.synchronize()
+            if it >= max(1, a.warmup):
+                ms.append(e0.elapsed_time(e1))
+            st = c.stats()
+            lv, _ = c.kept_cells()
+            vol = float(np.sum(np.ldexp(1.0, -n * lv.astype(np.int64)))) / roots
+            c.close()
+        rings["all" if ring < 0 else str(ring)] = {
+            "ms": statistics.median(ms), "cells_built": st["cum_cells_built"], "kept": int(st["n_kept"]),
+            "kept_volume_fraction": vol}
+    clocks = clk.stop()
+    r0 = rings["0"]
+    line = {"metric": "graph-construction cells/s", "value": r0["cells_built"] / (r0["ms"] / 1e3),
+            "unit": "cells/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": r0["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "cstr_paper_rings", "system": "cstr_paper (Eq. 4, Table 2)",
+                       "root_cells": prob["n0"], "samples_per_dim": prob["k"], "controls": len(prob["controls"]),
+                       "levels": prob["levels"], "rule": "outer", "split": "boundary + rings 0/1/3/5, or all",
+                       "precision": "fp32 propagation, double-word / fp64 recheck"},
+            "rings": rings, "all_split_over_adaptive": rings["all"]["ms"] / r0["ms"], "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = _args()
     prob = _workload(a.workload)
+    if "rings" in prob:
+        if a.impl == "gis":
+            run_rings(a, prob["rings"])
+        return
     if "batch" in prob:
         if a.impl == "gis":
             run_batch(a, prob["batch"])

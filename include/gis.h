@@ -118,6 +118,13 @@ typedef struct {
                                the first work of each kind (per dynamics, n, samples
                                per dimension, controls; cached for the process);
                                1: the built-in choices. Results do not depend on it */
+    int32_t split_ring;     /* cells a subdivision splits: the boundary cells
+                               (Sec. 3.1.1, exact rule) plus the kept cells within
+                               this many rings of cells meeting their closed boxes
+                               (the neighbourhood that stands in for the N nearest
+                               neighbours of Sec. 3.1.2); -1: every kept cell (the
+                               all-split scheme); 0 (default): the boundary only    */
+    int32_t reserved;
 } gis_options;
 
 /* One live cell: box = prod [lo + idx w_level, lo + (idx+1) w_level],

@@ -621,6 +621,7 @@ struct Engine {
     uint8_t *alive = nullptr; size_t c_alive = 0;
     int32_t *front[2] = {}; size_t c_front[2] = {0, 0};
     uint8_t *bnd = nullptr; size_t c_bnd = 0;
+    uint8_t *bnd2 = nullptr; size_t c_bnd2 = 0;   // the rings' second buffer
     int64_t *packed = nullptr; size_t c_packed = 0;
     int64_t *pscan = nullptr; size_t c_pscan = 0;
     uint8_t *scratch = nullptr; size_t c_scratch = 0;
@@ -645,6 +646,7 @@ struct Engine {
         else gis_default_options(&opt);
         if (opt.enclosure_store < 0 || opt.enclosure_store > 2) throw Error{GIS_EINVAL, "enclosure_store: 0, 1 or 2"};
         if (opt.fixed_shapes != 0 && opt.fixed_shapes != 1) throw Error{GIS_EINVAL, "fixed_shapes: 0 or 1"};
+        if (opt.split_ring < -1 || opt.split_ring > 64) throw Error{GIS_EINVAL, "split_ring: -1 .. 64"};
         if (opt.lanes_per_pair != 0 && opt.lanes_per_pair != 1 && opt.lanes_per_pair != 2 && opt.lanes_per_pair != 4 &&
             opt.lanes_per_pair != 8 && opt.lanes_per_pair != 16)
             throw Error{GIS_EINVAL, "lanes_per_pair: 0 (auto), 1, 2, 4, 8 or 16"};
@@ -1594,6 +1596,22 @@ struct Engine {
             auto sub = with_n(cont, n);
             if (sub.empty()) continue;
             CK(launch_classify(n, d_desc, make_work(slot_ranges(sub), 256), alive, bnd, packed, inst_i32, st));
+        }
+        // the rings around the boundary cells (or every kept cell)
+        if (opt.split_ring != 0) {
+            mem.ensure(bnd2, c_bnd2, NLs);
+            const int passes = opt.split_ring < 0 ? 1 : opt.split_ring;
+            for (int r = 0; r < passes; r++) {
+                CK(cudaMemsetAsync(bnd2, 0, NLs, st));
+                for (int n = 1; n <= MAXN; n++) {
+                    auto sub = with_n(cont, n);
+                    if (sub.empty()) continue;
+                    CK(launch_ring(n, opt.split_ring, d_desc, make_work(slot_ranges(sub), 256), alive, bnd, bnd2,
+                                   packed, inst_i32, st));
+                }
+                std::swap(bnd, bnd2);
+                std::swap(c_bnd, c_bnd2);
+            }
         }
         CK(launch_scan_i64(packed, pscan, NL, scratch, st));
         std::vector<int64_t> be(2 * cont.size());

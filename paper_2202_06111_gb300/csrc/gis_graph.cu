@@ -409,6 +409,88 @@ cudaError_t launch_classify(int n, const InstDesc *D, const WorkList &w, const u
     return cudaGetLastError();
 }
 
+// A ring of the neighbourhood that stands in for the N nearest neighbours of
+// Sec. 3.1.2: a kept cell not yet marked is marked when a live leaf whose closed
+// box meets its own is marked (the same closed-touch descent as k_classify);
+// ALL marks every kept cell (the all-split scheme).
+template <int N, bool ALL>
+__global__ void __launch_bounds__(256) k_ring(const InstDesc *__restrict__ D, const Range *__restrict__ R, int nr,
+                                              const uint8_t *__restrict__ alive, const uint8_t *__restrict__ bnd_in,
+                                              uint8_t *__restrict__ bnd_out, int64_t *__restrict__ packed,
+                                              int32_t *__restrict__ inst_maxlvl)
+{
+    RANGE_HEAD(256)
+    const int64_t s = rg.first + local;
+    bool b = bnd_in[s];
+    if (!alive[s] || b) {
+        bnd_out[s] = b;
+        return;
+    }
+    const int node = I.live[s - I.slot_base];
+    const int L = I.lvl[node];
+    if (ALL) {
+        b = true;
+    } else {
+        int idx[N];
+#pragma unroll
+        for (int d = 0; d < N; d++) idx[d] = I.idx[d][node];
+        auto rf = [&](int Lp, int d, int &a, int &bb) {
+            const int i = idx[d];
+            if (Lp <= L) {
+                const int sh = L - Lp;
+                a = ((i + (1 << sh) - 1) >> sh) - 1;
+                bb = (i + 1) >> sh;
+            } else {
+                const int sh = Lp - L;
+                a = (i << sh) - 1;
+                bb = (i + 1) << sh;
+            }
+            const int last = (I.n0[d] << Lp) - 1;
+            a = a < 0 ? 0 : a;
+            bb = bb > last ? last : bb;
+        };
+        bool hit = false;
+        auto visit = [&](int nd, uint8_t st) {
+            if (st == ST_ALIVE && bnd_in[I.slot[nd]]) {
+                hit = true;
+                return false;
+            }
+            return true;
+        };
+        descend<N>(I, rf, visit);
+        b = hit;
+    }
+    bnd_out[s] = b;
+    if (b) {
+        packed[s] = 1;
+        atomicMax(&inst_maxlvl[rg.inst], L + 1);
+    }
+}
+
+cudaError_t launch_ring(int n, int ring, const InstDesc *D, const WorkList &w, const uint8_t *alive,
+                        const uint8_t *bnd_in, uint8_t *bnd_out, int64_t *packed, int32_t *inst_maxlvl,
+                        cudaStream_t st)
+{
+    if (w.n_blocks == 0) return cudaSuccess;
+    dim3 g((unsigned)w.n_blocks), b(256);
+#define RING_CASE(NN)                                                                                        \
+    case NN:                                                                                                 \
+        if (ring < 0)                                                                                        \
+            k_ring<NN, true><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges, alive, bnd_in, bnd_out, packed,      \
+                                              inst_maxlvl);                                                  \
+        else                                                                                                 \
+            k_ring<NN, false><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges, alive, bnd_in, bnd_out, packed,     \
+                                               inst_maxlvl);                                                 \
+        note_launch();                                                                                       \
+        break;
+    switch (n) {
+        RING_CASE(1) RING_CASE(2) RING_CASE(3) RING_CASE(4)
+    default: return cudaErrorInvalidValue;
+    }
+#undef RING_CASE
+    return cudaGetLastError();
+}
+
 // New live list of an instance: its kept, unsplit cells in slot order, then
 // the children of its boundary cells (child c of the r-th boundary cell at
 // n_keep + 2^n r + c, node id n_nodes + 2^n r + c, idx 2 idx + bit).

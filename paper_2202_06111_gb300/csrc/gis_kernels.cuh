@@ -211,6 +211,12 @@ cudaError_t launch_cexport(const InstDesc *D, const WorkList &w8, const int64_t 
 cudaError_t launch_mark_dead(const InstDesc *D, const WorkList &wslots, const uint8_t *alive, cudaStream_t st);
 cudaError_t launch_classify(int n, const InstDesc *D, const WorkList &wslots, const uint8_t *alive,
                             uint8_t *bnd, int64_t *packed, int32_t *inst_maxlvl, cudaStream_t st);
+// one ring around the marked cells (ring < 0: every kept cell): bnd_out marks
+// bnd_in's cells and the kept cells meeting one of them; packed and the
+// per-problem finest level follow
+cudaError_t launch_ring(int n, int ring, const InstDesc *D, const WorkList &wslots, const uint8_t *alive,
+                        const uint8_t *bnd_in, uint8_t *bnd_out, int64_t *packed, int32_t *inst_maxlvl,
+                        cudaStream_t st);
 struct SplitInst {               // per instance, for the split kernel
     int32_t *new_live;
     int32_t n_nodes;             // first child id

@@ -52,7 +52,8 @@ class gis_controls(C.Structure):
 class gis_options(C.Structure):
     _fields_ = [("rule", C.c_int32), ("precision", C.c_int32), ("band", C.c_double),
                 ("lanes_per_pair", C.c_int32), ("timing", C.c_int32), ("max_device_bytes", C.c_int64),
-                ("round_limit", C.c_int64), ("enclosure_store", C.c_int32), ("fixed_shapes", C.c_int32)]
+                ("round_limit", C.c_int64), ("enclosure_store", C.c_int32), ("fixed_shapes", C.c_int32),
+                ("split_ring", C.c_int32), ("reserved", C.c_int32)]
 
 
 class gis_cell(C.Structure):
@@ -204,6 +205,8 @@ def options(p: dict | None = None, **kw) -> gis_options:
         o.precision = PRECISIONS[p.get("precision", "fp32")]
         if "band" in p:
             o.band = p["band"]
+        if "split_ring" in p:
+            o.split_ring = int(p["split_ring"])
     for k, v in kw.items():
         setattr(o, k, v)
     return o

@@ -142,6 +142,18 @@ def test_staged_edges_and_fallbacks(gis, monkeypatch, per_cell):
     run_both(gis, dict(W.cartpole_48(levels=1, n0=5), rule="outer"), 1)
 
 
+@pytest.mark.parametrize("ring", [1, 3, -1])
+@pytest.mark.parametrize("rule", ["inner", "outer"])
+def test_split_rings(gis, ring, rule):
+    """Subdivision of the boundary cells plus the kept cells within `ring`
+    rings of them (-1: every kept cell), level by level against the oracle."""
+    run_both(gis, dict(W.cstr_256(levels=2, n0=17), rule=rule, split_ring=ring), 2)
+
+
+def test_split_rings_4d(gis):
+    run_both(gis, dict(W.cartpole_48(levels=1, n0=5), rule="outer", split_ring=1), 1)
+
+
 def test_everything_leaves(gis):
     """x+ = 2x + 3: every image leaves X, nothing is kept, no split."""
     prob = W.problem(W.linmap([[2.0]], [[1.0]]), [-1.0], [1.0], 16, 2, [[3.0]], 1.0, 0, precision="fp32")
