@@ -929,7 +929,8 @@ cudaError_t launch_place(const int64_t *cbase, const int32_t *chk_cell, const in
 // chunks than the arrays hold. Zeroes the per-cell edge and in-degree counts.
 __global__ void __launch_bounds__(256) k_cexpand(const int64_t *__restrict__ cbase, int64_t NL, int64_t cap,
                                                  int32_t *__restrict__ cell, int32_t *__restrict__ stop,
-                                                 int32_t *__restrict__ ccnt, int32_t *__restrict__ rcnt)
+                                                 int32_t *__restrict__ ccnt, int32_t *__restrict__ rcnt,
+                                                 uint8_t *__restrict__ lost)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s < NL) {
@@ -941,14 +942,17 @@ __global__ void __launch_bounds__(256) k_cexpand(const int64_t *__restrict__ cba
         return;
     }
     if (s >= NL) return;
-    for (int64_t k = cbase[s]; k < cbase[s + 1]; k++) cell[k] = (int32_t)s;
+    for (int64_t k = cbase[s]; k < cbase[s + 1]; k++) {
+        cell[k] = (int32_t)s;
+        if (lost) lost[k] = 0;
+    }
 }
 
 cudaError_t launch_cexpand(const int64_t *cbase, int64_t NL, const ChunkWork &cw, int32_t *ccnt, int32_t *rcnt,
-                           cudaStream_t st)
+                           uint8_t *lost, cudaStream_t st)
 {
     if (NL == 0) return cudaSuccess;
-    k_cexpand<<<(unsigned)((NL + 255) / 256), 256, 0, st>>>(cbase, NL, cw.cap, cw.cell, cw.stop, ccnt, rcnt);
+    k_cexpand<<<(unsigned)((NL + 255) / 256), 256, 0, st>>>(cbase, NL, cw.cap, cw.cell, cw.stop, ccnt, rcnt, lost);
     note_launch();
     return cudaGetLastError();
 }

@@ -1358,8 +1358,7 @@ struct Engine {
                 sa.seg = seg;
                 sa.seg_cap = (int64_t)c_seg;
                 mem.ensure(chk_lost, c_chk_lost, (size_t)cap);
-                sa.lost = chk_lost;
-                CK(cudaMemsetAsync(chk_lost, 0, (size_t)cap, st));
+                sa.lost = chk_lost;                // zeroed by k_cexpand
             }
             const ChunkWork cw{chk_cell, chk_cnt, nullptr, ctl + 18, cap};
             mem.ensure(scratch, c_scratch, scan_scratch_bytes(std::max<int64_t>(P, NL) + 1));
@@ -1368,7 +1367,7 @@ struct Engine {
             // staged edges (40, 41), segments (42), staging overflow (43)
             CK(cudaMemsetAsync(ctl + 12, 0, 32 * sizeof(int32_t), st));
             if (attempt > 0) CK(cudaMemsetAsync(pcnt, 0, Ps * sizeof(int32_t), st));   // k_cinc ran
-            CK(launch_cexpand(cbase, NL, cw, ccnt, rcnt, st));
+            CK(launch_cexpand(cbase, NL, cw, ccnt, rcnt, sa.lost, st));
             for (int n = 1; n <= MAXN; n++)
                 CK(launch_cedges(false, n, seg_depth[n], d_desc, seg_base[n], seg_base[n + 1], cbase, cw,
                                  grab + (n - 1), cinst, g, sa, st));
@@ -1378,8 +1377,7 @@ struct Engine {
             }
             timer.end();
             timer.begin(PH_SCAN);
-            CK(launch_scan_i32(ccnt, coff, NL, scratch, st));
-            CK(launch_scan_i32(rcnt, roff, NL, scratch, st));
+            CK(launch_scan2_i32(ccnt, coff, rcnt, roff, NL, scratch, st));
             timer.end();
             unsigned char *hp = pinned(256);
             CK(cudaMemcpyAsync(hp, coff + NL, sizeof(int64_t), cudaMemcpyDeviceToHost, st));

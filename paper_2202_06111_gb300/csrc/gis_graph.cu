@@ -119,7 +119,7 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *total)
 }
 
 template <class T>
-__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const T *__restrict__ in, int64_t n, int64_t *__restrict__ part)
+__device__ __forceinline__ void scan_reduce_tile(const T *__restrict__ in, int64_t n, int64_t *__restrict__ part)
 {
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
     int64_t s = 0;
@@ -132,11 +132,17 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const T *__restrict__ in
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
+template <class T>
+__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const T *__restrict__ in, int64_t n, int64_t *__restrict__ part)
+{
+    scan_reduce_tile<T>(in, n, part);
+}
+
 // part_scan: the scanned tile sums, or (raw) the tile sums themselves
 template <class T>
-__global__ void __launch_bounds__(SCAN_T) k_scan_apply(const T *__restrict__ in, int64_t n,
-                                                       const int64_t *__restrict__ part_scan, bool raw,
-                                                       int64_t *__restrict__ out)
+__device__ __forceinline__ void scan_apply_tile(const T *__restrict__ in, int64_t n,
+                                                const int64_t *__restrict__ part_scan, bool raw,
+                                                int64_t *__restrict__ out)
 {
     __shared__ int64_t s_v[SCAN_TILE];
     __shared__ int64_t s_pre;
@@ -172,6 +178,28 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_apply(const T *__restrict__ in,
         if (j < n) out[j] = s_v[i];
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = pre + tot;   // thread 0: pre = block offset
+}
+
+template <class T>
+__global__ void __launch_bounds__(SCAN_T) k_scan_apply(const T *__restrict__ in, int64_t n,
+                                                       const int64_t *__restrict__ part_scan, bool raw,
+                                                       int64_t *__restrict__ out)
+{
+    scan_apply_tile<T>(in, n, part_scan, raw, out);
+}
+
+// Two scans of the same length in the same launches (blockIdx.y picks one).
+__global__ void __launch_bounds__(SCAN_T) k_scan2_reduce(const int32_t *__restrict__ a, const int32_t *__restrict__ b,
+                                                         int64_t n, int64_t *__restrict__ part, int64_t nb)
+{
+    scan_reduce_tile<int32_t>(blockIdx.y ? b : a, n, part + blockIdx.y * nb);
+}
+__global__ void __launch_bounds__(SCAN_T) k_scan2_apply(const int32_t *__restrict__ a, const int32_t *__restrict__ b,
+                                                        int64_t n, const int64_t *__restrict__ part, int64_t nb,
+                                                        int64_t *__restrict__ oa, int64_t *__restrict__ ob)
+{
+    scan_apply_tile<int32_t>(blockIdx.y ? b : a, n, part ? part + blockIdx.y * nb : nullptr, part != nullptr,
+                             blockIdx.y ? ob : oa);
 }
 
 size_t scan_scratch_bytes(int64_t n)
@@ -216,6 +244,24 @@ cudaError_t launch_scan_i32(const int32_t *in, int64_t *out, int64_t n, void *sc
 cudaError_t launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, void *scratch, cudaStream_t st)
 {
     return scan_rec<int64_t>(in, out, n, (int64_t *)scratch, st);
+}
+
+cudaError_t launch_scan2_i32(const int32_t *a, int64_t *oa, const int32_t *b, int64_t *ob, int64_t n, void *scratch,
+                             cudaStream_t st)
+{
+    const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (n == 0 || nb > SCAN_DIRECT) {          // large: the scans one after the other
+        cudaError_t e = launch_scan_i32(a, oa, n, scratch, st);
+        return e != cudaSuccess ? e : launch_scan_i32(b, ob, n, scratch, st);
+    }
+    int64_t *part = (int64_t *)scratch;
+    if (nb > 1) {
+        k_scan2_reduce<<<dim3((unsigned)nb, 2), SCAN_T, 0, st>>>(a, b, n, part, nb);
+        note_launch();
+    }
+    k_scan2_apply<<<dim3((unsigned)nb, 2), SCAN_T, 0, st>>>(a, b, n, nb > 1 ? part : nullptr, nb, oa, ob);
+    note_launch();
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

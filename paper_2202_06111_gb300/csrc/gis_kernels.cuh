@@ -73,6 +73,9 @@ cudaError_t launch_recheck(int phase, int dyn, int n, const RecheckArgs &a, cuda
 size_t scan_scratch_bytes(int64_t n);
 cudaError_t launch_scan_i32(const int32_t *in, int64_t *out, int64_t n, void *scratch, cudaStream_t st);
 cudaError_t launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, void *scratch, cudaStream_t st);
+// two int32 scans of the same length in the same launches
+cudaError_t launch_scan2_i32(const int32_t *a, int64_t *oa, const int32_t *b, int64_t *ob, int64_t n, void *scratch,
+                             cudaStream_t st);
 cudaError_t launch_scan_u8(const uint8_t *in, int64_t *out, int64_t n, void *scratch, cudaStream_t st);
 cudaError_t launch_inst_totals(const int64_t *pscan, const int64_t *be, int n, int64_t *out, cudaStream_t st);
 cudaError_t launch_init_roots(uint8_t *lvl, uint8_t *state, int32_t *const *idx, int32_t *child, int32_t *live,
@@ -172,9 +175,10 @@ struct StageArgs {
 };
 cudaError_t launch_place(const int64_t *cbase, const int32_t *chk_cell, const int64_t *chk_off, int64_t nchunks,
                          const StageArgs &sa, bool any_lost, int64_t nseg, const CellGraph &g, cudaStream_t st);
-// the cell of each chunk; zeroes the per-cell counts ccnt and rcnt
+// the cell of each chunk; zeroes the per-cell counts ccnt and rcnt and, with
+// lost, the chunks' lost marks
 cudaError_t launch_cexpand(const int64_t *cbase, int64_t NL, const ChunkWork &cw, int32_t *ccnt, int32_t *rcnt,
-                           cudaStream_t st);
+                           uint8_t *lost, cudaStream_t st);
 // edges of the walked cells c0 <= s < c1, all of dimension n and at most
 // `depth` levels below their roots; cbase = exclusive scan of the chunk
 // counts; grab: the chunk counter of this launch (zeroed)
