@@ -120,6 +120,21 @@ def _dist():
     return ws, rank, local
 
 
+def aggregate_ranks(total_ms, cells, ws, device="cpu"):
+    """Whole-job throughput of ws independent replicas (one per rank, no
+    data-path collective): the cells every rank built over the slowest rank's
+    time. Returns (max time in ms, cells over all ranks, cells/s)."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        c = torch.tensor([float(cells)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        total_ms, cells = float(t.item()), float(c.item())
+    return total_ms, cells, cells / (total_ms / 1e3)
+
+
 def cpu_baseline(prob, seconds_cap=30.0):
     """The oracle as it stands, all host threads, on the full workload (one solve)."""
     import oracle
@@ -223,15 +238,10 @@ def run_gis(a, prob):
         c.close()
     torch.cuda.synchronize()
     clocks = clk.stop() if clk else None
-    total_ms = sum(per_step)
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     cells = sum(s["cum_cells_built"] for s in stats)
     edges = sum(s["cum_edges"] for s in stats)
     launches = sum(s["cum_launches"] for s in stats)
-    value = cells * ws / (total_ms / 1e3)
+    total_ms, _, value = aggregate_ranks(sum(per_step), cells, ws, "cuda")
 
     # end to end through the C ABI: create from host arrays, solve, read the kept cells
     e2e_times, d2h = [], 0
