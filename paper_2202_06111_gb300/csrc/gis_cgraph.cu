@@ -1126,12 +1126,21 @@ __global__ void __launch_bounds__(256) k_cprune(CPruneArgs a)
 
 cudaError_t launch_cprune(const CPruneArgs &a, int64_t n_slots, cudaStream_t st)
 {
-    int dev = 0, sms = 0, per_sm = 0;
+    // resident blocks per SM and SMs, queried once per device
+    static int cached_sms[64] = {}, cached_per_sm[64] = {};
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cprune, 256, 0);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached_per_sm[dev]) {
+        int sms_q = 0, per_q = 0;
+        cudaDeviceGetAttribute(&sms_q, cudaDevAttrMultiProcessorCount, dev);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_q, k_cprune, 256, 0);
+        if (e != cudaSuccess) return e;
+        if (per_q < 1) return cudaErrorInvalidConfiguration;
+        cached_sms[dev] = sms_q;
+        cached_per_sm[dev] = per_q;
+    }
+    const int sms = cached_sms[dev], per_sm = cached_per_sm[dev];
     // a block per 256 cells, up to every block that fits (a cooperative launch
     // needs them all resident): large graphs get the most gathers in flight,
     // small ones cheaper grid barriers
