@@ -152,7 +152,7 @@ def _check_fixed_point(s, rule):
 
 @pytest.mark.parametrize("rule", ["inner", "outer"])
 def test_invariants_after_solve(orc, rule):
-    """Spec invariant for INNER: every kept cell has a control whose image
+    """The INNER invariant: every kept cell has a control whose image
     lies in X and whose image cells are all kept; for OUTER every kept cell has
     an edge to a kept cell; and the kept set is a fixed point at every level."""
     prob = dict(W.cstr_256(levels=2, n0=24), rule=rule)
