@@ -9,7 +9,8 @@ compiled without FMA contraction.
 
 Problems are plain dicts (see ``paper_2202_06111_gb300.workloads``):
 ``dyn`` (name), ``n``, ``m``, ``params``, ``dt``, ``substeps``, ``lo``, ``hi``,
-``n0``, ``k``, ``controls`` (n_u x m), ``rule`` ("inner" | "outer"), optionally
+``n0``, ``k``, ``controls`` (n_u x m), ``rule`` ("inner" | "outer" | "scc": the
+largest strongly connected component and its ancestors, Def. 3), optionally
 ``split_ring`` (cells split besides the boundary cells: those within this many
 rings of them, -1 every kept cell; default 0).
 """
@@ -26,7 +27,7 @@ _SRC = os.path.join(_HERE, "gis_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 DYN_IDS = {"linmap": 0, "vdp": 1, "cstr_dl": 2, "cartpole": 3, "cstr_paper": 4}
-RULES = {"inner": 0, "outer": 1}
+RULES = {"inner": 0, "outer": 1, "scc": 2}
 F_INX, F_TOUCH_DEAD, F_NONFINITE = 1, 2, 4
 DEAD, ALIVE, SPLIT = 0, 1, 2
 MAXN = 4

@@ -46,7 +46,7 @@
 #define ORC_MAXLEVEL 16
 
 enum { ORC_LINMAP = 0, ORC_VDP = 1, ORC_CSTR_DL = 2, ORC_CARTPOLE = 3, ORC_CSTR_PAPER = 4 };
-enum { ORC_INNER = 0, ORC_OUTER = 1 };
+enum { ORC_INNER = 0, ORC_OUTER = 1, ORC_SCC = 2 };
 enum { ORC_DEAD = 0, ORC_ALIVE = 1, ORC_SPLIT = 2 };
 enum { ORC_F_INX = 1, ORC_F_TOUCH_DEAD = 2, ORC_F_NONFINITE = 4 };
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2, ORC_ESTATE = -3 };
@@ -61,7 +61,7 @@ typedef struct {
     double lo[ORC_MAXN], hi[ORC_MAXN]; /* X = prod [lo_d, hi_d] */
     int32_t n0[ORC_MAXN]; /* root cells per dimension */
     int32_t k;          /* samples per dimension (k = 1: the cell centre) */
-    int32_t rule;       /* ORC_INNER or ORC_OUTER */
+    int32_t rule;       /* ORC_INNER, ORC_OUTER or ORC_SCC */
 } orc_problem;
 
 typedef struct {
@@ -581,10 +581,126 @@ static int orc_viable_pair(const int64_t *off, const int32_t *tgt, const uint8_t
     return 1;
 }
 
+/* Def. 3 read literally: the largest strongly connected component of the
+ * directed graph (cell i -> cell j when some control of i has target j),
+ * together with every cell that has a path into it. Readings where the
+ * definition is silent: a component must hold a cycle (a single cell counts
+ * only with an edge to itself, else it carries no infinite path); every
+ * component of the largest size is kept; a graph without a cycle keeps
+ * nothing. Components by Tarjan's algorithm (iterative), then a backward
+ * search from the kept components. The targets of cell i are contiguous:
+ * tgt[off[i n_u] .. off[(i+1) n_u]). */
+static int orc_prune_scc(int64_t n_cells, int32_t n_u, const int64_t *off, const int32_t *tgt, uint8_t *kept,
+                         int64_t *n_kept)
+{
+    int64_t N = n_cells ? n_cells : 1;
+    int64_t *index = (int64_t *)malloc((size_t)N * sizeof(int64_t));
+    int64_t *low = (int64_t *)malloc((size_t)N * sizeof(int64_t));
+    int64_t *comp = (int64_t *)malloc((size_t)N * sizeof(int64_t));
+    int64_t *stk = (int64_t *)malloc((size_t)N * sizeof(int64_t));      /* Tarjan's stack */
+    int64_t *cs_node = (int64_t *)malloc((size_t)N * sizeof(int64_t));  /* call stack: node */
+    int64_t *cs_edge = (int64_t *)malloc((size_t)N * sizeof(int64_t));  /*             next edge */
+    uint8_t *on = (uint8_t *)calloc((size_t)N, 1);
+    int64_t *csize = (int64_t *)calloc((size_t)N, sizeof(int64_t));
+    uint8_t *cyc = (uint8_t *)calloc((size_t)N, 1);
+    if (!index || !low || !comp || !stk || !cs_node || !cs_edge || !on || !csize || !cyc) {
+        free(index); free(low); free(comp); free(stk); free(cs_node); free(cs_edge); free(on); free(csize); free(cyc);
+        return ORC_ENOMEM;
+    }
+    for (int64_t i = 0; i < n_cells; i++) index[i] = -1;
+    int64_t counter = 0, sp = 0, ncomp = 0;
+    for (int64_t root = 0; root < n_cells; root++) {
+        if (index[root] >= 0) continue;
+        int64_t depth = 0;
+        cs_node[0] = root;
+        cs_edge[0] = off[root * n_u];
+        index[root] = low[root] = counter++;
+        stk[sp++] = root;
+        on[root] = 1;
+        while (depth >= 0) {
+            int64_t v = cs_node[depth];
+            int64_t e = cs_edge[depth], e1 = off[(v + 1) * n_u];
+            if (e < e1) {
+                cs_edge[depth] = e + 1;
+                int64_t w = tgt[e];
+                if (index[w] < 0) {                 /* descend */
+                    index[w] = low[w] = counter++;
+                    stk[sp++] = w;
+                    on[w] = 1;
+                    depth++;
+                    cs_node[depth] = w;
+                    cs_edge[depth] = off[w * n_u];
+                } else if (on[w] && index[w] < low[v]) {
+                    low[v] = index[w];
+                }
+                continue;
+            }
+            if (low[v] == index[v]) {               /* v roots a component */
+                int64_t w;
+                do {
+                    w = stk[--sp];
+                    on[w] = 0;
+                    comp[w] = ncomp;
+                    csize[ncomp]++;
+                } while (w != v);
+                ncomp++;
+            }
+            depth--;
+            if (depth >= 0) {
+                int64_t u = cs_node[depth];
+                if (low[v] < low[u]) low[u] = low[v];
+            }
+        }
+    }
+    /* components holding a cycle: more than one cell, or a cell with an edge to itself */
+    for (int64_t c = 0; c < ncomp; c++) cyc[c] = csize[c] > 1;
+    for (int64_t i = 0; i < n_cells; i++)
+        for (int64_t e = off[i * n_u]; e < off[(i + 1) * n_u]; e++)
+            if (tgt[e] == i) cyc[comp[i]] = 1;
+    int64_t best = 0;
+    for (int64_t c = 0; c < ncomp; c++)
+        if (cyc[c] && csize[c] > best) best = csize[c];
+    /* the largest components, then every cell with a path into them */
+    int64_t qn = 0;
+    for (int64_t i = 0; i < n_cells; i++) {
+        kept[i] = best > 0 && cyc[comp[i]] && csize[comp[i]] == best;
+        if (kept[i]) stk[qn++] = i;
+    }
+    int64_t E = off[n_cells * n_u];
+    int64_t *poff = (int64_t *)calloc((size_t)N + 1, sizeof(int64_t));
+    int64_t *pred = (int64_t *)malloc((size_t)(E ? E : 1) * sizeof(int64_t));
+    int64_t *fill = (int64_t *)malloc((size_t)N * sizeof(int64_t));
+    int rc = ORC_OK;
+    if (!poff || !pred || !fill) {
+        rc = ORC_ENOMEM;
+    } else {
+        for (int64_t e = 0; e < E; e++) poff[tgt[e] + 1]++;
+        for (int64_t i = 0; i < n_cells; i++) poff[i + 1] += poff[i];
+        for (int64_t i = 0; i < n_cells; i++) fill[i] = poff[i];
+        for (int64_t i = 0; i < n_cells; i++)
+            for (int64_t e = off[i * n_u]; e < off[(i + 1) * n_u]; e++) pred[fill[tgt[e]]++] = i;
+        for (int64_t h = 0; h < qn; h++) {
+            int64_t j = stk[h];
+            for (int64_t e = poff[j]; e < poff[j + 1]; e++)
+                if (!kept[pred[e]]) {
+                    kept[pred[e]] = 1;
+                    stk[qn++] = pred[e];
+                }
+        }
+        int64_t nk = 0;
+        for (int64_t i = 0; i < n_cells; i++) nk += kept[i];
+        if (n_kept) *n_kept = nk;
+    }
+    free(poff); free(pred); free(fill);
+    free(index); free(low); free(comp); free(stk); free(cs_node); free(cs_edge); free(on); free(csize); free(cyc);
+    return rc;
+}
+
 int orc_prune_graph(int64_t n_cells, int32_t n_u, const int64_t *off, const int32_t *tgt,
                     const uint8_t *flag, int32_t rule, uint8_t *kept, int64_t *n_kept)
 {
     if (n_cells < 0 || n_u < 1) return ORC_EINVAL;
+    if (rule == ORC_SCC) return orc_prune_scc(n_cells, n_u, off, tgt, kept, n_kept);
     int64_t P = n_cells * n_u, E = off[P];
     /* predecessors of every cell */
     int64_t *poff = (int64_t *)calloc((size_t)n_cells + 1, sizeof(int64_t));
