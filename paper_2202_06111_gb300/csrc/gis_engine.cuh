@@ -1321,7 +1321,7 @@ struct Engine {
         StageArgs sa{};
         const char *fixed_per = std::getenv("GIS_STAGE_PER_CELL");
         const double fper = fixed_per ? std::atof(fixed_per) : -1.0;
-        if (walked > 0 && fper != 0.0) {
+        if (walked > 0 && fper != 0.0 && cap < ((int64_t)1 << 31)) {   // segment records hold int32 chunk ids
             const double per = fper > 0 ? fper : stage_per_cell > 0 ? 1.25 * stage_per_cell : 64.0;
             const int64_t scap = (int64_t)(per * (double)walked) + (fper > 0 ? 1 : 65536);
             const int64_t gcap = cap + scap / (CE_EB_HOST - 32) + 4096;
@@ -1352,6 +1352,7 @@ struct Engine {
         for (int attempt = 0;; attempt++) {
             mem.ensure(chk_cell, c_chk_cell, (size_t)cap);
             mem.ensure(chk_cnt, c_chk_cnt, (size_t)cap);
+            if (cap >= ((int64_t)1 << 31)) sa = StageArgs{};   // chunk ids beyond a segment record's int32
             if (sa.stg) {
                 // a segment per chunk and per full buffer
                 mem.ensure(seg, c_seg, (size_t)(cap + sa.cap / (CE_EB_HOST - 32) + 4096));
