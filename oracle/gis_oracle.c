@@ -62,6 +62,7 @@ typedef struct {
     int32_t n0[ORC_MAXN]; /* root cells per dimension */
     int32_t k;          /* samples per dimension (k = 1: the cell centre) */
     int32_t rule;       /* ORC_INNER, ORC_OUTER or ORC_SCC */
+    int32_t enclosure;  /* 0: bounding box of the sample lattice; 1: interval enclosure of the cell's image */
 } orc_problem;
 
 typedef struct {
@@ -252,9 +253,13 @@ static int64_t orc_num_samples(const orc_problem *P)
 
 /* Image bounding box of (cell, control): per-dimension min / max over the
  * propagated samples. Returns 0 if every image coordinate is finite, else 1. */
+static int orc_image_enclosure(const orc_problem *P, int L, const int32_t *idx, const double *u,
+                               double *ymin, double *ymax);
+
 static int orc_image_bbox(const orc_problem *P, int L, const int32_t *idx, const double *u,
                           double *ymin, double *ymax)
 {
+    if (P->enclosure == 1) return orc_image_enclosure(P, L, idx, u, ymin, ymax);
     int n = P->n, nonfinite = 0;
     int64_t S = orc_num_samples(P);
     for (int d = 0; d < n; d++) { ymin[d] = INFINITY; ymax[d] = -INFINITY; }
@@ -267,6 +272,194 @@ static int orc_image_bbox(const orc_problem *P, int L, const int32_t *idx, const
             if (y[d] < ymin[d]) ymin[d] = y[d];
             if (y[d] > ymax[d]) ymax[d] = y[d];
         }
+    }
+    return nonfinite;
+}
+
+/* ------------------------------------------------------------------------
+ * Interval enclosure of a cell's image (NEXT f3, "enclosure" = 1): the RK4
+ * step (or the discrete map) evaluated in interval arithmetic over the whole
+ * closed cell, every operation rounded outward, so that the box holds the
+ * exact image of every point of the cell (the sampled box of Sec. 2.4 holds
+ * only the images of the samples). Each result of +, -, *, / is rounded to
+ * nearest (within half an ulp) and then moved one ulp outward. exp, sin and
+ * cos come from the C library, read as within 1 ulp: two ulps outward. The
+ * natural extension over-approximates (each occurrence of a variable ranges
+ * independently), which costs width, not rigour.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    double lo, hi;
+} orc_iv;
+
+static double orc_dn(double x) { return nextafter(x, -INFINITY); }
+static double orc_up(double x) { return nextafter(x, INFINITY); }
+static orc_iv iv_pt(double a) { orc_iv r = {a, a}; return r; }
+static orc_iv iv_wide(double a) { orc_iv r = {orc_dn(a), orc_up(a)}; return r; }   /* a rounded real */
+static orc_iv iv_add(orc_iv a, orc_iv b) { orc_iv r = {orc_dn(a.lo + b.lo), orc_up(a.hi + b.hi)}; return r; }
+static orc_iv iv_sub(orc_iv a, orc_iv b) { orc_iv r = {orc_dn(a.lo - b.hi), orc_up(a.hi - b.lo)}; return r; }
+static orc_iv iv_neg(orc_iv a) { orc_iv r = {-a.hi, -a.lo}; return r; }
+static orc_iv iv_mul(orc_iv a, orc_iv b)
+{
+    double p[4] = {a.lo * b.lo, a.lo * b.hi, a.hi * b.lo, a.hi * b.hi};
+    double lo = p[0], hi = p[0];
+    for (int i = 1; i < 4; i++) {
+        if (isnan(p[i])) { lo = -INFINITY; hi = INFINITY; break; }
+        if (p[i] < lo) lo = p[i];
+        if (p[i] > hi) hi = p[i];
+    }
+    if (isnan(p[0])) { lo = -INFINITY; hi = INFINITY; }
+    orc_iv r = {orc_dn(lo), orc_up(hi)};
+    return r;
+}
+static orc_iv iv_sqr(orc_iv a)
+{
+    double l2 = a.lo * a.lo, h2 = a.hi * a.hi;
+    orc_iv r;
+    if (a.lo >= 0.0) { r.lo = orc_dn(l2); r.hi = orc_up(h2); }
+    else if (a.hi <= 0.0) { r.lo = orc_dn(h2); r.hi = orc_up(l2); }
+    else { r.lo = 0.0; r.hi = orc_up(l2 > h2 ? l2 : h2); }
+    return r;
+}
+static orc_iv iv_div(orc_iv a, orc_iv b)
+{
+    if (!(b.lo > 0.0 || b.hi < 0.0)) { orc_iv r = {-INFINITY, INFINITY}; return r; }   /* 0 in the divisor */
+    orc_iv rb = {orc_dn(1.0 / b.hi), orc_up(1.0 / b.lo)};
+    return iv_mul(a, rb);
+}
+static orc_iv iv_exp(orc_iv a)
+{
+    orc_iv r = {orc_dn(orc_dn(exp(a.lo))), orc_up(orc_up(exp(a.hi)))};
+    if (r.lo < 0.0) r.lo = 0.0;
+    return r;
+}
+/* sin over [lo, hi]: the end values, and +-1 where a maximum (pi/2 + 2 k pi)
+ * or minimum (-pi/2 + 2 k pi) may lie inside (tested with a margin that
+ * covers pi's rounding); cos(x) = sin(x + pi/2) the same way. */
+static int orc_holds_phase(double lo, double hi, double phase)
+{
+    const double twopi = 6.283185307179586;
+    double k = ceil((lo - phase) / twopi - 1e-9);
+    return phase + k * twopi <= hi + 1e-9;
+}
+static orc_iv iv_sin_shift(orc_iv a, int cosine)
+{
+    orc_iv r = {-1.0, 1.0};
+    if (!(a.hi - a.lo < 6.0) || !isfinite(a.lo) || !isfinite(a.hi)) return r;
+    double f0 = cosine ? cos(a.lo) : sin(a.lo), f1 = cosine ? cos(a.hi) : sin(a.hi);
+    double lo = f0 < f1 ? f0 : f1, hi = f0 < f1 ? f1 : f0;
+    lo = orc_dn(orc_dn(lo));
+    hi = orc_up(orc_up(hi));
+    const double halfpi = 1.5707963267948966;
+    double pmax = cosine ? 0.0 : halfpi, pmin = cosine ? 2.0 * halfpi : -halfpi;
+    if (orc_holds_phase(a.lo, a.hi, pmax)) hi = 1.0;
+    if (orc_holds_phase(a.lo, a.hi, pmin)) lo = -1.0;
+    r.lo = lo < -1.0 ? -1.0 : lo;
+    r.hi = hi > 1.0 ? 1.0 : hi;
+    return r;
+}
+
+static void orc_rhs_iv(const orc_problem *P, const orc_iv *x, const orc_iv *u, orc_iv *dx)
+{
+    const double *p = P->p;
+    switch (P->dyn) {
+    case ORC_LINMAP: {
+        int n = P->n, m = P->m;
+        for (int i = 0; i < n; i++) {
+            orc_iv acc = iv_pt(0.0);
+            for (int j = 0; j < n; j++) acc = iv_add(acc, iv_mul(iv_pt(p[i * n + j]), x[j]));
+            for (int j = 0; j < m; j++) acc = iv_add(acc, iv_mul(iv_pt(p[n * n + i * m + j]), u[j]));
+            dx[i] = acc;
+        }
+        break;
+    }
+    case ORC_VDP:
+        dx[0] = x[1];
+        dx[1] = iv_add(iv_add(iv_neg(x[0]), iv_mul(iv_mul(iv_pt(p[0]), iv_sub(iv_pt(1.0), iv_sqr(x[0]))), x[1])), u[0]);
+        break;
+    case ORC_CSTR_DL: {
+        orc_iv e = iv_exp(iv_div(x[1], iv_add(iv_pt(1.0), iv_div(x[1], iv_pt(p[3])))));
+        orc_iv r = iv_mul(iv_mul(iv_pt(p[0]), iv_sub(iv_pt(1.0), x[0])), e);
+        dx[0] = iv_add(iv_neg(x[0]), r);
+        dx[1] = iv_sub(iv_add(iv_neg(x[1]), iv_mul(iv_pt(p[1]), r)), iv_mul(iv_pt(p[2]), iv_sub(x[1], u[0])));
+        break;
+    }
+    case ORC_CARTPOLE: {
+        orc_iv mc = iv_pt(p[0]), mp = iv_pt(p[1]), l = iv_pt(p[2]), g = iv_pt(p[3]);
+        orc_iv s = iv_sin_shift(x[2], 0), c = iv_sin_shift(x[2], 1);
+        orc_iv tot = iv_add(mc, mp), pml = iv_mul(mp, l);
+        orc_iv temp = iv_div(iv_add(u[0], iv_mul(iv_mul(pml, iv_sqr(x[3])), s)), tot);
+        orc_iv four3 = iv_div(iv_pt(4.0), iv_pt(3.0));
+        orc_iv den = iv_mul(l, iv_sub(four3, iv_div(iv_mul(mp, iv_sqr(c)), tot)));
+        orc_iv thacc = iv_div(iv_sub(iv_mul(g, s), iv_mul(c, temp)), den);
+        dx[0] = x[1];
+        dx[1] = iv_sub(temp, iv_div(iv_mul(iv_mul(pml, thacc), c), tot));
+        dx[2] = x[3];
+        dx[3] = thacc;
+        break;
+    }
+    case ORC_CSTR_PAPER: {
+        orc_iv q = iv_pt(p[0]), V = iv_pt(p[1]), cAf = iv_pt(p[2]), Tf = iv_pt(p[3]), ER = iv_pt(p[4]);
+        orc_iv k0 = iv_pt(p[5]), mdH = iv_pt(p[6]), UA = iv_pt(p[7]), cp = iv_pt(p[8]), rho = iv_pt(p[9]);
+        orc_iv rate = iv_mul(iv_mul(k0, iv_exp(iv_neg(iv_div(ER, x[1])))), x[0]);
+        orc_iv qV = iv_div(q, V), rcp = iv_mul(rho, cp);
+        dx[0] = iv_sub(iv_mul(qV, iv_sub(cAf, x[0])), rate);
+        dx[1] = iv_add(iv_add(iv_mul(qV, iv_sub(Tf, x[1])), iv_mul(iv_div(mdH, rcp), rate)),
+                       iv_mul(iv_div(UA, iv_mul(V, rcp)), iv_sub(u[0], x[1])));
+        break;
+    }
+    default:
+        for (int d = 0; d < P->n; d++) { dx[d].lo = -INFINITY; dx[d].hi = INFINITY; }
+    }
+}
+
+static void orc_step_iv(const orc_problem *P, const orc_iv *x0, const orc_iv *u, orc_iv *y)
+{
+    int n = P->n;
+    if (P->substeps == 0) {
+        if (P->dyn == ORC_LINMAP) orc_rhs_iv(P, x0, u, y);
+        else for (int d = 0; d < n; d++) { y[d].lo = -INFINITY; y[d].hi = INFINITY; }
+        return;
+    }
+    orc_iv x[ORC_MAXN], k1[ORC_MAXN], k2[ORC_MAXN], k3[ORC_MAXN], k4[ORC_MAXN], xt[ORC_MAXN];
+    orc_iv h = iv_div(iv_pt(P->dt), iv_pt((double)P->substeps));      /* dt / s as a real */
+    orc_iv hh = iv_mul(h, iv_pt(0.5)), h6 = iv_div(h, iv_pt(6.0)), two = iv_pt(2.0);
+    for (int d = 0; d < n; d++) x[d] = x0[d];
+    for (int st = 0; st < P->substeps; st++) {
+        orc_rhs_iv(P, x, u, k1);
+        for (int d = 0; d < n; d++) xt[d] = iv_add(x[d], iv_mul(hh, k1[d]));
+        orc_rhs_iv(P, xt, u, k2);
+        for (int d = 0; d < n; d++) xt[d] = iv_add(x[d], iv_mul(hh, k2[d]));
+        orc_rhs_iv(P, xt, u, k3);
+        for (int d = 0; d < n; d++) xt[d] = iv_add(x[d], iv_mul(h, k3[d]));
+        orc_rhs_iv(P, xt, u, k4);
+        for (int d = 0; d < n; d++)
+            x[d] = iv_add(x[d], iv_mul(h6, iv_add(iv_add(iv_add(k1[d], iv_mul(two, k2[d])), iv_mul(two, k3[d])),
+                                                  k4[d])));
+    }
+    for (int d = 0; d < n; d++) y[d] = x[d];
+}
+
+/* The closed cell as a box of reals: lo + idx w .. lo + (idx + 1) w with
+ * w = (hi - lo) / (n0 2^L), each bound enclosed in interval arithmetic. */
+static int orc_image_enclosure(const orc_problem *P, int L, const int32_t *idx, const double *u,
+                               double *ymin, double *ymax)
+{
+    int n = P->n;
+    orc_iv x[ORC_MAXN], uu[ORC_MAXM], y[ORC_MAXN];
+    for (int d = 0; d < n; d++) {
+        orc_iv w = iv_div(iv_sub(iv_pt(P->hi[d]), iv_pt(P->lo[d])), iv_pt((double)orc_cells(P, L, d)));
+        orc_iv a = iv_add(iv_pt(P->lo[d]), iv_mul(iv_pt((double)idx[d]), w));
+        orc_iv b = iv_add(a, w);
+        x[d].lo = a.lo;
+        x[d].hi = b.hi;
+    }
+    for (int j = 0; j < P->m; j++) uu[j] = iv_pt(u[j]);
+    orc_step_iv(P, x, uu, y);
+    int nonfinite = 0;
+    for (int d = 0; d < n; d++) {
+        ymin[d] = y[d].lo;
+        ymax[d] = y[d].hi;
+        if (!isfinite(y[d].lo) || !isfinite(y[d].hi)) nonfinite = 1;
     }
     return nonfinite;
 }
