@@ -12,7 +12,8 @@ Problems are plain dicts (see ``paper_2202_06111_gb300.workloads``):
 ``n0``, ``k``, ``controls`` (n_u x m), ``rule`` ("inner" | "outer" | "scc": the
 largest strongly connected component and its ancestors, Def. 3), optionally
 ``enclosure`` ("samples": the bounding box of the sample lattice, default;
-"interval": an interval enclosure of the whole cell's image), optionally
+"interval": an interval enclosure of the whole cell's image), ``split`` ("all":
+2^n children, default; "cycled": 2 children halving one dimension, cycled), optionally
 ``split_ring`` (cells split besides the boundary cells: those within this many
 rings of them, -1 every kept cell; default 0).
 """
@@ -52,7 +53,8 @@ class _Problem(C.Structure):
     _fields_ = [("dyn", C.c_int32), ("n", C.c_int32), ("m", C.c_int32), ("substeps", C.c_int32),
                 ("dt", C.c_double), ("p", C.c_double * 32),
                 ("lo", C.c_double * MAXN), ("hi", C.c_double * MAXN),
-                ("n0", C.c_int32 * MAXN), ("k", C.c_int32), ("rule", C.c_int32), ("enclosure", C.c_int32)]
+                ("n0", C.c_int32 * MAXN), ("k", C.c_int32), ("rule", C.c_int32), ("enclosure", C.c_int32),
+                ("split", C.c_int32)]
 
 
 _lib = None
@@ -120,6 +122,7 @@ def _struct(prob: dict) -> _Problem:
     s.k = prob["k"]
     s.rule = RULES[prob.get("rule", "inner")]
     s.enclosure = {"samples": 0, "interval": 1}[prob.get("enclosure", "samples")]
+    s.split = {"all": 0, "cycled": 1}[prob.get("split", "all")]
     return s
 
 

@@ -63,6 +63,8 @@ typedef struct {
     int32_t k;          /* samples per dimension (k = 1: the cell centre) */
     int32_t rule;       /* ORC_INNER, ORC_OUTER or ORC_SCC */
     int32_t enclosure;  /* 0: bounding box of the sample lattice; 1: interval enclosure of the cell's image */
+    int32_t split;      /* 0: a split cell has 2^n children (every dimension halved); 1: cycled
+                           bisection, 2 children halving dimension (depth mod n) */
 } orc_problem;
 
 typedef struct {
@@ -219,15 +221,27 @@ static void orc_step_eval(const orc_problem *P, const double *x0, const double *
  * Grid geometry (Sec. 2.1): a level-L cell is a closed box of width
  * w_L = (hi - lo) / (n0 * 2^L) per dimension, lower corner lo + idx * w_L.
  * ---------------------------------------------------------------------- */
+/* Halvings of dimension d in a cell at depth L: L with every dimension split
+ * at each level; with cycled bisection depth t splits dimension t mod n, so d
+ * has been halved floor(L / n) times, plus once if d < L mod n. */
+static int orc_dlev(const orc_problem *P, int L, int d)
+{
+    if (P->split != 1) return L;
+    return L / P->n + (d < L % P->n ? 1 : 0);
+}
+
 static double orc_width(const orc_problem *P, int L, int d)
 {
-    return (P->hi[d] - P->lo[d]) / (double)((int64_t)P->n0[d] << L);
+    return (P->hi[d] - P->lo[d]) / (double)((int64_t)P->n0[d] << orc_dlev(P, L, d));
 }
 
 static int64_t orc_cells(const orc_problem *P, int L, int d)
 {
-    return (int64_t)P->n0[d] << L;
+    return (int64_t)P->n0[d] << orc_dlev(P, L, d);
 }
+
+/* children of a split node */
+static int64_t orc_nchild(const orc_problem *P) { return P->split == 1 ? 2 : (int64_t)1 << P->n; }
 
 /* Sample lattice of one cell: k points per dimension, x_j = lo_cell + w (j/(k-1)),
  * corners included; k = 1 is the cell centre. Sample s has digit j_d = (s / k^d) % k. */
@@ -526,7 +540,7 @@ static void orc_visit(const orc_solver *S, int64_t node, const orc_ranges *R, or
     for (int d = 0; d < S->P.n; d++)
         if (nd->idx[d] < R->rng[L][d][0] || nd->idx[d] > R->rng[L][d][1]) return;
     if (nd->state == ORC_SPLIT) {
-        int64_t nc = (int64_t)1 << S->P.n;
+        int64_t nc = orc_nchild(&S->P);
         for (int64_t c = 0; c < nc; c++) orc_visit(S, nd->child + c, R, acc);
     } else if (nd->state == ORC_ALIVE) {
         if (acc->out) acc->out[acc->count] = (int32_t)S->slot_of[node];
@@ -970,13 +984,16 @@ static void orc_touch_ranges(const orc_solver *S, const orc_node *nd, orc_ranges
     int n = S->P.n, L = nd->level;
     for (int Lp = 0; Lp <= S->max_level; Lp++) {
         for (int d = 0; d < n; d++) {
+            /* per dimension the halvings of the two depths (equal to the depths
+             * unless the bisection is cycled) */
             int64_t a, b, i = nd->idx[d];
-            if (Lp <= L) {
-                int64_t s = (int64_t)1 << (L - Lp);
+            int ld = orc_dlev(&S->P, L, d), lpd = orc_dlev(&S->P, Lp, d);
+            if (lpd <= ld) {
+                int64_t s = (int64_t)1 << (ld - lpd);
                 a = (i + s - 1) / s - 1;   /* ceil(i/s) - 1, i >= 0 */
                 b = (i + 1) / s;           /* floor((i+1)/s) */
             } else {
-                int64_t s = (int64_t)1 << (Lp - L);
+                int64_t s = (int64_t)1 << (lpd - ld);
                 a = i * s - 1;
                 b = (i + 1) * s;
             }
@@ -1060,15 +1077,16 @@ int orc_classify(orc_solver *S, uint8_t *bnd_out, int64_t *n_bnd)
     return ORC_OK;
 }
 
-/* Split every boundary cell into its 2^n children (Sec. 2.1, Sec. 3.1): the
- * union of the covering is unchanged, removed cells stay removed. */
+/* Split every boundary cell into its 2^n children (Sec. 2.1, Sec. 3.1), or into
+ * 2 with cycled bisection: the union of the covering is unchanged, removed
+ * cells stay removed. */
 int orc_subdivide(orc_solver *S, int64_t *n_split)
 {
     int64_t nb = 0;
     int rc = orc_classify(S, NULL, &nb);
     if (rc != ORC_OK) return rc;
     int n = S->P.n;
-    int64_t nc = (int64_t)1 << n;
+    int64_t nc = orc_nchild(&S->P);
     for (int64_t s = 0; s < S->n_live; s++) {
         if (!S->bnd[s]) continue;
         int64_t parent = S->live[s];
@@ -1076,7 +1094,12 @@ int orc_subdivide(orc_solver *S, int64_t *n_split)
         for (int64_t c = 0; c < nc; c++) {
             int32_t idx[ORC_MAXN];
             int L = S->nodes[parent].level;
-            for (int d = 0; d < n; d++) idx[d] = 2 * S->nodes[parent].idx[d] + (int32_t)((c >> (n - 1 - d)) & 1);
+            if (S->P.split == 1) {               /* halve dimension L mod n only */
+                for (int d = 0; d < n; d++) idx[d] = S->nodes[parent].idx[d];
+                idx[L % n] = 2 * idx[L % n] + (int32_t)c;
+            } else {
+                for (int d = 0; d < n; d++) idx[d] = 2 * S->nodes[parent].idx[d] + (int32_t)((c >> (n - 1 - d)) & 1);
+            }
             rc = orc_push_node(S, L + 1, idx, ORC_ALIVE);
             if (rc != ORC_OK) return rc;
         }

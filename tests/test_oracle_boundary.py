@@ -150,3 +150,49 @@ def test_split_rings_brute_force(orc, ring):
     assert len(set(lv.tolist())) == (1 if ring == -1 else 2)
     assert 0 < want0.sum() < mark.sum() <= kept.sum()
     assert np.array_equal(got, mark)
+
+
+@pytest.mark.parametrize("ring", [0, 1])
+def test_boundary_cycled_bisection_brute_force(orc, ring):
+    """With cycled bisection (2 children, halving dimension depth mod n) the
+    boundary rule and its rings use the same closed-touch relation: brute force
+    in integer coordinates of the finest halvings of each dimension."""
+    base = dict(W.problem(W.vdp(1.0), [-3, -3], [3, 3], 8, 3, W.controls_grid(-1, 1, 3), 0.25, 2, rule="outer",
+                          precision="fp64"), split="cycled", split_ring=ring)
+    s = orc.Solver(base)
+    for _ in range(3):
+        s.build_graph()
+        s.prune()
+        s.subdivide()
+    s.build_graph()
+    s.prune()
+    lv, idx = s.live()
+    kept = s.kept()
+    n = 2
+
+    def dlev(L):
+        return np.array([L // n + (d < L % n) for d in range(n)], np.int64)
+    nl, nst, nidx, _ = s.nodes()
+    F = np.max([dlev(int(L)) for L in nl], axis=0)
+    top = np.array(base["n0"], np.int64) << F
+
+    def box(L, i):
+        sh = F - dlev(int(L))
+        return np.asarray(i, np.int64) << sh, (np.asarray(i, np.int64) + 1) << sh
+    lo_hi = [box(lv[c], idx[c]) for c in range(len(lv))]
+    dead = [box(nl[j], nidx[j]) for j in range(len(nl)) if nst[j] == orc.DEAD]
+    dead += [lo_hi[c] for c in range(len(lv)) if not kept[c]]
+    mark = np.zeros(len(lv), bool)
+    for c in range(len(lv)):
+        if kept[c]:
+            a, b = lo_hi[c]
+            mark[c] = bool(np.any(a == 0) or np.any(b == top)) or any(_touch(a, b, x, y) for x, y in dead)
+    for _ in range(ring):
+        nxt = mark.copy()
+        for c in range(len(lv)):
+            if kept[c] and not mark[c]:
+                nxt[c] = any(mark[o] and _touch(*lo_hi[c], *lo_hi[o]) for o in range(len(lv)))
+        mark = nxt
+    got = s.classify()
+    assert len(set(lv.tolist())) >= 2 and 0 < mark.sum() <= kept.sum()
+    assert np.array_equal(got, mark)

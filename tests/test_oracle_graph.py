@@ -57,6 +57,17 @@ def test_identity_map_gives_closed_neighbourhood(orc, n, n0):
         assert list(tgt[off[i]:off[i + 1]]) == want
 
 
+def _dlev(prob, lv):
+    """Halvings per dimension of cells at depths lv: the depth itself, or with
+    cycled bisection depth // n plus one for the dimensions below depth % n."""
+    n = prob["n"]
+    lv = np.asarray(lv)[:, None]
+    if prob.get("split", "all") != "cycled":
+        return np.repeat(lv, n, axis=1)
+    d = np.arange(n)[None, :]
+    return lv // n + (d < lv % n)
+
+
 def _tree_leaves(s):
     lv, st, idx, ch = s.nodes()
     leaf = st != 2
@@ -72,7 +83,7 @@ def _bruteforce_graph(prob, s, slack=1e-12):
     lo, hi, n0 = np.array(prob["lo"]), np.array(prob["hi"]), np.array(prob["n0"])
     eps = slack * (hi - lo).max()
     llv, lst, lidx = _tree_leaves(s)
-    w = (hi - lo)[None, :] / (n0[None, :] * (2.0 ** llv[:, None]))
+    w = (hi - lo)[None, :] / (n0[None, :] * (2.0 ** _dlev(prob, llv)))
     cell_lo = lo[None, :] + lidx * w
     cell_hi = lo[None, :] + (lidx + 1) * w
     live_lv, live_idx = s.live()
@@ -149,3 +160,60 @@ def test_bbox_is_minmax_of_propagated_samples(orc):
             ys = np.array([orc.step(prob, x, ctrl[u]) for x in orc.cell_samples(prob, int(lv[slot]), idx[slot])])
             got = bbox[slot * len(ctrl) + u]
             assert list(got[:2]) == list(ys.min(0)) and list(got[2:]) == list(ys.max(0))
+
+
+@pytest.mark.parametrize("rule", ["outer", "inner"])
+def test_targets_bruteforce_cycled_bisection(orc, rule):
+    """Cycled bisection (a split halves dimension depth mod n only): after four
+    refinements the covering mixes cells of several shapes; the descent finds
+    exactly the leaves the brute force finds."""
+    prob = dict(W.problem(W.vdp(1.0), [-4, -4], [4, 4], 8, 3, W.controls_grid(-1, 1, 3), 0.25, 2, rule=rule),
+                split="cycled")
+    s = orc.Solver(prob)
+    for L in range(5):
+        s.build_graph()
+        _bruteforce_graph(prob, s)
+        s.prune()
+        if L < 4:
+            s.subdivide()
+    if rule == "outer":
+        assert s.max_level() == 4
+
+
+def test_cycled_bisection_tiles_X(orc):
+    """The leaves (alive and removed) of a cycled-bisection tree tile X: in integer
+    coordinates of the finest halvings their boxes fill the grid exactly once."""
+    prob = dict(W.problem(W.vdp(1.0), [-4, -4], [4, 4], 6, 3, W.controls_grid(-1, 1, 3), 0.25, 2, rule="outer"),
+                split="cycled")
+    s = orc.Solver(prob)
+    for _ in range(4):
+        s.build_graph()
+        s.prune()
+        s.subdivide()
+    lv, st, idx = _tree_leaves(s)
+    dl = _dlev(prob, lv)
+    F = dl.max(axis=0)
+    cover = np.zeros([6 << int(F[0]), 6 << int(F[1])], np.int32)
+    for j in range(len(lv)):
+        sh = F - dl[j]
+        a, b = idx[j] << sh, (idx[j] + 1) << sh
+        cover[a[0]:b[0], a[1]:b[1]] += 1
+    assert len(set(lv.tolist())) > 2 and np.all(cover == 1)
+
+
+def test_cycled_bisection_in_one_dimension_is_the_plain_split(orc):
+    prob = W.problem(W.linmap([[1.7]], [[1.0]]), [-1.0], [1.0], 12, 3, W.controls_grid(-0.3, 0.3, 3), 1.0, 0,
+                     rule="outer")
+    res = []
+    for split in ("all", "cycled"):
+        s = orc.Solver(dict(prob, split=split))
+        out = []
+        for L in range(4):
+            s.build_graph()
+            off, tgt, flag, _ = s.graph()
+            out.append((s.prune(), off.tolist(), tgt.tolist(), flag.tolist()))
+            if L < 3:
+                out.append(s.subdivide())
+        res.append(out)
+    assert res[0] == res[1]
+
