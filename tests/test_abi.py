@@ -57,6 +57,9 @@ def test_struct_layouts_match_header(tmp_path):
 def test_default_options(lib):
     o = gis.options()
     assert o.rule == 0 and o.precision == 1 and o.band == 0.0 and o.lanes_per_pair == 0
+    assert o.fixed_shapes == 0 and o.split_ring == 0 and o.enclosure_store == 0 and o.max_device_bytes == 0
+    p = gis.options({"rule": "outer", "split_ring": 3}, fixed_shapes=1)
+    assert p.rule == 1 and p.split_ring == 3 and p.fixed_shapes == 1
 
 
 def test_null_arguments_rejected_without_touching_a_gpu(lib):
