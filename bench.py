@@ -135,23 +135,37 @@ def aggregate_ranks(total_ms, cells, ws, device="cpu"):
     return total_ms, cells, cells / (total_ms / 1e3)
 
 
+def _oracle_solve(prob):
+    """One FP64 oracle solve: (cells built, seconds, seconds per phase)."""
+    import oracle
+    ph = {"build_graph": 0.0, "prune": 0.0, "subdivide": 0.0}
+    t0 = time.perf_counter()
+    s = oracle.Solver(prob)
+    cells = 0
+    for L in range(prob["levels"] + 1):
+        t = time.perf_counter()
+        s.build_graph()
+        ph["build_graph"] += time.perf_counter() - t
+        cells += s.num_live()
+        t = time.perf_counter()
+        s.prune()
+        ph["prune"] += time.perf_counter() - t
+        if L < prob["levels"]:
+            t = time.perf_counter()
+            s.subdivide()
+            ph["subdivide"] += time.perf_counter() - t
+    return cells, time.perf_counter() - t0, ph
+
+
 def cpu_baseline(prob, seconds_cap=30.0):
     """The oracle as it stands, all host threads, on the full workload (one solve)."""
     import oracle
     oracle.build()
     threads = oracle.set_threads(0)
-    t = time.perf_counter()
-    s = oracle.Solver(prob)
-    cells = 0
-    for L in range(prob["levels"] + 1):
-        s.build_graph()
-        cells += s.num_live()
-        s.prune()
-        if L < prob["levels"]:
-            s.subdivide()
-    dt = time.perf_counter() - t
+    cells, dt, ph = _oracle_solve(prob)
     return {"value": cells / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"one full FP64 oracle solve of the workload ({cells} cells built, {dt:.2f} s)"}, dt
+            "sample": f"one full FP64 oracle solve of the workload ({cells} cells built, {dt:.2f} s)",
+            "phases_s": ph}, dt
 
 
 def run_reference(a, prob):
@@ -161,28 +175,21 @@ def run_reference(a, prob):
     import oracle
     oracle.build()
     threads = oracle.set_threads(0)
-    times, cells = [], 0
+    times, cells, phases = [], 0, {}
     for i in range(a.warmup + a.steps):
-        t = time.perf_counter()
-        s = oracle.Solver(prob)
-        c = 0
-        for L in range(prob["levels"] + 1):
-            s.build_graph()
-            c += s.num_live()
-            s.prune()
-            if L < prob["levels"]:
-                s.subdivide()
-        dt = time.perf_counter() - t
+        c, dt, ph = _oracle_solve(prob)
         if i >= a.warmup:
             times.append(dt)
             cells = c
+            for k, v in ph.items():
+                phases[k] = phases.get(k, 0.0) + v / a.steps
     ms = 1e3 * sum(times) / len(times)
     value = cells / (ms / 1e3)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "config": _config(prob, a.workload),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": "one full FP64 oracle solve of the workload per step"},
+                             "sample": "one full FP64 oracle solve of the workload per step", "phases_s": phases},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -22,4 +22,7 @@ def test_reference_arm_json_line():
     assert d["higher_is_better"] is True and d["config"]["workload"] == "cstr_256"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
+    ph = d["cpu_baseline"]["phases_s"]
+    assert set(ph) == {"build_graph", "prune", "subdivide"} and all(v >= 0 for v in ph.values())
+    assert sum(ph.values()) <= d["ms_per_step"] / 1e3
     assert d["e2e"] == {"value": d["value"], "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
