@@ -340,10 +340,13 @@ void gis_server_destroy(gis_server *srv);
  * This is the layout gis_get_graph returns. Sizes above GIS_NOALLOC_MAX_* are
  * rejected with GIS_EUNSUPPORTED before any work is queued. The first call on
  * a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture. Every
- * call uses the same array, so calls that overlap on the GPU (from several
- * streams or threads) race and give wrong results: serialise them. The call
- * synchronises `stream` before it returns.                                   */
+ * that device current; make that first call before any stream capture. The
+ * address is cached per device and looked up again when the device's context
+ * has changed (after a cudaDeviceReset the next call is again such a first
+ * call). Every call uses the same array, so calls that overlap on the GPU
+ * (from several streams or threads) race and give wrong results: serialise
+ * them. The call synchronises `stream` twice: after validating the graph and
+ * before it returns.                                                         */
 gis_status gis_prune_graph_noalloc(int64_t n_cells, int32_t n_controls, const int64_t *off, const int32_t *tgt,
                                    const uint8_t *flag, int64_t n_edges, int32_t rule, uint8_t *kept,
                                    int64_t *n_kept, void *stream);

@@ -52,9 +52,45 @@ static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];
 
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
-void *g_dev_ptr[MAX_DEVICES] = {};
+struct ScratchSlot {
+    void *ptr;                      // device address of g_scratch in that context
+    unsigned long long ctx_id;      // the context it was looked up in
+    bool known;                     // ctx_id is meaningful
+};
+ScratchSlot g_slot[MAX_DEVICES] = {};
 
-// Device address of g_scratch on the current device (looked up once per device).
+// Unique id of the calling thread's current CUDA context, through the driver
+// entry points the runtime exposes (no link against the driver library);
+// false if there is no current context or the driver lacks cuCtxGetId.
+bool current_ctx_id(unsigned long long *id)
+{
+    typedef int (*GetCurrent)(void **);
+    typedef int (*GetId)(void *, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr, *g = nullptr;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            get_current = (GetCurrent)f;
+            get_id = (GetId)g;
+        }
+        cudaGetLastError();
+    }
+    if (!get_current || !get_id) return false;
+    void *ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx) return false;
+    return get_id(ctx, id) == 0;
+}
+
+// Device address of g_scratch on the current device. It is looked up once per
+// device with that device current, and again whenever the device's context
+// has changed since (a cudaDeviceReset loads the module anew, possibly at
+// another address), or on every call where the context cannot be identified.
 cudaError_t scratch_ptr(void **out)
 {
     int dev = 0;
@@ -62,13 +98,17 @@ cudaError_t scratch_ptr(void **out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_dev_ptr[dev]) {
+    ScratchSlot &sl = g_slot[dev];
+    unsigned long long id = 0;
+    const bool have_id = current_ctx_id(&id);
+    if (!sl.ptr || !sl.known || !have_id || sl.ctx_id != id) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess) return e;
-        g_dev_ptr[dev] = p;
+        sl.ptr = p;
+        sl.known = current_ctx_id(&sl.ctx_id);   // the lookup made the context current
     }
-    *out = g_dev_ptr[dev];
+    *out = sl.ptr;
     return cudaSuccess;
 }
 
@@ -144,13 +184,15 @@ extern "C" gis_status gis_prune_graph_noalloc(int64_t n_cells, int32_t n_control
         return fail(GIS_EINVAL, "gis_prune_graph_noalloc: negative size or no controls");
     if (rule != GIS_RULE_INNER && rule != GIS_RULE_OUTER)
         return fail(GIS_EINVAL, "gis_prune_graph_noalloc: bad rule");
-    const int64_t P = n_cells * n_controls;
-    if (n_cells > NA_MAX_CELLS || P > NA_MAX_PAIRS || n_edges > NA_MAX_EDGES) {
+    // each factor is bounded before the product is formed (no overflow)
+    const bool fits = n_cells <= NA_MAX_CELLS && n_controls <= NA_MAX_PAIRS && n_edges <= NA_MAX_EDGES;
+    const int64_t P = fits ? n_cells * n_controls : -1;
+    if (!fits || P > NA_MAX_PAIRS) {
         char b[256];
         std::snprintf(b, sizeof b,
-                      "gis_prune_graph_noalloc: %lld cells / %lld pairs / %lld edges exceed the fixed scratch "
-                      "(at most %lld / %lld / %lld)", (long long)n_cells, (long long)P, (long long)n_edges,
-                      (long long)NA_MAX_CELLS, (long long)NA_MAX_PAIRS, (long long)NA_MAX_EDGES);
+                      "gis_prune_graph_noalloc: %lld cells x %lld controls / %lld edges exceed the fixed scratch "
+                      "(at most %lld cells, %lld pairs, %lld edges)", (long long)n_cells, (long long)n_controls,
+                      (long long)n_edges, (long long)NA_MAX_CELLS, (long long)NA_MAX_PAIRS, (long long)NA_MAX_EDGES);
         return fail(GIS_EUNSUPPORTED, b);
     }
     if (n_cells > 0 && (!off || !flag || !kept || (n_edges > 0 && !tgt)))

@@ -3,14 +3,16 @@
 Some callers cannot allocate device memory (a fixed memory arena, an
 allocator that owns the device, paths that must not synchronise). This entry
 point prunes a graph they pass in, with its scratch in a fixed array of the
-library. Checked through the C ABI against gis_prune on the same graphs, on
-several calls in a row (the shared scratch keeps the previous call's
-contents), and for the size limit."""
+library. Checked through the C ABI against gis_prune and against the oracle's
+greatest fixed point (Sec. 2.3) on the same graphs, on several calls in a row
+(the shared scratch keeps the previous call's contents), and for the size
+limits."""
 import ctypes as C
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2202_06111_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -64,6 +66,9 @@ def test_noalloc_prune_matches_gis_prune(lib):
         assert rc == gis.OK, gis.load().gis_last_error(None)
         assert np.array_equal(kept, kept_ref)
         assert nk == int(kept_ref.sum())
+        # the oracle's fixed point on the same CSR
+        want = oracle.prune_graph(n_cells, nu, off, tgt, flag, rule=rule)
+        assert np.array_equal(kept.astype(bool), want)
 
 
 def test_noalloc_rejects_oversize_and_bad_graphs(lib):
@@ -73,6 +78,11 @@ def test_noalloc_rejects_oversize_and_bad_graphs(lib):
     rc = L.gis_prune_graph_noalloc(big, 1, None, None, None, 0, 0, None, None, None)
     assert rc == gis.EUNSUPPORTED
     assert b"exceed" in L.gis_last_error(None)
+    # factors whose product would overflow int64 are rejected, not multiplied
+    rc = L.gis_prune_graph_noalloc((1 << 62) - 1, 4, None, None, None, 0, 0, None, None, None)
+    assert rc == gis.EUNSUPPORTED
+    rc = L.gis_prune_graph_noalloc(2, (1 << 31) - 1, None, None, None, 0, 0, None, None, None)
+    assert rc == gis.EUNSUPPORTED
     off = np.array([0, 1, 2], np.int64)
     tgt = np.array([0, 5], np.int32)                 # 5 is not a cell of a 2-cell graph
     flag = np.array([1, 1], np.uint8)
