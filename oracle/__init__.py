@@ -93,6 +93,7 @@ def lib():
         L.orc_range.argtypes = [C.POINTER(_Problem), i32, i32, C.c_double, C.c_double, vp]
         L.orc_prune_graph.argtypes = [i64, i32, vp, vp, vp, i32, vp, C.POINTER(i64)]
         L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_build_slice.argtypes = [vp, i64, i64, C.POINTER(i64)]
         _lib = L
     return _lib
 
@@ -207,6 +208,14 @@ class Solver:
 
     def build_graph(self):
         _check(lib().orc_build_graph(self._h))
+
+    def build_slice(self, first: int, count: int) -> int:
+        """Graph construction of live cells [first, first + count) of the
+        current covering, discarded afterwards (a bounded timing sample);
+        returns its edge count. The solver keeps no graph."""
+        ne = C.c_int64(0)
+        _check(lib().orc_build_slice(self._h, first, count, C.byref(ne)))
+        return ne.value
 
     def prune(self) -> int:
         nk = C.c_int64(0)

@@ -94,6 +94,7 @@ typedef struct {
     uint8_t *kept;      /* per slot, after prune */
     uint8_t *bnd;       /* per slot, after classify: the cells to split */
     int32_t ring;       /* split rings around the boundary cells (-1: every kept cell) */
+    int32_t numbered;   /* live / slot_of number the current covering */
 } orc_solver;
 
 static int orc_threads = 1;
@@ -605,6 +606,7 @@ static void orc_free_graph(orc_solver *S)
     free(S->bnd); S->bnd = NULL;
     S->n_live = 0;
     S->have_graph = S->have_prune = 0;
+    S->numbered = 0;
 }
 
 /* ------------------------------------------------------------------------
@@ -692,11 +694,12 @@ static void orc_pair_ranges(const orc_solver *S, const double *ymin, const doubl
 
 /* Symbolic image of the current covering (Def. 1): per (live cell, control)
  * the image box, the in-X flag, and every live leaf meeting the box. */
-int orc_build_graph(orc_solver *S)
+/* The current covering: every live leaf, in canonical order (level, then idx
+ * lexicographic), numbered by its slot. */
+static int orc_number_live(orc_solver *S)
 {
-    if (!S) return ORC_EINVAL;
     orc_free_graph(S);
-    int n = S->P.n, nu = S->n_u;
+    int n = S->P.n;
     int64_t nl = 0;
     for (int64_t i = 0; i < S->n_nodes; i++) nl += S->nodes[i].state == ORC_ALIVE;
     S->live = (int64_t *)malloc((size_t)(nl ? nl : 1) * sizeof(int64_t));
@@ -711,6 +714,17 @@ int orc_build_graph(orc_solver *S)
     for (int64_t i = 0; i < S->n_nodes; i++) S->slot_of[i] = -1;
     for (int64_t s = 0; s < nl; s++) S->slot_of[S->live[s]] = s;
     S->n_live = nl;
+    S->numbered = 1;
+    return ORC_OK;
+}
+
+int orc_build_graph(orc_solver *S)
+{
+    if (!S) return ORC_EINVAL;
+    int rc = orc_number_live(S);
+    if (rc != ORC_OK) return rc;
+    int n = S->P.n, nu = S->n_u;
+    int64_t nl = S->n_live;
 
     int64_t P = nl * nu;
     S->off = (int64_t *)calloc((size_t)P + 1, sizeof(int64_t));
@@ -762,6 +776,72 @@ int orc_build_graph(orc_solver *S)
         qsort(S->tgt + S->off[p], (size_t)acc.count, sizeof(int32_t), orc_cmp_i32);
     }
     S->have_graph = 1;
+    return ORC_OK;
+}
+
+/* Graph construction of a contiguous slice of the covering, for timing a
+ * bounded sample of a workload: the same two passes as orc_build_graph (image
+ * box, flags and target count of every pair, then the sorted targets) over
+ * the pairs of live cells [first, first + count), into buffers freed before
+ * returning. The solver keeps no graph afterwards. *n_edges: the slice's
+ * edges. */
+int orc_build_slice(orc_solver *S, int64_t first, int64_t count, int64_t *n_edges)
+{
+    if (!S || first < 0 || count < 0) return ORC_EINVAL;
+    if (!S->numbered || !S->live) {
+        int rc = orc_number_live(S);
+        if (rc != ORC_OK) return rc;
+    }
+    int n = S->P.n, nu = S->n_u;
+    if (first > S->n_live) first = S->n_live;
+    if (count > S->n_live - first) count = S->n_live - first;
+    int64_t P = count * nu, p0 = first * nu;
+    double *bbox = (double *)malloc((size_t)(P ? P : 1) * 2 * n * sizeof(double));
+    uint8_t *flag = (uint8_t *)calloc((size_t)(P ? P : 1), 1);
+    int64_t *off = (int64_t *)calloc((size_t)P + 1, sizeof(int64_t));
+    if (!bbox || !flag || !off) { free(bbox); free(flag); free(off); return ORC_ENOMEM; }
+    #pragma omp parallel for schedule(dynamic, 64) num_threads(orc_threads)
+    for (int64_t q = 0; q < P; q++) {
+        int64_t p = p0 + q;
+        const orc_node *nd = &S->nodes[S->live[p / nu]];
+        const double *u = S->u + (p % nu) * S->P.m;
+        double *ymin = bbox + q * 2 * n, *ymax = ymin + n;
+        int nonfinite = orc_image_bbox(&S->P, nd->level, nd->idx, u, ymin, ymax);
+        uint8_t f = 0;
+        int64_t c = 0;
+        if (nonfinite) {
+            f = ORC_F_NONFINITE;
+        } else {
+            int inx = 1;
+            for (int d = 0; d < n; d++)
+                if (!(ymin[d] >= S->P.lo[d] && ymax[d] <= S->P.hi[d])) inx = 0;
+            if (inx) f |= ORC_F_INX;
+            orc_ranges R;
+            orc_pair_ranges(S, ymin, ymax, &R);
+            orc_acc acc = {NULL, 0, 0};
+            orc_descend(S, &R, &acc);
+            if (acc.touch_dead) f |= ORC_F_TOUCH_DEAD;
+            c = acc.count;
+        }
+        flag[q] = f;
+        off[q + 1] = c;
+    }
+    for (int64_t q = 0; q < P; q++) off[q + 1] += off[q];
+    int64_t E = off[P];
+    int32_t *tgt = (int32_t *)malloc((size_t)(E ? E : 1) * sizeof(int32_t));
+    if (!tgt) { free(bbox); free(flag); free(off); return ORC_ENOMEM; }
+    #pragma omp parallel for schedule(dynamic, 64) num_threads(orc_threads)
+    for (int64_t q = 0; q < P; q++) {
+        if (flag[q] & ORC_F_NONFINITE) continue;
+        const double *ymin = bbox + q * 2 * n, *ymax = ymin + n;
+        orc_ranges R;
+        orc_pair_ranges(S, ymin, ymax, &R);
+        orc_acc acc = {tgt + off[q], 0, 0};
+        orc_descend(S, &R, &acc);
+        qsort(tgt + off[q], (size_t)acc.count, sizeof(int32_t), orc_cmp_i32);
+    }
+    if (n_edges) *n_edges = E;
+    free(bbox); free(flag); free(off); free(tgt);
     return ORC_OK;
 }
 
@@ -1063,6 +1143,7 @@ int orc_classify(orc_solver *S, uint8_t *bnd_out, int64_t *n_bnd)
     if (!S || !S->have_prune) return ORC_ESTATE;
     for (int64_t s = 0; s < S->n_live; s++)
         if (!S->kept[s]) S->nodes[S->live[s]].state = ORC_DEAD;
+    S->numbered = 0;                     /* the removed cells leave the covering */
     free(S->bnd);
     S->bnd = (uint8_t *)calloc((size_t)(S->n_live ? S->n_live : 1), 1);
     if (!S->bnd) return ORC_ENOMEM;
@@ -1108,6 +1189,7 @@ int orc_subdivide(orc_solver *S, int64_t *n_split)
     }
     if (n_split) *n_split = nb;
     S->have_graph = S->have_prune = 0;
+    S->numbered = 0;
     return ORC_OK;
 }
 

@@ -170,3 +170,17 @@ def test_paper_cstr_eq4(gis):
     """The dimensional CSTR of Eq. 4 / Table 2 on X = [0,1] x [345,355] (FP64:
     near 350 K an FP32 state carries only 3e-5 K, amplified by the reaction)."""
     run_both(gis, dict(W.cstr_paper_problem(n0=(24, 24)), rule="outer", precision="fp64"), 2)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("rule", ["inner", "outer"])
+def test_nonfinite_images(gis, precision, rule):
+    """Non-finite sample images (x+ = 1e308 x overflows; a control that
+    overflows beside one that does not): such pairs leave X with no target on
+    both sides, even where a finite sample lands inside X."""
+    one = W.problem(W.linmap([[1e308]], [[0.0]]), [-4.0], [4.0], 4, 2, [[0.0]], 1.0, 0, rule=rule,
+                    precision=precision)
+    assert run_both(gis, one, 1)[0][0] == 0
+    two = W.problem(W.linmap([[0.5]], [[1e308]]), [-1.0], [1.0], 8, 2, [[0.0], [2.0]], 1.0, 0, rule=rule,
+                    precision=precision)
+    assert run_both(gis, two, 1)[0][0] == 8

@@ -217,3 +217,68 @@ def test_cycled_bisection_in_one_dimension_is_the_plain_split(orc):
         res.append(out)
     assert res[0] == res[1]
 
+
+
+def _overflow_map(rule):
+    """x+ = 1e308 x on X = [-4, 4], four cells, corner samples: the corner at
+    x = 0 maps to 0, every other corner overflows to +-inf. The cells [-2, 0]
+    and [0, 2] therefore have one finite image, 0, inside X."""
+    dyn = W.linmap([[1e308]], [[0.0]])
+    return dict(W.problem(dyn, [-4.0], [4.0], 4, 2, [[0.0]], 1.0, 0), rule=rule)
+
+
+@pytest.mark.parametrize("rule", ["inner", "outer"])
+def test_nonfinite_image_leaves_x(orc, rule):
+    """Reading 8 (the paper defines no image for a sample whose image is not a
+    number): a pair with a non-finite sample image leaves X and has no target,
+    even where its finite samples land inside X. Mistakes this catches: a box
+    and targets taken from the finite samples only (cells [-2, 0] and [0, 2]
+    would meet the cells around 0 and stay in X), an infinite extreme let
+    through the in-X test, a removed-leaf flag set on such a pair."""
+    s = orc.Solver(_overflow_map(rule))
+    s.build_graph()
+    off, tgt, flag, _ = s.graph()
+    assert len(flag) == 4
+    assert np.all(flag == orc.F_NONFINITE)
+    assert np.all(np.diff(off) == 0) and len(tgt) == 0
+    # the finite sample of the two middle cells is still the image of x = 0
+    lo, hi, nf = orc.pair_bbox(_overflow_map(rule), 0, [1], [0.0])
+    assert nf and lo[0] == 0.0 and hi[0] == 0.0
+    assert s.prune() == 0
+    assert not s.kept().any()
+
+
+def test_nonfinite_control_drops_only_its_pairs(orc):
+    """Two controls on a contraction: u = 0 keeps x+ = x / 2 inside X, u = 2
+    overflows (1e308 * 2 = inf). Only the u = 2 pairs are non-finite and
+    target-free, and both rules keep every cell through u = 0."""
+    dyn = W.linmap([[0.5]], [[1e308]])
+    for rule in ("inner", "outer"):
+        p = dict(W.problem(dyn, [-1.0], [1.0], 8, 2, [[0.0], [2.0]], 1.0, 0), rule=rule)
+        s = orc.Solver(p)
+        s.build_graph()
+        off, tgt, flag, _ = s.graph()
+        cnt = np.diff(off)
+        assert np.all(flag[1::2] == orc.F_NONFINITE) and np.all(cnt[1::2] == 0)
+        assert np.all(flag[0::2] == orc.F_INX) and np.all(cnt[0::2] >= 1)
+        assert s.prune() == 8
+
+
+def test_build_slice_counts_the_slice_edges(orc):
+    """The timing slice builds the same pairs as the full graph: its edge count
+    equals the full graph's edges of those cells, at level 0 and after a
+    refinement."""
+    p = dict(W.cstr_256(levels=1, n0=12), rule="outer")
+    s = orc.Solver(p)
+    nu = len(p["controls"])
+    for L in range(2):
+        s.build_graph()
+        off, _, _, _ = s.graph()
+        nl = s.num_live()
+        for first, count in ((0, nl), (5, 17), (nl - 3, 10)):
+            end = min(nl, first + count)
+            assert s.build_slice(first, count) == off[end * nu] - off[first * nu]
+        s.build_graph()
+        s.prune()
+        if L == 0:
+            s.subdivide()
