@@ -94,6 +94,9 @@ def lib():
         L.orc_prune_graph.argtypes = [i64, i32, vp, vp, vp, i32, vp, C.POINTER(i64)]
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_build_slice.argtypes = [vp, i64, i64, C.POINTER(i64)]
+        L.orc_own_exp.restype = C.c_double
+        L.orc_own_exp.argtypes = [C.c_double]
+        L.orc_own_sincos.argtypes = [C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         _lib = L
     return _lib
 
@@ -164,6 +167,18 @@ def pair_bbox(prob, level, idx, u):
     lo, hi = np.zeros(MAXN), np.zeros(MAXN)
     nf = lib().orc_pair_bbox(C.byref(_struct(prob)), level, _ptr(idx), _ptr(u), _ptr(lo), _ptr(hi))
     return lo[:n], hi[:n], bool(nf)
+
+
+def own_exp(x: float) -> float:
+    """The interval mode's own e^x (range reduction + Taylor)."""
+    return lib().orc_own_exp(float(x))
+
+
+def own_sincos(x: float):
+    """The interval mode's own (sin x, cos x); None beyond |x| = 65536."""
+    s, c = C.c_double(), C.c_double()
+    ok = lib().orc_own_sincos(float(x), C.byref(s), C.byref(c))
+    return (s.value, c.value) if ok else None
 
 
 def level_range(prob, level, d, ymin, ymax):

@@ -298,10 +298,81 @@ static int orc_image_bbox(const orc_problem *P, int L, const int32_t *idx, const
  * exact image of every point of the cell (the sampled box of Sec. 2.4 holds
  * only the images of the samples). Each result of +, -, *, / is rounded to
  * nearest (within half an ulp) and then moved one ulp outward. exp, sin and
- * cos come from the C library, read as within 1 ulp: two ulps outward. The
- * natural extension over-approximates (each occurrence of a variable ranges
- * independently), which costs width, not rigour.
+ * cos are the routines below (a fixed sequence of round-to-nearest
+ * operations, so that any implementation of the same sequence gives the same
+ * bits), widened by more than their proven error and then one ulp outward.
+ * The natural extension over-approximates (each occurrence of a variable
+ * ranges independently), which costs width, not rigour.
  * ---------------------------------------------------------------------- */
+
+/* exp, sin and cos of the interval mode: Cody & Waite's additive range
+ * reduction (W. J. Cody, W. Waite, "Software Manual for the Elementary
+ * Functions", 1980) with a constant split so that k times its leading part is
+ * exact, then the Taylor series of the reduced argument by Horner's rule.
+ * Constants: ln 2 = LN2_HI + LN2_LO with LN2_HI = ln 2 to 32 significant bits
+ * (k LN2_HI exact for |k| < 2^21); pi/2 = PIO2_1 + PIO2_2 + PIO2_3 with the
+ * first two to 33 significant bits (k PIO2_i exact for |k| < 2^20); 1/i!
+ * rounded to nearest.
+ * Error bounds (u = 2^-53). exp, x in [-700, 709]: |r| <= 0.347; truncation
+ * after r^17 below 2^-78; Horner's 2 x 17 roundings at most 34 u e^|r| / e^r
+ * < 2^-47 relative; the reduction's three roundings below 2^-52 absolute in
+ * r, so 2^-52 relative in e^r; 2^k scales exactly (no subnormal results).
+ * Total below 2^-46 relative: widened by 2^-40 of the value. sin / cos,
+ * |x| <= 65536 (|k| < 2^16): the reduction errs by at most 3 u |r| + |k| 2^-106
+ * < 2^-52 absolute (|r| <= 0.786), sin and cos are 1-Lipschitz; the series in
+ * r^2 to degree 25 / 24 truncate below 2^-90, and their 2 x 13 roundings are
+ * below 27 u cosh(0.786) < 2^-47 absolute. Total below 2^-46 absolute:
+ * widened by 2^-40. */
+static const double ORC_INV_LN2 = 0x1.71547652b82fep+0;
+static const double ORC_LN2_HI = 0x1.62e42ff000000p-1;
+static const double ORC_LN2_LO = -0x1.718432a1b0e26p-35;
+static const double ORC_TWO_OVER_PI = 0x1.45f306dc9c883p-1;
+static const double ORC_PIO2_1 = 0x1.921fb54400000p+0;
+static const double ORC_PIO2_2 = 0x1.0b4611a600000p-34;
+static const double ORC_PIO2_3 = 0x1.3198a2e037073p-69;
+static const double ORC_INV_FACT[26] = {
+    0x1.0000000000000p+0, 0x1.0000000000000p+0, 0x1.0000000000000p-1, 0x1.5555555555555p-3,
+    0x1.5555555555555p-5, 0x1.1111111111111p-7, 0x1.6c16c16c16c17p-10, 0x1.a01a01a01a01ap-13,
+    0x1.a01a01a01a01ap-16, 0x1.71de3a556c734p-19, 0x1.27e4fb7789f5cp-22, 0x1.ae64567f544e4p-26,
+    0x1.1eed8eff8d898p-29, 0x1.6124613a86d09p-33, 0x1.93974a8c07c9dp-37, 0x1.ae7f3e733b81fp-41,
+    0x1.ae7f3e733b81fp-45, 0x1.952c77030ad4ap-49, 0x1.6827863b97d97p-53, 0x1.2f49b46814157p-57,
+    0x1.e542ba4020225p-62, 0x1.71b8ef6dcf572p-66, 0x1.0ce396db7f853p-70, 0x1.761b41316381ap-75,
+    0x1.f2cf01972f578p-80, 0x1.3f3ccdd165fa9p-84};
+
+/* e^x for x in [-700, 709]; +inf above, 0 below, NaN for NaN */
+double orc_own_exp(double x)
+{
+    if (isnan(x)) return x;
+    if (x > 709.0) return INFINITY;
+    if (x < -700.0) return 0.0;
+    double k = rint(x * ORC_INV_LN2);
+    double r = (x - k * ORC_LN2_HI) - k * ORC_LN2_LO;
+    double p = ORC_INV_FACT[17];
+    for (int i = 16; i >= 0; i--) p = p * r + ORC_INV_FACT[i];
+    return ldexp(p, (int)k);
+}
+
+/* sin x and cos x for |x| <= 65536; returns 0 (and leaves s, c) otherwise */
+int orc_own_sincos(double x, double *s, double *c)
+{
+    if (!(fabs(x) <= 65536.0)) return 0;
+    double k = rint(x * ORC_TWO_OVER_PI);
+    double r = ((x - k * ORC_PIO2_1) - k * ORC_PIO2_2) - k * ORC_PIO2_3;
+    double z = r * r;
+    double ps = ORC_INV_FACT[25], pc = ORC_INV_FACT[24];   /* sign (-1)^12 = +1 */
+    for (int j = 11; j >= 0; j--) {
+        double sg = (j & 1) ? -1.0 : 1.0;
+        ps = ps * z + sg * ORC_INV_FACT[2 * j + 1];
+        pc = pc * z + sg * ORC_INV_FACT[2 * j];
+    }
+    double sr = r * ps, cr = pc;
+    int q = (int)(((long long)k % 4 + 4) % 4);
+    double sv = q == 0 ? sr : q == 1 ? cr : q == 2 ? -sr : -cr;
+    double cv = q == 0 ? cr : q == 1 ? -sr : q == 2 ? -cr : sr;
+    *s = sv;
+    *c = cv;
+    return 1;
+}
 typedef struct {
     double lo, hi;
 } orc_iv;
@@ -341,9 +412,25 @@ static orc_iv iv_div(orc_iv a, orc_iv b)
     orc_iv rb = {orc_dn(1.0 / b.hi), orc_up(1.0 / b.lo)};
     return iv_mul(a, rb);
 }
+/* exp is increasing: [exp(lo), exp(hi)], each end widened by 2^-40 of
+ * itself; below -700 the lower end is 0 and the upper 2^-1009 > e^-700 */
+static double orc_exp_dn(double x)
+{
+    if (x < -700.0) return 0.0;
+    double v = orc_own_exp(x);
+    if (!(v < INFINITY)) return v;
+    return orc_dn(v - v * 0x1p-40);
+}
+static double orc_exp_up(double x)
+{
+    if (x < -700.0) return 0x1p-1009;
+    double v = orc_own_exp(x);
+    if (!(v < INFINITY)) return v;
+    return orc_up(v + v * 0x1p-40);
+}
 static orc_iv iv_exp(orc_iv a)
 {
-    orc_iv r = {orc_dn(orc_dn(exp(a.lo))), orc_up(orc_up(exp(a.hi)))};
+    orc_iv r = {orc_exp_dn(a.lo), orc_exp_up(a.hi)};
     if (r.lo < 0.0) r.lo = 0.0;
     return r;
 }
@@ -360,10 +447,12 @@ static orc_iv iv_sin_shift(orc_iv a, int cosine)
 {
     orc_iv r = {-1.0, 1.0};
     if (!(a.hi - a.lo < 6.0) || !isfinite(a.lo) || !isfinite(a.hi)) return r;
-    double f0 = cosine ? cos(a.lo) : sin(a.lo), f1 = cosine ? cos(a.hi) : sin(a.hi);
+    double s0, c0, s1, c1;
+    if (!orc_own_sincos(a.lo, &s0, &c0) || !orc_own_sincos(a.hi, &s1, &c1)) return r;
+    double f0 = cosine ? c0 : s0, f1 = cosine ? c1 : s1;
     double lo = f0 < f1 ? f0 : f1, hi = f0 < f1 ? f1 : f0;
-    lo = orc_dn(orc_dn(lo));
-    hi = orc_up(orc_up(hi));
+    lo = orc_dn(lo - 0x1p-40);
+    hi = orc_up(hi + 0x1p-40);
     const double halfpi = 1.5707963267948966;
     double pmax = cosine ? 0.0 : halfpi, pmin = cosine ? 2.0 * halfpi : -halfpi;
     if (orc_holds_phase(a.lo, a.hi, pmax)) hi = 1.0;

@@ -85,3 +85,40 @@ def test_interval_graph_contains_the_sampled_graph(orc):
         assert a <= b
         grew += len(b) > len(a)
     assert grew > 0
+
+
+def test_own_exp_error_bound(orc):
+    """The interval mode's e^x (range reduction + Taylor) is within 2^-46 of
+    e^x relative (its proven bound; the enclosure widens by 2^-40) over the
+    whole domain, at the reduction's switch points and at exact values."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.prec = 120
+    rng = np.random.default_rng(11)
+    xs = list(rng.uniform(-700.0, 709.0, 3000)) + list(rng.uniform(-2.0, 2.0, 2000))
+    xs += [(k + 0.5) * 0.6931471805599453 for k in range(-1000, 1020, 7)] + [0.0, 1.0, -1.0, 709.0, -700.0]
+    worst = 0.0
+    for x in xs:
+        v = orc.own_exp(x)
+        ex = mp.exp(mp.mpf(x))
+        worst = max(worst, float(abs((mp.mpf(v) - ex) / ex)))
+    assert worst < 2.0 ** -46
+    assert orc.own_exp(0.0) == 1.0
+    assert orc.own_exp(710.0) == float("inf") and orc.own_exp(-701.0) == 0.0
+
+
+def test_own_sincos_error_bound(orc):
+    """sin / cos of the interval mode: within 2^-46 absolute for |x| <= 65536,
+    quadrants and signs included (near multiples of pi/2 and far out), and
+    refused beyond."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.prec = 160
+    rng = np.random.default_rng(12)
+    xs = list(rng.uniform(-4.0, 4.0, 2000)) + list(rng.uniform(-65536.0, 65536.0, 2000))
+    xs += [k * 1.5707963267948966 + d for k in range(-40, 41) for d in (-1e-9, 0.0, 1e-9)]
+    worst = 0.0
+    for x in xs:
+        s, c = orc.own_sincos(x)
+        worst = max(worst, float(abs(mp.mpf(s) - mp.sin(mp.mpf(x)))), float(abs(mp.mpf(c) - mp.cos(mp.mpf(x)))))
+    assert worst < 2.0 ** -46
+    assert orc.own_sincos(0.0) == (0.0, 1.0)
+    assert orc.own_sincos(65537.0) is None and orc.own_sincos(float("nan")) is None
