@@ -64,3 +64,13 @@ def first_edge_diff(gpu_graph, orc_graph, perm, nu):
 def kept_keys(level, idx):
     k = keys(level, idx)
     return set(map(tuple, k.tolist()))
+
+
+def digest(level, idx):
+    """Count and SHA-256 of a cell set: rows (level, idx_0..idx_{n-1}) as
+    little-endian int32, sorted lexicographically (the form of the stored
+    oracle digests in tests/golden/kept_digests.json)."""
+    import hashlib
+    rows = keys(level, idx)
+    rows = rows[np.lexsort(rows.T[::-1])] if len(rows) else rows
+    return {"count": int(len(rows)), "sha256": hashlib.sha256(rows.astype("<i4").tobytes()).hexdigest()}
