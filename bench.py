@@ -1,17 +1,21 @@
 """Benchmark of the GIS hot path on GB300.
 
-One step = one whole solve of the dimensionless-CSTR workload (256^2 root
-cells, 4x4 samples, 11 controls, RK4 4 x 0.0125, three levels of boundary
-subdivision, FP32 propagation with FP64 recheck): leaf materialisation,
-propagation, image boxes, recheck, count / scan / fill, transpose, prune,
-boundary classification and subdivision, through the C ABI of libgis.
+One step = one whole solve of the 4-D cart-pole workload (48^4 root cells,
+2^4 corner samples, 9 forces, one RK4 step of 0.02, two levels of boundary
+subdivision, OUTER rule, FP32 propagation with the certified recheck tiers):
+leaf materialisation, propagation, image boxes, recheck, count / scan / fill,
+transpose, prune, boundary classification and subdivision, through the C ABI
+of libgis. `--workload cstr_256` runs the dimensionless-CSTR workload (256^2
+roots, 3 levels); batch_512, serving_2000 and cstr_paper_rings have runners
+of their own.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gis|reference]
+                  [--workload cartpole_48|cstr_256|vdp_64|batch_512|serving_2000|cstr_paper_rings]
 
 Prints one JSON line (rank 0). The metric is graph-construction throughput:
 live cells whose graph was built, summed over the levels of the solve, per
-second of solve time. --impl reference times the FP64 CPU oracle on the same
-workload and metric on the host cores.
+second of solve time. --impl reference times the FP64 CPU oracle on the host
+cores on a bounded sample of the same workload and metric.
 """
 from __future__ import annotations
 
@@ -31,6 +35,46 @@ METRIC = "graph-construction cells/s"
 UNIT = "cells/s"
 FP32_LANES_PER_SM = 128
 
+# Plain operations of one evaluation of each model's right-hand side g(x, u),
+# counted from its defining expression: (add / sub / mul with an FMA as 2, a
+# division by a parameter counted as the product with its reciprocal;
+# divisions by a state-dependent value; exp / sin / cos). The last two go to
+# the special-function units and are reported beside the FLOPs, not in them.
+RHS_OPS = {"vdp": (6, 0, 0), "cstr_dl": (11, 1, 1), "cartpole": (17, 1, 2), "cstr_paper": (12, 1, 1)}
+RK4_OPS_PER_DIM = 13   # three stage states (2 each) and the weighted update (7)
+
+
+def pair_work(prob):
+    """Algorithmic work of one (cell, control) pair of propagation and bbox:
+    S s (4 f_g + 13 n) FLOPs plus 2 n (S - 1) compares (one map application
+    instead of s RK4 substeps for a discrete map), and its SFU operations."""
+    n, k, s = prob["n"], prob["k"], prob["substeps"]
+    S = k ** n
+    if prob["dyn"] == "linmap":
+        f_g, div, tr = 2 * n * (n + prob.get("m", 1)), 0, 0
+    else:
+        f_g, div, tr = RHS_OPS[prob["dyn"]]
+    if s == 0:
+        flops, sfu = S * f_g, S * (div + tr)
+    else:
+        flops, sfu = S * s * (4 * f_g + RK4_OPS_PER_DIM * n), S * s * 4 * (div + tr)
+    return flops + 2 * n * (S - 1), sfu
+
+
+def graph_bytes(prob, pairs, pair_edges, builds):
+    """Algorithmic bytes of edge construction: the targets (4 per
+    (cell, control) edge), the pair offsets (8 per pair and build), the image
+    box re-read by the fill (8n per pair) and the count pass's count and flag
+    (5 per pair)."""
+    n = prob["n"]
+    return 4.0 * pair_edges + 8.0 * (pairs + builds) + 8.0 * n * pairs + 5.0 * pairs
+
+
+# DRAM traffic of the graph phase's kernels (count, scans, place / fill, the
+# carried cells' edges) per (cell, control) edge, from one ncu capture of a
+# smaller case of the same workload; None where the kernels changed since.
+GRAPH_TRAFFIC = {}
+
 
 def _args():
     ap = argparse.ArgumentParser()
@@ -38,7 +82,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gis", choices=["gis", "reference"])
-    ap.add_argument("--workload", default="cstr_256")
+    ap.add_argument("--workload", default="cartpole_48")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -157,47 +201,159 @@ def _oracle_solve(prob):
     return cells, time.perf_counter() - t0, ph
 
 
-def cpu_baseline(prob, seconds_cap=30.0):
-    """The oracle as it stands, all host threads, on the full workload (one solve)."""
-    import oracle
-    oracle.build()
-    threads = oracle.set_threads(0)
-    cells, dt, ph = _oracle_solve(prob)
-    return {"value": cells / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"one full FP64 oracle solve of the workload ({cells} cells built, {dt:.2f} s)",
-            "phases_s": ph}, dt
+# Workloads whose whole oracle solve is too large for a bounded sample (the
+# 48^4 cart-pole's level-2 graph alone would need over 100 GB of host memory
+# in the oracle's per-pair layout): the sample is the oracle's graph
+# construction of a run of the level-0 cells instead, `SLICE_CELLS` a step.
+SLICE_CELLS = {"cartpole_48": 400_000}
+
+
+class OracleSampler:
+    """Bounded samples of the oracle's graph construction on a workload: a
+    whole solve where one is short, else consecutive runs of level-0 cells."""
+
+    def __init__(self, prob, name):
+        import oracle
+        oracle.build()
+        self.threads = oracle.set_threads(0)
+        self.prob, self.slice = prob, SLICE_CELLS.get(name)
+        self.solver, self.next = None, 0
+        if self.slice:
+            self.solver = oracle.Solver(prob)
+            t = time.perf_counter()
+            self.solver.build_slice(0, 0)          # numbers the level-0 covering once
+            self.setup_s = time.perf_counter() - t
+            self.n_cells = self.solver.num_live()
+
+    def describe(self):
+        if self.slice:
+            return (f"FP64 oracle graph construction (image boxes, flags, edges) of {self.slice} consecutive "
+                    f"level-0 cells of the {self.n_cells} per step, on {self.threads} host threads; "
+                    f"the whole solve does not fit the sample (nor host memory at level 2)")
+        return f"one full FP64 oracle solve of the workload per step, on {self.threads} host threads"
+
+    def step(self):
+        """(cells, seconds, per-phase seconds) of one sample."""
+        if not self.slice:
+            return _oracle_solve(self.prob)
+        first = self.next
+        if first >= self.n_cells:
+            first = 0
+        count = min(self.slice, self.n_cells - first)
+        t = time.perf_counter()
+        self.solver.build_slice(first, count)
+        dt = time.perf_counter() - t
+        self.next = first + count
+        return count, dt, {"build_graph": dt}
+
+
+def cpu_baseline(prob, name, target_s=15.0):
+    """The oracle as it stands on all host threads, on a bounded sample of the
+    workload (about target_s seconds)."""
+    smp = OracleSampler(prob, name)
+    cells, secs, phases = 0, 0.0, {}
+    while True:
+        c, dt, ph = smp.step()
+        cells += c
+        secs += dt
+        for k, v in ph.items():
+            phases[k] = phases.get(k, 0.0) + v
+        if secs >= target_s or not smp.slice:
+            break
+    return {"value": cells / secs, "unit": UNIT, "cores": smp.threads, "kind": "oracle",
+            "sample": f"{smp.describe()}; {cells} cells in {secs:.1f} s", "phases_s": phases}
 
 
 def run_reference(a, prob):
     ws, rank, local = _dist()
     if rank != 0:
         return
-    import oracle
-    oracle.build()
-    threads = oracle.set_threads(0)
+    smp = OracleSampler(prob, a.workload)
     times, cells, phases = [], 0, {}
     for i in range(a.warmup + a.steps):
-        c, dt, ph = _oracle_solve(prob)
+        c, dt, ph = smp.step()
         if i >= a.warmup:
             times.append(dt)
-            cells = c
+            cells += c
             for k, v in ph.items():
                 phases[k] = phases.get(k, 0.0) + v / a.steps
     ms = 1e3 * sum(times) / len(times)
-    value = cells / (ms / 1e3)
+    value = cells / sum(times)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "config": _config(prob, a.workload),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": "one full FP64 oracle solve of the workload per step", "phases_s": phases},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": smp.threads, "kind": "oracle",
+                             "sample": smp.describe(), "phases_s": phases},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _kept_key_set(ctx):
+    import numpy as np
+    lv, idx = ctx.kept_cells()
+    rows = np.concatenate([lv[:, None].astype(np.int64), idx.astype(np.int64)], axis=1)
+    return rows[np.lexsort(rows.T[::-1])] if len(rows) else rows
+
+
+def _roofline(prob, name, agg, steps, peaks, src, sms):
+    """Per-phase achieved work against the peaks, from the library's CUDA-event
+    phase times: propagation in algorithmic FLOPs (pair_work), edge
+    construction and pruning in algorithmic bytes. The dominant phase (most
+    time) is the headline."""
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    hbm = float(peaks["hbm_gbs"])
+    flops_pp, sfu_pp = pair_work(prob)
+    pairs_prop = agg["cum_pairs_propagated"]
+    pairs_built = agg["cum_cells_built"] * len(prob["controls"])
+    builds = steps * (prob["levels"] + 1)
+    phases = {}
+    t_prop = agg["ms_prop"] / 1e3
+    t_a5 = (agg["ms_prop"] + agg["ms_bin"] + agg["ms_recheck"]) / 1e3
+    alg_flops = flops_pp * pairs_prop
+    if t_prop > 0:
+        phases["prop"] = {"kernels": "k_prop32_lat / k_prop32_sib / k_prop32 (or k_prop64)",
+                          "ms_per_step": 1e3 * t_prop / steps, "bound": "alu", "unit": "TFLOP/s",
+                          "achieved": alg_flops / t_prop / 1e12, "frac": alg_flops / t_prop / 1e12 / fp32_peak,
+                          "flops_per_pair": flops_pp, "sfu_ops_per_pair": sfu_pp,
+                          "executed_certified_tflops": agg["prop_flops"] / t_prop / 1e12,
+                          "with_bin_and_recheck_frac": alg_flops / t_a5 / 1e12 / fp32_peak}
+    t_graph = (agg["ms_count"] + agg["ms_scan"] + agg["ms_fill"] + agg["ms_transpose"]) / 1e3
+    gb = graph_bytes(prob, pairs_built, agg["cum_edges"], builds)
+    if t_graph > 0:
+        phases["graph"] = {"kernels": "k_cchunks, k_cexpand, k_cedges, k_cinc, scans, k_place",
+                           "ms_per_step": 1e3 * t_graph / steps, "bound": "hbm", "unit": "GB/s",
+                           "achieved": gb / t_graph / 1e9, "frac": gb / t_graph / 1e9 / hbm,
+                           "bytes_per_step": gb / steps}
+    t_prune = agg["ms_prune"] / 1e3
+    if t_prune > 0:
+        phases["prune"] = {"kernels": "k_cprune_init, k_cprune", "ms_per_step": 1e3 * t_prune / steps,
+                           "bound": "hbm", "unit": "GB/s", "achieved": agg["prune_bytes"] / t_prune / 1e9,
+                           "frac": agg["prune_bytes"] / t_prune / 1e9 / hbm,
+                           "bytes_per_step": agg["prune_bytes"] / steps}
+    for k in ("ms_bin", "ms_recheck", "ms_classify", "ms_split", "ms_other"):
+        phases[k[3:]] = {"ms_per_step": agg[k] / steps}
+    dom = max(("prop", "graph", "prune"), key=lambda k: phases.get(k, {}).get("ms_per_step", -1))
+    d = phases[dom]
+    traffic = None
+    tr = GRAPH_TRAFFIC.get(name) if dom == "graph" else None
+    if tr:
+        traffic = tr * agg["cum_edges"] / steps
+    roof = {"bound": d["bound"], "kernel": dom, "achieved": d["achieved"],
+            "peak": fp32_peak if d["bound"] == "alu" else hbm, "unit": d["unit"], "frac": d["frac"],
+            "traffic": traffic,
+            "peak_source": ("derived: SMs x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS.json has no FP32 "
+                            "figure)" if d["bound"] == "alu" else f"{src} HBM copy (MEASURED_PEAKS.json hbm_gbs)"),
+            "work": ("algorithmic FLOPs: S s (4 f_g + 13 n) + 2 n (S - 1) per propagated pair" if dom == "prop" else
+                     "algorithmic bytes: 4 per (cell, control) edge + (8 + 8n + 5) per pair + 8 per build"
+                     if dom == "graph" else "algorithmic bytes of the frontier prune"),
+            "phases": phases}
+    return roof
 
 
 def run_gis(a, prob):
     import torch
     from paper_2202_06111_gb300 import build, gis
-
     ws, rank, local = _dist()
     if ws > 1:
         import torch.distributed as dist
@@ -209,9 +365,8 @@ def run_gis(a, prob):
     stream = torch.cuda.Stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
 
-    def solve_once(timing=1):
-        ctx = gis.Context(prob, stream=stream.cuda_stream, timing=timing)
-        return ctx
+    def solve_once(p=prob, timing=1):
+        return gis.Context(p, stream=stream.cuda_stream, timing=timing)
 
     # warm-up (also builds the memory pool and any cached shapes)
     for _ in range(a.warmup):
@@ -224,13 +379,13 @@ def run_gis(a, prob):
     # timed: device time of gis_solve, CUDA events on the library's stream. Each
     # step creates its context before the first event and closes it after the
     # second, so the library's memory pool is reused as in a serving loop.
-    torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
     clk = Clocks(dev) if rank == 0 else None
     per_step, stats = [], []
+    kept32 = None
     torch.cuda.synchronize()
-    for _ in range(a.steps):
+    for i in range(a.steps):
         with torch.cuda.stream(stream):
             c = solve_once()
         flush.zero_()
@@ -242,6 +397,8 @@ def run_gis(a, prob):
         e1.synchronize()
         per_step.append(e0.elapsed_time(e1))
         stats.append(c.stats())
+        if i == 0:
+            kept32 = _kept_key_set(c)
         c.close()
     torch.cuda.synchronize()
     clocks = clk.stop() if clk else None
@@ -250,10 +407,11 @@ def run_gis(a, prob):
     launches = sum(s["cum_launches"] for s in stats)
     total_ms, _, value = aggregate_ranks(sum(per_step), cells, ws, "cuda")
 
-    # end to end through the C ABI: create from host arrays, solve, read the kept cells
+    # end to end through the C ABI: create from host arrays, solve, read the
+    # live cells (with their kept flags) back into host memory
     e2e_times, d2h = [], 0
     h2d = len(prob["controls"]) * 8 * prob.get("m", 1) + 8 * (32 + 4) + 8 * 8 + 4 * 5
-    for i in range(max(3, a.steps // 2)):
+    for i in range(max(2, min(5, a.steps // 2))):
         flush.zero_()
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -267,14 +425,16 @@ def run_gis(a, prob):
         e2e_times.append(dt)
     e2e_value = (cells / len(stats)) / statistics.mean(e2e_times)
 
-    # the same workload with every sample in FP64 (the plain FP64 GPU form)
+    # the same workload with every sample in FP64 (the plain FP64 GPU form), and
+    # whether it keeps the same cells
     p64 = dict(prob, precision="fp64")
+    fp64_runs = 2 if statistics.mean(per_step) < 1000 else 1
     with torch.cuda.stream(stream):
-        c = gis.Context(p64, stream=stream.cuda_stream)
+        c = gis.Context(dict(p64, n0=[4] * prob["n"]), stream=stream.cuda_stream)   # loads the FP64 kernels
         c.solve()
         c.close()
-    fp64_ms = []
-    for _ in range(2):
+    fp64_ms, same = [], None
+    for i in range(fp64_runs):
         flush.zero_()
         torch.cuda.synchronize()
         with torch.cuda.stream(stream):
@@ -285,8 +445,34 @@ def run_gis(a, prob):
         e1.record(stream)
         e1.synchronize()
         fp64_ms.append(e0.elapsed_time(e1))
-        same = c.stats()["cum_cells_built"] == stats[0]["cum_cells_built"]
+        if i == 0:
+            k64 = _kept_key_set(c)
+            same = bool(k64.shape == kept32.shape and (k64 == kept32).all())
         c.close()
+
+    # the cstr workload's headline rule is INNER, which removes nothing after
+    # level 0 there; the paper's OUTER reading removes cells at every level
+    outer = None
+    if prob.get("rule", "inner") == "inner" and prob["n"] == 2:
+        po = dict(prob, rule="outer")
+        oms, ost = [], None
+        for i in range(3):
+            flush.zero_()
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                c = solve_once(po)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c.solve()
+            e1.record(stream)
+            e1.synchronize()
+            if i > 0:
+                oms.append(e0.elapsed_time(e1))
+            ost = c.stats()
+            c.close()
+        outer = {"rule": "outer", "ms_per_step": statistics.mean(oms),
+                 "value": ost["cum_cells_built"] / (statistics.mean(oms) / 1e3), "unit": UNIT,
+                 "cells_per_step": ost["cum_cells_built"], "kept": ost["n_kept"]}
 
     if rank != 0:
         if ws > 1:
@@ -294,41 +480,17 @@ def run_gis(a, prob):
         return
     peaks, src = _peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     agg = {k: sum(s[k] for s in stats) for k in stats[0] if isinstance(stats[0][k], (int, float))}
-    phases = {"prop": ("ms_prop", "prop_flops", "alu"), "count": ("ms_count", "count_bytes", "hbm"),
-              "fill": ("ms_fill", "fill_bytes", "hbm"), "transpose": ("ms_transpose", "transpose_bytes", "hbm"),
-              "prune": ("ms_prune", "prune_bytes", "hbm")}
-    dom = max(phases, key=lambda k: agg[phases[k][0]])
-    ms_k, work_k, bound = phases[dom]
-    sec = agg[ms_k] / 1e3
-    if bound == "alu":
-        achieved = agg[work_k] / sec / 1e12
-        peak, unit = fp32_peak, "TFLOP/s"
-    else:
-        achieved = agg[work_k] / sec / 1e9
-        peak, unit = float(peaks["hbm_gbs"]), "GB/s"
-    by_phase = {}
-    for k, (m, w, b) in phases.items():
-        s_ = agg[m] / 1e3
-        if s_ > 0:
-            ach = agg[w] / s_ / (1e12 if b == "alu" else 1e9)
-            pk = fp32_peak if b == "alu" else float(peaks["hbm_gbs"])
-            by_phase[k] = {"ms_per_step": agg[m] / len(stats), "achieved": ach, "frac": ach / pk, "bound": b}
-    for k in ("ms_bin", "ms_recheck", "ms_scan", "ms_classify", "ms_split", "ms_other"):
-        by_phase[k[3:]] = {"ms_per_step": agg[k] / len(stats)}
-    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": f"{src} ({'FP32 FMA: SMs x 128 lanes x 2 x max SM clock' if bound == 'alu' else 'HBM copy'})",
-                "phases": by_phase}
+    roofline = _roofline(prob, a.workload, agg, len(stats), peaks, src, sms)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": total_ms / len(per_step), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(prob, a.workload),
-            "edges_per_s": edges * ws / (total_ms / 1e3), "solve_ms": {"mean": statistics.mean(per_step),
-                                                                       "p50": statistics.median(per_step),
-                                                                       "p99": max(per_step)},
+            "edges_per_s": edges * ws / (total_ms / 1e3),
+            "cell_edges_per_s": agg["cum_cell_edges"] * ws / (total_ms / 1e3),
+            "solve_ms": {"mean": statistics.mean(per_step), "p50": statistics.median(per_step),
+                         "p99": max(per_step)},
             "cells_per_step": cells / len(stats), "edges_per_step": edges / len(stats),
+            "kept_cells": stats[-1]["n_kept"],
             "recheck_pairs_per_step": agg["cum_recheck"] / len(stats),
             "recheck_samples_per_step": agg["cum_recheck_samples"] / len(stats),
             "recheck_fp64_pairs_per_step": agg["cum_recheck_fp64"] / len(stats),
@@ -341,11 +503,13 @@ def run_gis(a, prob):
                        "tune_launches_timed": agg["cum_tune_launches"]},
             "fp64_plain": {"ms_per_step": statistics.mean(fp64_ms),
                            "speedup_of_fp32_recheck": statistics.mean(fp64_ms) / (total_ms / len(per_step)),
-                           "same_cells_built": same},
+                           "same_kept_cells": same},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": 1e3 * statistics.mean(e2e_times)}}
+    if outer:
+        line["rule_outer"] = outer
     if ws == 1 and not a.no_cpu_baseline:
-        line["cpu_baseline"], _ = cpu_baseline(prob)
+        line["cpu_baseline"] = cpu_baseline(prob, a.workload)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.barrier()
