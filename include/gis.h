@@ -68,8 +68,14 @@ enum {
 /* Pruning rules (Sec. 2.3). OUTER: keep a cell iff some edge of some control
  * leads to a kept cell (non-leaving cells, Def. 3 read as every cell with an
  * infinite admissible path). INNER: keep a cell iff some control maps its
- * image box inside X, touching no removed cell, with every image cell kept. */
-enum { GIS_RULE_INNER = 0, GIS_RULE_OUTER = 1 };
+ * image box inside X, touching no removed cell, with every image cell kept.
+ * SCC: Def. 3 read literally -- the largest strongly connected component of
+ * the cell graph (B_i -> B_j when some control of B_i has target B_j) and
+ * every cell with a path into it; a component must hold a cycle (one cell
+ * only with an edge to itself), every component of the largest size is kept,
+ * a graph without a cycle keeps nothing. Its search runs forward-backward
+ * passes inside the OUTER fixed point (round_limit bounds the passes). */
+enum { GIS_RULE_INNER = 0, GIS_RULE_OUTER = 1, GIS_RULE_SCC = 2 };
 
 /* Precision of the propagation. FP64_PLAIN: every sample in FP64. FP32_RECHECK:
  * samples in certified FP32 -- midpoint-radius arithmetic whose radii bound
@@ -124,8 +130,28 @@ typedef struct {
                                (the neighbourhood that stands in for the N nearest
                                neighbours of Sec. 3.1.2); -1: every kept cell (the
                                all-split scheme); 0 (default): the boundary only    */
+    int32_t enclosure;      /* image of a cell (Sec. 2.2 leaves the method open):
+                               GIS_ENCLOSE_SAMPLES (default) the bounding box of the
+                               k^n sample lattice; GIS_ENCLOSE_INTERVAL an interval
+                               enclosure of the whole cell's image (computed in FP64
+                               whatever `precision` says)                          */
+    int32_t split;          /* GIS_SPLIT_ALL_DIMS (default) | GIS_SPLIT_CYCLED        */
     int32_t reserved;
 } gis_options;
+
+/* Image enclosures. SAMPLES: per (cell, control) the bounding box of the
+ * images of the k^n inclusive sample lattice (an under-approximation of
+ * F(B_i) that converges as the lattice refines). INTERVAL: the RK4 period (or
+ * discrete map) evaluated in interval arithmetic over the whole closed cell,
+ * every +, -, *, / rounded to nearest and moved one ulp outward, exp / sin /
+ * cos by fixed Cody-Waite + Taylor sequences widened beyond their proven
+ * error: the box holds the image of every point of the cell, so the graph
+ * holds every edge of Def. 1 and R_X is inside the kept set at every level
+ * (Prop. 1(iii)). k_samples is unused there.                                  */
+enum { GIS_ENCLOSE_SAMPLES = 0, GIS_ENCLOSE_INTERVAL = 1 };
+/* Subdivision (Sec. 2.1). ALL_DIMS: a split cell has 2^n children (every
+ * dimension halved). CYCLED: 2 children, halving dimension (depth mod n).     */
+enum { GIS_SPLIT_ALL_DIMS = 0, GIS_SPLIT_CYCLED = 1 };
 
 /* One live cell: box = prod [lo + idx w_level, lo + (idx+1) w_level],
  * w_level = (hi - lo) / (n0 2^level).                                         */
@@ -182,6 +208,13 @@ typedef struct {
                                    (0: no lattice kernel)                          */
     int32_t sibling_parents;  /* parents per sibling-lattice block (0: none)        */
     int64_t cum_tune_launches; /* launches the autotuner timed                      */
+    /* staging of the last build's edge walk (one walk serves count and fill) */
+    int64_t stage_cap;      /* edges the staging buffer held (0: no staging)      */
+    int64_t stage_edges;    /* walked edges the count pass produced               */
+    int64_t stage_lost_chunks; /* 1: some chunks found the buffer full and were
+                                  walked again by the fill                        */
+    int64_t free_bytes_at_stage; /* device memory free when the buffer was sized */
+    int64_t scc_passes;     /* forward-backward passes of the last SCC prune      */
 } gis_stats;
 
 typedef struct gis_ctx gis_ctx;
@@ -249,6 +282,8 @@ typedef struct {
     int32_t rule;           /* GIS_RULE_*                                         */
     int32_t precision;
     double band;
+    int32_t enclosure;      /* GIS_ENCLOSE_*                                      */
+    int32_t split;          /* GIS_SPLIT_*                                        */
 } gis_request;
 
 typedef struct {
@@ -316,6 +351,42 @@ gis_status gis_server_get_stats(gis_server *srv, gis_server_stats *out);
 
 /* Stops the worker after the current step; pending requests are dropped. */
 void gis_server_destroy(gis_server *srv);
+
+/* ---- one shard of a prune split across processes --------------------------
+ * The per-process subgraphs and merge of Sec. 3.2 (Fig. 6) applied to the
+ * fixed point of Sec. 2.3: the cells are split into contiguous ranges, one
+ * shard per process (one per GPU); a shard holds the (cell, control) pairs of
+ * its own cells and their targets as global cell ids. Pruning needs one
+ * exchange per round: each shard publishes the bitmap of its cells that died
+ * in the round (gis_shard_round's out_words: bit i = local cell i), the
+ * processes all-gather the slices in shard order into the round's bitmap of
+ * dead cells (bit j = global cell j), and each shard applies it to its own
+ * pairs. The rounds end when a gathered bitmap is empty; the kept cells are
+ * then the greatest fixed point of `rule` (INNER or OUTER), the same set the
+ * whole graph gives pruned in one process.
+ *   off[n_local * n_controls + 1]  host, int64 offsets of the local pairs
+ *                                  (pair = local cell * n_controls + control)
+ *   tgt[off[last]]                 host, int32 global target cell of every edge
+ *   flag[n_local * n_controls]     host, GIS_PAIR_* bits of every local pair
+ * The arrays are copied; the shard owns its device memory. A shard starts on
+ * a multiple of 32 cells and holds a multiple of 32 unless it is the last or
+ * empty (so the slices concatenate into whole words); EINVAL otherwise, and for
+ * offsets that decrease or targets out of range.                              */
+typedef struct gis_shard gis_shard;
+gis_status gis_shard_create(gis_shard **out, int64_t n_cells_total, int64_t first_cell, int64_t n_local,
+                            int32_t n_controls, const int64_t *off, const int32_t *tgt, const uint8_t *flag,
+                            int32_t rule, void *stream);
+/* One round. The first call (dead_words may be NULL) marks the cells with no
+ * viable pair; every later call applies dead_words -- device, the gathered
+ * bitmap of the previous round, ceil(n_cells_total / 32) words -- and marks the
+ * cells that die from it. out_words: device, ceil(n_local / 32) words,
+ * overwritten with this round's dead local cells; *n_new their number.
+ * Synchronises `stream`.                                                      */
+gis_status gis_shard_round(gis_shard *sh, const uint32_t *dead_words, uint32_t *out_words, int64_t *n_new);
+/* The local cells kept (1) or removed (0) so far: kept[n_local], host (may be
+ * NULL); *n_kept their number.                                                */
+gis_status gis_shard_kept(gis_shard *sh, uint8_t *kept, int64_t *n_kept);
+void gis_shard_destroy(gis_shard *sh);   /* NULL-safe */
 
 /* ---- pruning without device allocation ---------------------------------- */
 #define GIS_NOALLOC_MAX_CELLS 131072    /* 2^17 cells                          */

@@ -97,8 +97,8 @@ __global__ void __launch_bounds__(256) k_cchunks(const InstDesc *__restrict__ D,
     if (s >= NL) return;                           // whole warp
     const InstDesc &I = D[cinst[s]];
     if (lane < I.nu) pcnt[I.pair_base + (s - I.slot_base) * I.nu + lane] = 0;
-    if (s - I.slot_base < I.n_carry) {             // edges from the previous level's
-        if (lane == 0) nch[s] = 0;
+    if (s - I.slot_base < I.n_carry || I.split) {  // edges from the previous level's, or
+        if (lane == 0) nch[s] = 0;                 // (cycled bisection) the per-cell descent
         return;
     }
     const int n = I.n, Lf = I.Lf;
@@ -988,7 +988,7 @@ __global__ void __launch_bounds__(256) k_cprune_init(const InstDesc *__restrict_
     const int64_t p0 = I.pair_base + (s - I.slot_base) * I.nu;
     uint32_t m = 0;
     uint8_t info = 0;
-    if (I.rule == GIS_RULE_OUTER) {
+    if (I.rule != GIS_RULE_INNER) {                // OUTER, and the OUTER set the SCC rule searches
         const int w = 64 / I.nu;
         const int64_t cmax = w >= 32 ? (int64_t)INT_MAX : ((int64_t)1 << w) - 2;
         unsigned long long word = 0;

@@ -50,6 +50,10 @@ struct InstDesc {
     int32_t ntile[MAXN];        // tiles per dimension
     int64_t fresh0;             // live index of the first fresh cell (children of split cells)
     int32_t sib_groups;         // sibling groups (2^n children of one parent) per lattice block, 0: none
+    int32_t enclosure;          // GIS_ENCLOSE_SAMPLES | GIS_ENCLOSE_INTERVAL
+    int32_t split;              // GIS_SPLIT_ALL_DIMS | GIS_SPLIT_CYCLED
+    double dt;                  // sampling period
+    double praw[GIS_NPARAM];    // the parameters as given (the interval models use them)
     float p32[GIS_NPARAM];      // derived constants for the FP32 model
     float pr32[GIS_NPARAM];     // their radii: |p32 - exact value|, rounded up
     double p64[GIS_NPARAM];     // derived constants for the FP64 model (same ops as the definition)
@@ -61,7 +65,10 @@ struct InstDesc {
     float lo32[MAXN];
     float lor32[MAXN];          // radius of lo32
     int32_t n0[MAXN];
-    double w64[MAXL + 1][MAXN]; // (hi - lo) / (n0 2^L)
+    double w64[MAXL + 1][MAXN]; // (hi - lo) / (n0 2^dl[L][d]): the level-L width per dimension
+    uint8_t dl[MAXL + 1][MAXN]; // halvings of dimension d in a level-L cell: L when every split
+                                // halves every dimension; with cycled bisection (depth t halves
+                                // dimension t mod n) L / n, plus 1 if d < L mod n
     float w32[MAXL + 1][MAXN];
     float wr32[MAXL + 1][MAXN]; // radius of w32
     float invwf32[MAXN];        // 1 / w at Lf
@@ -471,6 +478,12 @@ __device__ __forceinline__ void sample64(const InstDesc &I, int L, const int32_t
         x[d] = __dadd_rn(base, __dmul_rn(w, I.frac64[j]));
     }
 }
+
+// Halvings of dimension d at level L, and the shift from level L to the finest level
+__device__ __forceinline__ int dlev(const InstDesc &I, int L, int d) { return I.dl[L][d]; }
+__device__ __forceinline__ int dshift(const InstDesc &I, int L, int d) { return I.dl[I.Lf][d] - I.dl[L][d]; }
+// children of a split node (the cycled bisection halves dimension (level mod n) only)
+__device__ __forceinline__ int nchildren(const InstDesc &I) { return I.split ? 2 : 1 << I.n; }
 
 // Level-L index range of the leaves meeting [c - 1, f] at the finest level Lf
 // (c = ceil(t_min), f = floor(t_max) at Lf): ceil and floor commute with the

@@ -8,11 +8,13 @@ using namespace gis;
 static void check_depth(const Inst &I, int level)
 {
     if (level > GIS_MAX_LEVEL) throw Error{GIS_EUNSUPPORTED, "maximum depth reached"};
-    if ((int64_t)((1 << I.dyn.n) - 1) * level + 1 > STACK)
+    if ((int64_t)(I.nchild() - 1) * level + 1 > STACK)
         throw Error{GIS_EUNSUPPORTED, "subdivision depth too large for this dimension"};
-    for (int d = 0; d < I.dyn.n; d++)
-        if (((int64_t)I.grid.root_cells[d] << level) > (int64_t)1 << 24)
+    for (int d = 0; d < I.dyn.n; d++) {
+        const int halvings = I.split == GIS_SPLIT_CYCLED ? level / I.dyn.n + (d < level % I.dyn.n ? 1 : 0) : level;
+        if (((int64_t)I.grid.root_cells[d] << halvings) > (int64_t)1 << 24)
             throw Error{GIS_EUNSUPPORTED, "finest grid above 2^24 cells per dimension"};
+    }
 }
 
 struct gis_ctx {
@@ -69,7 +71,7 @@ gis_status gis_create(gis_ctx **out, const gis_dynamics *dyn, const gis_grid *gr
         c = new gis_ctx();
         c->eng.init(opt, stream);
         const gis_options &o = c->eng.opt;
-        c->eng.add(*dyn, *grid, *controls, o.rule, o.precision, o.band, 0);
+        c->eng.add(*dyn, *grid, *controls, o.rule, o.precision, o.band, 0, o.enclosure, o.split);
         *out = c;
         return GIS_OK;
     } catch (const Error &e) {
@@ -237,7 +239,7 @@ gis_status gis_batch_solve(const gis_request *reqs, int32_t n, gis_result *res, 
             res[i].levels_done = 0;
             res[i].n_kept = res[i].n_cells = res[i].n_edges_total = res[i].cells_built = 0;
             const gis_request &r = reqs[i];
-            E->add(r.dyn, r.grid, r.controls, r.rule, r.precision, r.band, r.levels);
+            E->add(r.dyn, r.grid, r.controls, r.rule, r.precision, r.band, r.levels, r.enclosure, r.split);
         }
         std::vector<int> act;
         for (int i = 0; i < n; i++) act.push_back(i);

@@ -87,11 +87,14 @@ struct Mem {
     cudaStream_t st = nullptr;
     cudaMemPool_t pool = nullptr;
     int64_t limit = 0, used = 0;
+    int64_t fail_after = -1;     // test hook: the allocation this many from now fails once
     std::map<void *, size_t> sizes;
 
     void *alloc(size_t bytes)
     {
         if (bytes == 0) bytes = 16;
+        if (fail_after >= 0 && fail_after-- == 0)
+            throw Error{GIS_ENOMEM, "allocation failure injected by GIS_TEST_FAIL_ALLOC"};
         if (limit > 0 && used + (int64_t)bytes > limit)
             throw Error{GIS_ENOMEM, "device memory limit reached (" + std::to_string(used + bytes) + " bytes)"};
         void *p = nullptr;
@@ -207,6 +210,8 @@ struct Inst {
     gis_grid grid{};
     std::vector<double> u;
     int nu = 0, rule = 0, precision = 0, levels = 0;
+    int enclosure = 0, split = 0;
+    int nchild() const { return split == GIS_SPLIT_CYCLED ? 2 : 1 << dyn.n; }
     double band = 1e-2;
     int S = 1;
     // host view of device state
@@ -328,8 +333,12 @@ inline int ipow(int b, int e)
 
 // Validate a problem; fills I (host part).
 inline void setup_inst(Inst &I, const gis_dynamics &dyn, const gis_grid &grid, const gis_controls &ctl, int rule,
-                       int precision, double band, int levels)
+                       int precision, double band, int levels, int enclosure = 0, int split = 0)
 {
+    if (enclosure != GIS_ENCLOSE_SAMPLES && enclosure != GIS_ENCLOSE_INTERVAL) throw Error{GIS_EINVAL, "bad enclosure"};
+    if (split != GIS_SPLIT_ALL_DIMS && split != GIS_SPLIT_CYCLED) throw Error{GIS_EINVAL, "bad split"};
+    // the interval enclosure is computed in FP64 and decided as FP64 extremes
+    if (enclosure == GIS_ENCLOSE_INTERVAL) precision = GIS_FP64_PLAIN;
     if (dyn.n < 1 || dyn.n > MAXN || dyn.m < 1 || dyn.m > MAXN) throw Error{GIS_EINVAL, "n and m must be in 1..4"};
     if (dyn.substeps < 0) throw Error{GIS_EINVAL, "substeps must be >= 0"};
     if (!(dyn.dt > 0) && dyn.substeps > 0) throw Error{GIS_EINVAL, "dt must be > 0"};
@@ -357,14 +366,17 @@ inline void setup_inst(Inst &I, const gis_dynamics &dyn, const gis_grid &grid, c
     }
     if (R > (int64_t)1 << 30) throw Error{GIS_EINVAL, "too many root cells"};
     if (levels < 0 || levels > MAXL) throw Error{GIS_EINVAL, "levels must be in 0..15"};
-    if ((int64_t)((1 << dyn.n) - 1) * levels + 1 > STACK)
+    const int nchild = split == GIS_SPLIT_CYCLED ? 2 : 1 << dyn.n;
+    if ((int64_t)(nchild - 1) * levels + 1 > STACK)
         throw Error{GIS_EUNSUPPORTED, "subdivision depth too large for this dimension"};
-    for (int d = 0; d < dyn.n; d++)
-        if (((int64_t)grid.root_cells[d] << levels) > (int64_t)1 << 24)
+    for (int d = 0; d < dyn.n; d++) {
+        const int halvings = split == GIS_SPLIT_CYCLED ? levels / dyn.n + (d < levels % dyn.n ? 1 : 0) : levels;
+        if (((int64_t)grid.root_cells[d] << halvings) > (int64_t)1 << 24)
             throw Error{GIS_EUNSUPPORTED, "finest grid above 2^24 cells per dimension"};
+    }
     if (ctl.n_controls < 1 || !ctl.u) throw Error{GIS_EINVAL, "need >= 1 control value"};
     if (ctl.n_controls > 32) throw Error{GIS_EUNSUPPORTED, "at most 32 control values per problem"};
-    if (rule != GIS_RULE_INNER && rule != GIS_RULE_OUTER) throw Error{GIS_EINVAL, "bad rule"};
+    if (rule != GIS_RULE_INNER && rule != GIS_RULE_OUTER && rule != GIS_RULE_SCC) throw Error{GIS_EINVAL, "bad rule"};
     if (precision != GIS_FP64_PLAIN && precision != GIS_FP32_RECHECK) throw Error{GIS_EINVAL, "bad precision"};
     if (precision == GIS_FP32_RECHECK && !(band >= 0 && band < 0.25)) throw Error{GIS_EINVAL, "band must be in [0, 1/4)"};
     I.dyn = dyn;
@@ -378,6 +390,8 @@ inline void setup_inst(Inst &I, const gis_dynamics &dyn, const gis_grid &grid, c
     I.band = band;
     I.levels = levels;
     I.S = S;
+    I.enclosure = enclosure;
+    I.split = split;
 }
 
 // Model constants. FP64: the exact values the defining expressions use
@@ -476,6 +490,9 @@ inline void fill_desc(Inst &I)
         D.hhr32 = radius_of(h * 0.5, D.hh32);
         D.h6r32 = radius_of(h / 6.0, D.h6_32);
     }
+    for (int L = 0; L <= MAXL; L++)
+        for (int d = 0; d < MAXN; d++)
+            D.dl[L][d] = (uint8_t)(I.split == GIS_SPLIT_CYCLED ? L / n + (d < L % n ? 1 : 0) : L);
     for (int d = 0; d < MAXN; d++) {
         D.lo[d] = d < n ? I.grid.lo[d] : 0;
         D.hi[d] = d < n ? I.grid.hi[d] : 1;
@@ -483,7 +500,7 @@ inline void fill_desc(Inst &I)
         D.lor32[d] = radius_of(D.lo[d], D.lo32[d]);
         D.n0[d] = d < n ? I.grid.root_cells[d] : 1;
         for (int L = 0; L <= MAXL; L++) {
-            D.w64[L][d] = (D.hi[d] - D.lo[d]) / (double)((int64_t)D.n0[d] << L);
+            D.w64[L][d] = (D.hi[d] - D.lo[d]) / (double)((int64_t)D.n0[d] << D.dl[L][d]);
             D.w32[L][d] = (float)D.w64[L][d];
             D.wr32[L][d] = radius_of(D.w64[L][d], D.w32[L][d]);
         }
@@ -496,11 +513,15 @@ inline void fill_desc(Inst &I)
         // (beyond, both sides clamp alike), so the error is at most
         // 3 * 2^-24 * (Nf + 4) + lo_err cells (x1.25 margin, which also covers
         // the FP64 decision's own rounding), plus the optional band.
-        const double Nf = (double)((int64_t)D.n0[d] << I.Lf);
+        const double Nf = (double)((int64_t)D.n0[d] << D.dl[I.Lf][d]);
         const double lo_err = std::fabs((double)D.lo32[d] - D.lo[d]) / wf;
         const double tb = 1.25 * (lo_err + 3.0 * 5.9604645e-8 * (Nf + 4.0));
         D.tmargin[d] = (float)(I.band + tb);
     }
+    D.enclosure = I.enclosure;
+    D.split = I.split;
+    D.dt = I.dyn.dt;
+    for (int i = 0; i < GIS_NPARAM; i++) D.praw[i] = I.dyn.params[i];
     D.fresh0 = I.n_live - I.n_fresh;
     D.sib_groups = sibling_groups(n, I.grid.k_samples);
     if (I.sib_cap > 0) D.sib_groups = std::min(D.sib_groups, I.sib_cap);
@@ -633,6 +654,18 @@ struct Engine {
     // small control block: [0..2] sizes, [3] bar, [4] err, [5] rounds, [6] rq count, [7] edge err, [8..9] scanned
     int32_t *ctl = nullptr;
 
+    // Def. 3 read literally (rule SCC): per slot colour, OUTER set, closure
+    // marks, trimming counts; backward frontiers; kept colours; control words
+    int32_t *scc_color = nullptr; size_t c_scc_color = 0;
+    uint8_t *scc_kin = nullptr; size_t c_scc_kin = 0;
+    uint32_t *scc_mark = nullptr; size_t c_scc_mark = 0;
+    int32_t *scc_din = nullptr, *scc_dout = nullptr; size_t c_scc_din = 0, c_scc_dout = 0;
+    int32_t *scc_bf[2] = {}; size_t c_scc_bf[2] = {0, 0};
+    uint8_t *scc_best = nullptr; size_t c_scc_best = 0;
+    unsigned long long *scc_ctl = nullptr; size_t c_scc_ctl = 0;
+    int64_t last_scc_passes = 0;
+    int64_t last_stage_cap = 0, last_stage_edges = 0, last_stage_lost = 0, last_free_at_stage = 0;
+
     bool have_graph = false, have_prune = false, have_bnd = false;
     int last_rounds = 0;
     int64_t last_recheck = 0, last_new_pairs = 0, last_split = 0, last_kept = 0;
@@ -700,6 +733,22 @@ struct Engine {
         return pin;
     }
 
+    // device memory free for this engine: the device's free memory plus what
+    // the library's pool holds unused (freed by earlier contexts, reusable)
+    size_t free_bytes()
+    {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        if (mem.pool) {
+            unsigned long long res = 0, used = 0;
+            if (cudaMemPoolGetAttribute(mem.pool, cudaMemPoolAttrReservedMemCurrent, &res) == cudaSuccess &&
+                cudaMemPoolGetAttribute(mem.pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && res > used)
+                fr += (size_t)(res - used);
+            cudaGetLastError();
+        }
+        return fr;
+    }
+
     void sync()
     {
         CK(cudaStreamSynchronize(st));
@@ -708,11 +757,12 @@ struct Engine {
 
     // ---- instances --------------------------------------------------------
     int add(const gis_dynamics &dyn, const gis_grid &grid, const gis_controls &ctl_, int rule, int precision,
-            double band, int levels)
+            double band, int levels, int enclosure = 0, int split = 0)
     {
         Inst *I = new Inst();
         try {
-            setup_inst(*I, dyn, grid, ctl_, rule, precision, band, levels);
+            setup_inst(*I, dyn, grid, ctl_, rule, precision, band, levels, enclosure, split);
+            precision = I->precision;
             int64_t R = 1;
             for (int d = 0; d < dyn.n; d++) R *= grid.root_cells[d];
             I->n_nodes = R;
@@ -979,8 +1029,8 @@ struct Engine {
         if (I.desc.ntile[0] > 0 && I.level == 0 && I.n_fresh == I.n_live && I.n_live == I.n_nodes &&
             opt.lanes_per_pair == 0)
             return PK_LATTICE;
-        if (I.desc.sib_groups > 0 && I.n_fresh < I.n_nodes && I.n_fresh % (1 << I.dyn.n) == 0 &&
-            opt.lanes_per_pair == 0)
+        if (I.desc.sib_groups > 0 && I.split == GIS_SPLIT_ALL_DIMS && I.n_fresh < I.n_nodes &&
+            I.n_fresh % (1 << I.dyn.n) == 0 && opt.lanes_per_pair == 0)
             return PK_SIBLING;
         return PK_PAIR;
     }
@@ -1108,7 +1158,9 @@ struct Engine {
         // engine's previous build) take their edges from that graph
         for (int i : ids) {
             Inst &I = *inst[i];
-            I.n_carry = (have_prev && I.built_at == build_no - 1) ? I.n_live - I.n_fresh : 0;
+            // (a cycled problem's cells all take the per-cell descent)
+            I.n_carry = (have_prev && I.built_at == build_no - 1 && I.split != GIS_SPLIT_CYCLED) ? I.n_live - I.n_fresh
+                                                                                                : 0;
             I.built_at = build_no;
         }
         build_no++;
@@ -1172,6 +1224,9 @@ struct Engine {
                 double pts = 1;
                 for (int d = 0; d < I.dyn.n; d++) pts *= 2.0 * (I.grid.k_samples - 1) + 1;
                 cum.prop_flops += sample_ball_flops(I) * pts * (double)ng * I.nu;
+            } else if (I.enclosure == GIS_ENCLOSE_INTERVAL) {
+                // interval enclosure of each whole cell (lanes = -2 marks it)
+                groups[{I.dyn.dyn_id, I.dyn.n, I.precision, -2}].push_back({I.tix, first, I.n_fresh * I.nu});
             } else {
                 const int lanes = I.precision == GIS_FP64_PLAIN ? 1 : lanes_for(I);
                 groups[{I.dyn.dyn_id, I.dyn.n, I.precision, lanes}].push_back({I.tix, first, I.n_fresh * I.nu});
@@ -1186,7 +1241,9 @@ struct Engine {
         for (auto &g : groups) {
             const int dyn = std::get<0>(g.first), n = std::get<1>(g.first), prec = std::get<2>(g.first);
             const int lanes = std::get<3>(g.first);
-            if (prec == GIS_FP64_PLAIN) {
+            if (lanes == -2) {
+                CK(launch_prop_iv(dyn, n, d_desc, make_work(g.second, prop_iv_threads()), st));
+            } else if (prec == GIS_FP64_PLAIN) {
                 CK(launch_prop64(dyn, n, d_desc, make_work(g.second, 256), st));
             } else if (lanes == 0) {
                 CK(launch_prop32_lattice(dyn, n, d_desc, make_work(g.second, 1), st));
@@ -1298,6 +1355,14 @@ struct Engine {
                     r.push_back({inst[i]->tix, inst[i]->slot_base, inst[i]->n_carry});
             return r;
         };
+        // cells of cycled-bisection problems: the per-cell descent
+        auto cycled = [&](int n) {
+            std::vector<RangeSpec> r;
+            for (int i : ids)
+                if (inst[i]->dyn.n == n && inst[i]->split == GIS_SPLIT_CYCLED && inst[i]->n_live > 0)
+                    r.push_back({inst[i]->tix, inst[i]->slot_base, inst[i]->n_live});
+            return r;
+        };
         // work chunks of the walked cells' union boxes (cells of one dimension
         // are contiguous: number() orders the problems by dimension); the chunk
         // arrays are sized from the previous build and grown if they overflow
@@ -1323,20 +1388,40 @@ struct Engine {
         const double fper = fixed_per ? std::atof(fixed_per) : -1.0;
         if (walked > 0 && fper != 0.0 && cap < ((int64_t)1 << 31)) {   // segment records hold int32 chunk ids
             const double per = fper > 0 ? fper : stage_per_cell > 0 ? 1.25 * stage_per_cell : 64.0;
-            const int64_t scap = (int64_t)(per * (double)walked) + (fper > 0 ? 1 : 65536);
-            const int64_t gcap = cap + scap / (CE_EB_HOST - 32) + 4096;
+            const int64_t want = (int64_t)(per * (double)walked) + (fper > 0 ? 1 : 65536);
+            int64_t scap = want;
             auto grown = [](size_t have, int64_t need, size_t el) {
                 return (size_t)need <= have ? 0.0 : (double)std::max<size_t>((size_t)need, have + have / 2) * el;
             };
-            const double extra = grown(c_stg, scap, sizeof(unsigned long long)) + grown(c_seg, gcap, sizeof(SegRec));
+            auto extra_for = [&](int64_t sc) {
+                const int64_t gc = cap + sc / (CE_EB_HOST - 32) + 4096;
+                return grown(c_stg, sc, sizeof(unsigned long long)) + grown(c_seg, gc, sizeof(SegRec));
+            };
+            double extra = extra_for(scap);
             // a large growth must also leave room for the edge arrays that follow
-            // (forward and reverse, 16 bytes an edge); small ones skip the query
+            // (forward and reverse, 16 bytes an edge, the expected edges of the
+            // walked cells plus a tenth); small ones skip the query. Where the
+            // whole staging does not fit beside them, a smaller buffer (at least a
+            // quarter) stages what it holds and only the chunks that find it full
+            // are walked again by the fill
             bool room = extra <= 256.0 * (1 << 20);
             if (!room) {
-                size_t fr = 0, tot = 0;
-                cudaMemGetInfo(&fr, &tot);
-                room = extra + 16.0 * (double)scap <= 0.8 * (double)fr;
+                const size_t fr = free_bytes();
+                last_free_at_stage = (int64_t)fr;
+                const double expect = fper > 0 ? (double)want : (double)want / 1.25;
+                const double edges_reserve = 16.0 * 1.1 * expect;
+                room = extra + edges_reserve <= 0.85 * (double)fr;
+                if (!room) {
+                    const double budget = 0.85 * (double)fr - edges_reserve;
+                    const int64_t fit = budget > 0 ? (int64_t)(budget / (8.0 + (double)sizeof(SegRec) / 64.0)) : 0;
+                    if (fit >= want / 4) {
+                        scap = std::min(want, fit);
+                        extra = extra_for(scap);
+                        room = extra + edges_reserve <= 0.85 * (double)fr;
+                    }
+                }
             }
+            const int64_t gcap = cap + scap / (CE_EB_HOST - 32) + 4096;
             if (room && (mem.limit == 0 || (double)mem.used + extra <= 0.8 * (double)mem.limit)) {
                 mem.ensure(stg, c_stg, (size_t)scap);
                 mem.ensure(seg, c_seg, (size_t)gcap);
@@ -1375,6 +1460,8 @@ struct Engine {
             for (int n = 1; n <= MAXN; n++) {
                 const auto r = carried(n);
                 if (!r.empty()) CK(launch_cinc(false, n, d_desc, make_work(r, cedges_cells_per_block()), g, prev, st));
+                const auto c = cycled(n);
+                if (!c.empty()) CK(launch_sedges(false, n, d_desc, make_work(c, sedges_cells_per_block()), g, st));
             }
             timer.end();
             timer.begin(PH_SCAN);
@@ -1405,7 +1492,10 @@ struct Engine {
             std::memcpy(&nseg, hp + 64, sizeof(nseg));
             std::memcpy(&sover, hp + 68, sizeof(sover));
         }
-        if (sa.stg && walked > 0) stage_per_cell = (double)staged / (double)walked;
+        if (sa.stg && walked > 0) stage_per_cell = (double)staged / (double)walked;   // top counts every edge
+        last_stage_cap = sa.stg ? sa.cap : 0;
+        last_stage_edges = (int64_t)staged;
+        last_stage_lost = sover ? 1 : 0;
         const bool placed = sa.stg != nullptr;   // chunks that lost a flush are walked again
         last_recheck = hq[0];
         if (last_recheck > 0) {
@@ -1449,6 +1539,8 @@ struct Engine {
         for (int n = 1; n <= MAXN; n++) {
             const auto r = carried(n);
             if (!r.empty()) CK(launch_cinc(true, n, d_desc, make_work(r, cedges_cells_per_block()), g, prev, st));
+            const auto c = cycled(n);
+            if (!c.empty()) CK(launch_sedges(true, n, d_desc, make_work(c, sedges_cells_per_block()), g, st));
         }
         have_prev = true;
         prev_NL = NL;
@@ -1524,12 +1616,123 @@ struct Engine {
         a.spin_limit = (int64_t)1 << 25;
         if (NL > 0) CK(launch_cprune(a, NL, st));
         timer.end();
+        last_scc_passes = 0;
+        for (int i : step)
+            if (inst[i]->rule == GIS_RULE_SCC && inst[i]->n_live > 0) scc_prune(*inst[i]);
         mem.ensure(kept_i64, c_kept_i64, step.size() + 1);
         CK(cudaMemsetAsync(kept_i64, 0, step.size() * sizeof(int64_t), st));
         CK(launch_count_kept(ws, alive, kept_i64, st));
         prune_pending = true;
         have_prune = true;
         if (sync_now) finish_prune();
+    }
+
+    // Def. 3 read literally for problem I, once `alive` holds the OUTER fixed
+    // point K: the largest cycle-holding strongly connected components inside
+    // K and every cell with a path into them (gis_scc.cu). Parts are searched
+    // largest first; a part smaller than the best component found is dropped.
+    void scc_prune(Inst &I)
+    {
+        const size_t NLs = (size_t)std::max<int64_t>(NL, 1);
+        mem.ensure(scc_color, c_scc_color, NLs);
+        mem.ensure(scc_kin, c_scc_kin, NLs);
+        mem.ensure(scc_mark, c_scc_mark, NLs);
+        mem.ensure(scc_din, c_scc_din, NLs);
+        mem.ensure(scc_dout, c_scc_dout, NLs);
+        mem.ensure(scc_bf[0], c_scc_bf[0], NLs);
+        mem.ensure(scc_bf[1], c_scc_bf[1], NLs);
+        mem.ensure(scc_ctl, c_scc_ctl, 32);
+        SccArgs a{};
+        a.s0 = I.slot_base;
+        a.s1 = I.slot_base + I.n_live;
+        a.coff = coff;
+        a.cent = cent;
+        a.roff = roff;
+        a.rsrc = rsrc;
+        a.color = scc_color;
+        a.kin = scc_kin;
+        a.mark = scc_mark;
+        a.din = scc_din;
+        a.dout = scc_dout;
+        a.front[0] = front[0];
+        a.front[1] = front[1];
+        a.bfront[0] = scc_bf[0];
+        a.bfront[1] = scc_bf[1];
+        a.cnt = scc_ctl;                                // words 0 .. 7
+        a.key = scc_ctl + 8;
+        uint32_t *w = (uint32_t *)(scc_ctl + 9);        // 32-bit words after the counters
+        a.sizes = w;
+        a.sizes2 = w + 3;
+        a.bar = w + 6;
+        a.bar2 = w + 7;
+        a.err = (int32_t *)(w + 8);
+        a.spin_limit = (int64_t)1 << 25;
+        const int64_t limit = opt.round_limit > 0 ? opt.round_limit : ((int64_t)1 << 30);
+        unsigned long long h[16];
+        auto clear = [&]() { CK(cudaMemsetAsync(scc_ctl, 0, 16 * sizeof(unsigned long long), st)); };
+        auto read = [&]() {
+            unsigned char *hp = pinned(256);
+            CK(cudaMemcpyAsync(hp, scc_ctl, 16 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+            sync();
+            std::memcpy(h, hp, sizeof h);
+            int32_t err = 0;
+            std::memcpy(&err, (const unsigned char *)h + 9 * 8 + 8 * 4, sizeof err);
+            if (err != 0) throw Error{(gis_status)err, "scc: a bounded device wait ran out"};
+        };
+        // trim part c; returns the cells left in it
+        auto trim = [&](int32_t c, int64_t size) {
+            clear();
+            CK(launch_scc_trim(a, c, st));
+            read();
+            return size - (int64_t)h[1];
+        };
+        clear();
+        CK(launch_scc_colors(a, alive, st));
+        read();
+        std::vector<std::pair<int32_t, int64_t>> parts;    // (colour, cells)
+        int32_t ncol = 1;
+        const int64_t k0 = trim(0, (int64_t)h[0]);
+        if (k0 > 0) parts.push_back({0, k0});
+        int64_t best = 0;
+        std::vector<int32_t> bests;
+        while (!parts.empty()) {
+            auto it = std::max_element(parts.begin(), parts.end(),
+                                       [](const std::pair<int32_t, int64_t> &x, const std::pair<int32_t, int64_t> &y) {
+                                           return x.second < y.second;
+                                       });
+            const int32_t c = it->first;
+            const int64_t size = it->second;
+            parts.erase(it);
+            if (size < std::max<int64_t>(best, 1)) break;   // every other part is smaller still
+            if (++last_scc_passes > limit) throw Error{GIS_ETIMEOUT, "scc: pass limit reached"};
+            clear();
+            CK(launch_scc_closures(a, c, st));
+            const int32_t cS = ncol, cF = ncol + 1, cB = ncol + 2;
+            ncol += 3;
+            CK(launch_scc_split(a, c, cS, cF, cB, st));
+            read();
+            const int64_t nS = (int64_t)h[4], nF = (int64_t)h[5], nB = (int64_t)h[6], nR = (int64_t)h[7];
+            const bool cyclic = nS >= 2 || (nS == 1 && h[2] != 0);
+            if (cyclic && nS > best) {
+                best = nS;
+                bests.assign(1, cS);
+            } else if (cyclic && nS == best) {
+                bests.push_back(cS);
+            }
+            const std::pair<int32_t, int64_t> rest[3] = {{cF, nF}, {cB, nB}, {c, nR}};
+            for (const auto &r : rest) {
+                if (r.second < std::max<int64_t>(best, 1)) continue;
+                const int64_t left = trim(r.first, r.second);
+                if (left >= std::max<int64_t>(best, 1)) parts.push_back({r.first, left});
+            }
+        }
+        std::vector<uint8_t> isb((size_t)ncol, 0);
+        for (int32_t c : bests) isb[(size_t)c] = 1;
+        mem.ensure(scc_best, c_scc_best, (size_t)ncol);
+        CK(cudaMemcpyAsync(scc_best, isb.data(), isb.size(), cudaMemcpyHostToDevice, st));
+        clear();
+        CK(launch_scc_keep(a, scc_best, ncol, alive, st));
+        read();                                           // also keeps isb alive until the copy ran
     }
 
     // read the prune's counts back: enqueue the copies into the pinned staging
@@ -1646,7 +1849,7 @@ struct Engine {
         for (size_t j = 0; j < cont.size(); j++) {
             Inst &I = *inst[cont[j]];
             const int64_t nb = tot[j] & 0xffffffffll, nkeep = tot[j] >> 32;
-            const int64_t kids = nb << I.dyn.n;
+            const int64_t kids = nb * I.nchild();
             if (I.n_nodes + kids >= ((int64_t)1 << 31) - 1) throw Error{GIS_EUNSUPPORTED, "more than 2^31 nodes"};
             grow_inst(I, I.n_nodes + kids, nkeep + kids);
             si[I.tix].new_live = I.live[1 - I.cur];
@@ -1668,7 +1871,7 @@ struct Engine {
         for (size_t j = 0; j < cont.size(); j++) {
             Inst &I = *inst[cont[j]];
             const int64_t nb = tot[j] & 0xffffffffll, nkeep = tot[j] >> 32;
-            const int64_t kids = nb << I.dyn.n;
+            const int64_t kids = nb * I.nchild();
             I.n_nodes += kids;
             I.n_live = nkeep + kids;
             I.n_fresh = kids;
@@ -1707,6 +1910,11 @@ struct Engine {
         s->n_new_pairs = last_new_pairs;
         s->n_recheck = last_recheck;
         s->prune_rounds = last_rounds;
+        s->stage_cap = last_stage_cap;
+        s->stage_edges = last_stage_edges;
+        s->stage_lost_chunks = last_stage_lost;
+        s->free_bytes_at_stage = last_free_at_stage;
+        s->scc_passes = last_scc_passes;
         s->lanes_per_pair = inst.empty() ? 0 : const_cast<Engine *>(this)->lanes_for(*inst[0]);
         if (!inst.empty()) {
             const Inst &I = *inst[0];

@@ -9,6 +9,8 @@
 //                       cooperative launch (gis_prune_graph_noalloc)
 //  k_classify           exact boundary rule (Sec. 3.1.1, Alg. 1, Remark 1)
 //  k_split              2^n children of boundary cells (Sec. 2.1, Sec. 3.1)
+#include <climits>
+
 #include "gis_kernels.cuh"
 
 namespace gis {
@@ -30,6 +32,8 @@ long long launches_total() { return t_launches; }
 
 // Visit every leaf of the tree whose level-L index lies in the per-level
 // ranges given by RF(L, d, a, b). Visitor V(node, state) returns false to stop.
+// A split node's children: 2^n (child c halves dimension d to 2 idx_d + bit
+// N-1-d of c), or with cycled bisection 2 (dimension level mod n only).
 template <int N, class RF, class V>
 __device__ __forceinline__ int descend(const InstDesc &I, const RF &rf, V &visit)
 {
@@ -62,11 +66,13 @@ __device__ __forceinline__ int descend(const InstDesc &I, const RF &rf, V &visit
                 pidx[d] = I.idx[d][node];
                 rf(L, d, ia[d], ib[d]);
             }
-            for (int c = (1 << N) - 1; c >= 0; c--) {
+            const int ds = (L - 1) % N;            // the dimension a cycled split halves
+            for (int c = nchildren(I) - 1; c >= 0; c--) {
                 bool in = true;
 #pragma unroll
                 for (int d = 0; d < N; d++) {
-                    const int ci = 2 * pidx[d] + ((c >> (N - 1 - d)) & 1);
+                    const int ci = I.split ? (d == ds ? 2 * pidx[d] + c : pidx[d])
+                                           : 2 * pidx[d] + ((c >> (N - 1 - d)) & 1);
                     in = in && ci >= ia[d] && ci <= ib[d];
                 }
                 if (!in) continue;
@@ -386,9 +392,10 @@ cudaError_t launch_mark_dead(const InstDesc *D, const WorkList &w, const uint8_t
 }
 
 // A kept cell is a boundary cell iff its closed box touches a face of X or a
-// removed leaf. Neighbour ranges in exact integers: a level-L' leaf j meets
-// the level-L cell i iff ceil(i / 2^(L-L')) - 1 <= j <= floor((i+1) / 2^(L-L'))
-// (L' <= L), or i 2^(L'-L) - 1 <= j <= (i+1) 2^(L'-L) (L' > L).
+// removed leaf. Neighbour ranges in exact integers, per dimension with l and
+// l' the halvings of the two levels along it: a level-L' leaf j meets the
+// level-L cell i iff ceil(i / 2^(l-l')) - 1 <= j <= floor((i+1) / 2^(l-l'))
+// (l' <= l), or i 2^(l'-l) - 1 <= j <= (i+1) 2^(l'-l) (l' > l).
 // packed = (kept and not boundary) << 32 | boundary, for one scan of both.
 template <int N>
 __global__ void __launch_bounds__(256) k_classify(const InstDesc *__restrict__ D, const Range *__restrict__ R, int nr,
@@ -409,21 +416,22 @@ __global__ void __launch_bounds__(256) k_classify(const InstDesc *__restrict__ D
 #pragma unroll
     for (int d = 0; d < N; d++) {
         idx[d] = I.idx[d][node];
-        b = b || idx[d] == 0 || idx[d] == (I.n0[d] << L) - 1;
+        b = b || idx[d] == 0 || idx[d] == (I.n0[d] << dlev(I, L, d)) - 1;
     }
     if (!b) {
         auto rf = [&](int Lp, int d, int &a, int &bb) {
             const int i = idx[d];
-            if (Lp <= L) {
-                const int sh = L - Lp;
+            const int ld = dlev(I, L, d), lpd = dlev(I, Lp, d);
+            if (lpd <= ld) {
+                const int sh = ld - lpd;
                 a = ((i + (1 << sh) - 1) >> sh) - 1;
                 bb = (i + 1) >> sh;
             } else {
-                const int sh = Lp - L;
+                const int sh = lpd - ld;
                 a = (i << sh) - 1;
                 bb = (i + 1) << sh;
             }
-            const int last = (I.n0[d] << Lp) - 1;
+            const int last = (I.n0[d] << lpd) - 1;
             a = a < 0 ? 0 : a;
             bb = bb > last ? last : bb;
         };
@@ -482,16 +490,17 @@ __global__ void __launch_bounds__(256) k_ring(const InstDesc *__restrict__ D, co
         for (int d = 0; d < N; d++) idx[d] = I.idx[d][node];
         auto rf = [&](int Lp, int d, int &a, int &bb) {
             const int i = idx[d];
-            if (Lp <= L) {
-                const int sh = L - Lp;
+            const int ld = dlev(I, L, d), lpd = dlev(I, Lp, d);
+            if (lpd <= ld) {
+                const int sh = ld - lpd;
                 a = ((i + (1 << sh) - 1) >> sh) - 1;
                 bb = (i + 1) >> sh;
             } else {
-                const int sh = Lp - L;
+                const int sh = lpd - ld;
                 a = (i << sh) - 1;
                 bb = (i + 1) << sh;
             }
-            const int last = (I.n0[d] << Lp) - 1;
+            const int last = (I.n0[d] << lpd) - 1;
             a = a < 0 ? 0 : a;
             bb = bb > last ? last : bb;
         };
@@ -539,7 +548,8 @@ cudaError_t launch_ring(int n, int ring, const InstDesc *D, const WorkList &w, c
 
 // New live list of an instance: its kept, unsplit cells in slot order, then
 // the children of its boundary cells (child c of the r-th boundary cell at
-// n_keep + 2^n r + c, node id n_nodes + 2^n r + c, idx 2 idx + bit).
+// n_keep + nc r + c, node id n_nodes + nc r + c; nc = 2^n children with idx
+// 2 idx + bit on every dimension, or 2 halving dimension (level mod n)).
 template <int N>
 __global__ void __launch_bounds__(256) k_split(const InstDesc *__restrict__ D, const Range *__restrict__ R, int nr,
                                                const uint8_t *__restrict__ alive, const uint8_t *__restrict__ bnd,
@@ -557,19 +567,22 @@ __global__ void __launch_bounds__(256) k_split(const InstDesc *__restrict__ D, c
         return;
     }
     const int r = (int)(v & 0xffffffffll);
-    const int first = si.n_nodes + (r << N);
+    const int nc = nchildren(I);
+    const int first = si.n_nodes + r * nc;
     const int L = I.lvl[node];
+    const int ds = L % N;                          // the dimension a cycled split halves
     int idx[N];
 #pragma unroll
     for (int d = 0; d < N; d++) idx[d] = I.idx[d][node];
-    for (int c = 0; c < (1 << N); c++) {
+    for (int c = 0; c < nc; c++) {
         const int cn = first + c;
         I.lvl[cn] = (uint8_t)(L + 1);
         I.state[cn] = ST_ALIVE;
         I.child[cn] = -1;
 #pragma unroll
-        for (int d = 0; d < N; d++) I.idx[d][cn] = 2 * idx[d] + ((c >> (N - 1 - d)) & 1);
-        si.new_live[si.n_keep + (r << N) + c] = cn;
+        for (int d = 0; d < N; d++)
+            I.idx[d][cn] = I.split ? (d == ds ? 2 * idx[d] + c : idx[d]) : 2 * idx[d] + ((c >> (N - 1 - d)) & 1);
+        si.new_live[si.n_keep + r * nc + c] = cn;
     }
     I.state[node] = ST_SPLIT;
     I.child[node] = first;
@@ -589,6 +602,134 @@ cudaError_t launch_split(int n, const InstDesc *D, const WorkList &w, const uint
     }
     return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Edges of the cells of problems refined by cycled bisection: one thread per
+// cell descends the subdivision tree over the hull of its controls' boxes
+// (descend() with each level's index range per dimension) and gives every
+// leaf the mask of the controls whose box it meets: at level L with s_d =
+// halvings(Lf, d) - halvings(L, d), leaf idx meets control u iff on every
+// dimension (idx + 1) << s_d >= c_u and idx << s_d <= f_u (c, f the finest
+// decisions). A live leaf with a non-empty mask is an edge (target, mask); a
+// removed one sets the removed-leaf flag of those controls. FILL = false:
+// edges per cell, targets per pair, in-degrees, pair-edge total; FILL = true:
+// the edges at coff[cell] and the reverse edges at rcur[target]++.
+// ---------------------------------------------------------------------------
+template <int N, bool FILL>
+__global__ void __launch_bounds__(128) k_sedges(const InstDesc *__restrict__ D, const Range *__restrict__ R, int nr,
+                                                const CellGraph g)
+{
+    RANGE_HEAD(128)
+    const int64_t s = rg.first + local;
+    const int ls = (int)(s - I.slot_base);
+    const int nu = I.nu;
+    const int64_t p0 = I.pair_base + (int64_t)ls * nu;
+    // the hull of the live controls' finest boxes
+    int cmin[N], fmax[N];
+    uint32_t live = 0;
+#pragma unroll
+    for (int d = 0; d < N; d++) { cmin[d] = INT_MAX; fmax[d] = INT_MIN; }
+    for (int u = 0; u < nu; u++) {
+        const int64_t p = p0 + u;
+        if (g.pflag[p] & PF_NONFINITE) continue;
+        bool nonempty = true;
+        int c[N], f[N];
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            c[d] = g.rng[p * 2 * MAXN + d];
+            f[d] = g.rng[p * 2 * MAXN + N + d];
+            int a, b;
+            level_range(c[d], f[d], dshift(I, 0, d), I.n0[d], a, b);
+            nonempty = nonempty && a <= b;
+        }
+        if (!nonempty) continue;
+        live |= 1u << u;
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            cmin[d] = min(cmin[d], c[d]);
+            fmax[d] = max(fmax[d], f[d]);
+        }
+    }
+    int32_t cnt[32];
+    for (int u = 0; u < nu; u++) cnt[u] = 0;
+    uint32_t touched = 0;
+    int64_t w = FILL ? g.coff[s] : 0;
+    int32_t nent = 0;
+    if (live) {
+        auto rf = [&](int L, int d, int &a, int &b) {
+            level_range(cmin[d], fmax[d], dshift(I, L, d), I.n0[d] << dlev(I, L, d), a, b);
+        };
+        auto visit = [&](int node, uint8_t st) {
+            const int L = I.lvl[node];
+            uint32_t m = 0;
+            for (int u = 0; u < nu; u++) {
+                if (!((live >> u) & 1u)) continue;
+                const int64_t p = p0 + u;
+                bool in = true;
+#pragma unroll
+                for (int d = 0; d < N; d++) {
+                    const int sh = dshift(I, L, d), i = I.idx[d][node];
+                    in = in && ((i + 1) << sh) >= g.rng[p * 2 * MAXN + d] && (i << sh) <= g.rng[p * 2 * MAXN + N + d];
+                }
+                m |= (uint32_t)in << u;
+            }
+            if (!m) return true;
+            if (st == ST_DEAD) {
+                touched |= m;
+                return true;
+            }
+            const int t = I.slot[node];
+            if (FILL) {
+                const unsigned long long r = atomicAdd(&g.rcur[t], 1ull);
+                if (w < g.ecap && r < (unsigned long long)g.ecap) {
+                    g.cent[w] = t;
+                    g.cmask[w] = m;
+                    g.rsrc[r] = (int32_t)s;
+                    g.rmask[r] = m;
+                } else {
+                    atomicExch(g.err, GIS_EBOUNDS);
+                }
+                w++;
+            } else {
+                atomicAdd(&g.rcnt[t], 1);
+                for (uint32_t mm = m; mm; mm &= mm - 1) cnt[__ffs(mm) - 1]++;
+            }
+            nent++;
+            return true;
+        };
+        if (descend<N>(I, rf, visit)) atomicExch(g.err, GIS_EBOUNDS);
+    }
+    if (!FILL) {
+        unsigned long long pe = 0;
+        for (int u = 0; u < nu; u++) {
+            g.pcnt[p0 + u] = cnt[u];
+            pe += (unsigned long long)cnt[u];
+            if ((touched >> u) & 1u) g.pflag[p0 + u] |= PF_TOUCH_DEAD;
+        }
+        g.ccnt[s] = nent;
+        if (pe) atomicAdd(g.pair_edges, pe);
+    }
+}
+
+cudaError_t launch_sedges(bool fill, int n, const InstDesc *D, const WorkList &w, const CellGraph &g, cudaStream_t st)
+{
+    if (w.n_blocks == 0) return cudaSuccess;
+    dim3 gr((unsigned)w.n_blocks), b(128);
+#define SE_CASE(NN)                                                                                    \
+    case NN:                                                                                           \
+        if (fill) k_sedges<NN, true><<<gr, b, 0, st>>>(D, w.d_ranges, w.n_ranges, g);                  \
+        else k_sedges<NN, false><<<gr, b, 0, st>>>(D, w.d_ranges, w.n_ranges, g);                      \
+        note_launch();                                                                                 \
+        break;
+    switch (n) {
+        SE_CASE(1) SE_CASE(2) SE_CASE(3) SE_CASE(4)
+    default: return cudaErrorInvalidValue;
+    }
+#undef SE_CASE
+    return cudaGetLastError();
+}
+
+int sedges_cells_per_block() { return 128; }
 
 // ---------------------------------------------------------------------------
 // Exports.

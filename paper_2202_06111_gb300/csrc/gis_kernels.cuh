@@ -39,6 +39,9 @@ bool lattice_tile(int n, int k, const int32_t *n0, int32_t *tile, int max_cells 
 cudaError_t launch_prop32_siblings(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st);
 int sibling_groups(int n, int k);
 cudaError_t launch_prop64(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st);
+// interval enclosure of each whole cell's image (FP64, one thread per pair)
+cudaError_t launch_prop_iv(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st);
+int prop_iv_threads();
 int prop_pairs_per_block(int lanes);
 int prop_block_threads();
 // binning: decisions at the finest level, band check, recheck queue
@@ -186,6 +189,11 @@ cudaError_t launch_cedges(bool fill, int n, int depth, const InstDesc *D, int64_
                           const int64_t *cbase, const ChunkWork &cw, unsigned long long *grab, const int32_t *cinst,
                           const CellGraph &g, const StageArgs &sa, cudaStream_t st);
 int cedges_cells_per_block();     // cells per block of k_cinc
+// edges of the cells of cycled-bisection problems: a thread per cell
+// descends the tree (count: fill = false; fill after the scans)
+cudaError_t launch_sedges(bool fill, int n, const InstDesc *D, const WorkList &wcells, const CellGraph &g,
+                          cudaStream_t st);
+int sedges_cells_per_block();
 cudaError_t launch_cprune_init(const InstDesc *D, const WorkList &wslots, const uint8_t *pflag, const int32_t *pcnt,
                                int32_t *pc, unsigned long long *pk, uint8_t *pinfo, uint32_t *vmask, uint8_t *alive,
                                int32_t *frontier0, uint32_t *sizes, cudaStream_t st);
@@ -209,6 +217,36 @@ struct CPruneArgs {
     int64_t spin_limit;
 };
 cudaError_t launch_cprune(const CPruneArgs &a, int64_t n_slots, cudaStream_t st);
+// Def. 3 read literally (gis_scc.cu): the largest strongly connected
+// components of one problem's cell graph (slots s0 .. s1) inside the OUTER
+// fixed point, and the cells with a path into them.
+struct SccArgs {
+    int64_t s0, s1;
+    const int64_t *coff;         // forward cell edges (global slots)
+    const int32_t *cent;
+    const int64_t *roff;         // reverse cell edges
+    const int32_t *rsrc;
+    int32_t *color;              // per slot: part (>= 0), -1 outside every part
+    uint8_t *kin;                // per slot: in the OUTER fixed point
+    uint32_t *mark;              // per slot: closure bits (1 forward, 2 backward, 4 kept)
+    int32_t *din, *dout;         // trimming: predecessors / successors inside the part
+    int32_t *front[2];           // frontiers of the trimming and of forward closures
+    int32_t *bfront[2];          // frontiers of backward closures
+    // control block, cleared by the caller before each phase:
+    uint32_t *sizes, *sizes2;    // [3] rotating frontier sizes (forward / backward)
+    uint32_t *bar, *bar2;        // grid barrier counters
+    int32_t *err;                // GIS_ETIMEOUT when a bounded wait ran out
+    unsigned long long *cnt;     // [8]: 0 cells of K, 1 trimmed, 2 pivot self-loop,
+                                 // 4..7 component / forward / backward / rest
+    unsigned long long *key;     // pivot key: (in + 1)(out + 1) << 32 | ~slot
+    int64_t spin_limit;
+};
+cudaError_t launch_scc_colors(const SccArgs &a, const uint8_t *alive, cudaStream_t st);
+cudaError_t launch_scc_trim(const SccArgs &a, int32_t c, cudaStream_t st);
+cudaError_t launch_scc_closures(const SccArgs &a, int32_t c, cudaStream_t st);
+cudaError_t launch_scc_split(const SccArgs &a, int32_t c, int32_t cS, int32_t cF, int32_t cB, cudaStream_t st);
+cudaError_t launch_scc_keep(const SccArgs &a, const uint8_t *is_best, int32_t ncolors, uint8_t *alive,
+                            cudaStream_t st);
 cudaError_t launch_cexport(const InstDesc *D, const WorkList &w8, const int64_t *coff, const int32_t *cent,
                            const uint32_t *cmask, const int64_t *poff, int32_t *tgt, cudaStream_t st);
 // mark removed, classify boundary, split

@@ -324,7 +324,7 @@ __device__ __forceinline__ void decide_exact(const InstDesc &I, int e, double v,
     const double at = fabs(t);
     if (!(fabs(t - rint(t)) > at * 8.8817841970012523e-16) || !(at > 1e-290))
         t = __ddiv_rn(num, I.w64[I.Lf][d]);
-    const double Nf = (double)((int64_t)I.n0[d] << I.Lf);
+    const double Nf = (double)((int64_t)I.n0[d] << I.dl[I.Lf][d]);
     if (e < N) {
         out = (int32_t)fmin(fmax(ceil(t), 0.0), Nf + 1.0);
         inx = inx && (v >= I.lo[d]);
@@ -343,7 +343,7 @@ __device__ __forceinline__ bool decide_approx(const InstDesc &I, int e, float a,
     const int d = e % N;
     const float tA = (a - I.lo32[d]) * I.invwf32[d];
     const float tB = (b - I.lo32[d]) * I.invwf32[d];
-    const float Nf = (float)(I.n0[d] << I.Lf);
+    const float Nf = (float)(I.n0[d] << I.dl[I.Lf][d]);
     float k0 = ceilf(__fsub_rd(tA, I.tmargin[d])), k1 = floorf(__fadd_ru(tB, I.tmargin[d]));
     k0 = fmaxf(k0, 0.0f);
     k1 = fminf(k1, Nf);

@@ -111,12 +111,9 @@ void gis_server::run()
     try {
         CK(cudaSetDevice(device));
         CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-        if (opt.max_device_bytes <= 0) {
-            size_t fr = 0, tot = 0;
-            CK(cudaMemGetInfo(&fr, &tot));
-            opt.max_device_bytes = (int64_t)(fr * 2 / 5);
-        }
         E = make_engine();
+        if (opt.max_device_bytes <= 0)           // free memory, the library pool's unused part included
+            opt.max_device_bytes = (int64_t)(E->free_bytes() * 2 / 5);
     } catch (const Error &e) {
         std::lock_guard<std::mutex> lk(mu);
         init_status = e.st;
@@ -132,6 +129,11 @@ void gis_server::run()
         cv.notify_all();
     }
     const int max_active = opt.max_active > 0 ? opt.max_active : 1024;
+    // test hook: GIS_TEST_FAIL_ALLOC=k makes the k-th device allocation of the
+    // first step that advances several requests fail (once), to exercise the
+    // out-of-memory re-queue below without exhausting the device
+    int64_t inject = -1;
+    if (const char *f = std::getenv("GIS_TEST_FAIL_ALLOC")) inject = std::atoll(f);
     while (!stop) {
         // admission
         std::vector<Pending> admit;
@@ -156,7 +158,7 @@ void gis_server::run()
             pd.req.controls.u = pd.u.data();
             try {
                 const int i = E->add(pd.req.dyn, pd.req.grid, pd.req.controls, pd.req.rule, pd.req.precision,
-                                     pd.req.band, pd.req.levels);
+                                     pd.req.band, pd.req.levels, pd.req.enclosure, pd.req.split);
                 ticket_of[i] = pd.ticket;
                 est_of[i] = pd.est;
                 active.push_back(i);
@@ -180,6 +182,10 @@ void gis_server::run()
             stats.active = (int64_t)active.size();
         }
         // one level of every active request
+        if (inject >= 0 && active.size() >= 2) {
+            E->mem.fail_after = inject;
+            inject = -1;
+        }
         try {
             E->build_graph(active);
             E->prune();
@@ -299,7 +305,8 @@ gis_status gis_server_submit(gis_server *s, const gis_request *req, uint64_t *ti
     // the same checks gis_create applies, before queueing
     try {
         Inst probe;
-        setup_inst(probe, req->dyn, req->grid, req->controls, req->rule, req->precision, req->band, req->levels);
+        setup_inst(probe, req->dyn, req->grid, req->controls, req->rule, req->precision, req->band, req->levels,
+                   req->enclosure, req->split);
     } catch (const Error &e) {
         set_last_error(e.msg);
         return e.st;

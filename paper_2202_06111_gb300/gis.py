@@ -23,8 +23,10 @@ LIB_PATH = os.path.join(_PKG, "libgis.so")
 MAXN, NPARAM = 4, 32
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ECANCELLED, EBOUNDS, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7, -8
 DYN_IDS = {"linmap": 0, "vdp": 1, "cstr_dl": 2, "cartpole": 3, "cstr_paper": 4}
-RULES = {"inner": 0, "outer": 1}
+RULES = {"inner": 0, "outer": 1, "scc": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1}
+ENCLOSURES = {"samples": 0, "interval": 1}
+SPLITS = {"all": 0, "cycled": 1}
 PAIR_INX, PAIR_TOUCH_DEAD, PAIR_NONFINITE = 1, 2, 4
 CELL_KEPT, CELL_BOUNDARY = 1, 2
 
@@ -53,7 +55,8 @@ class gis_options(C.Structure):
     _fields_ = [("rule", C.c_int32), ("precision", C.c_int32), ("band", C.c_double),
                 ("lanes_per_pair", C.c_int32), ("timing", C.c_int32), ("max_device_bytes", C.c_int64),
                 ("round_limit", C.c_int64), ("enclosure_store", C.c_int32), ("fixed_shapes", C.c_int32),
-                ("split_ring", C.c_int32), ("reserved", C.c_int32)]
+                ("split_ring", C.c_int32), ("enclosure", C.c_int32), ("split", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class gis_cell(C.Structure):
@@ -73,7 +76,9 @@ _STAT_FIELDS = [("finest_level", C.c_int32), ("level", C.c_int32), ("n_nodes", C
                 ("fill_bytes", C.c_double), ("transpose_bytes", C.c_double), ("cum_launches", C.c_int64),
                 ("cum_recheck_samples", C.c_int64), ("n_cell_edges", C.c_int64), ("cum_cell_edges", C.c_int64),
                 ("cum_recheck_fp64", C.c_int64), ("lattice_tile_cells", C.c_int32),
-                ("sibling_parents", C.c_int32), ("cum_tune_launches", C.c_int64)]
+                ("sibling_parents", C.c_int32), ("cum_tune_launches", C.c_int64), ("stage_cap", C.c_int64),
+                ("stage_edges", C.c_int64), ("stage_lost_chunks", C.c_int64), ("free_bytes_at_stage", C.c_int64),
+                ("scc_passes", C.c_int64)]
 
 
 class gis_stats(C.Structure):
@@ -82,7 +87,8 @@ class gis_stats(C.Structure):
 
 class gis_request(C.Structure):
     _fields_ = [("dyn", gis_dynamics), ("grid", gis_grid), ("controls", gis_controls), ("levels", C.c_int32),
-                ("rule", C.c_int32), ("precision", C.c_int32), ("band", C.c_double)]
+                ("rule", C.c_int32), ("precision", C.c_int32), ("band", C.c_double), ("enclosure", C.c_int32),
+                ("split", C.c_int32)]
 
 
 class gis_result(C.Structure):
@@ -130,6 +136,11 @@ SIGNATURES = {
     "gis_server_destroy": (None, [C.c_void_p]),
     "gis_prune_graph_noalloc": (C.c_int32, [C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                             C.c_int32, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p]),
+    "gis_shard_create": (C.c_int32, [C.POINTER(C.c_void_p), C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "gis_shard_round": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]),
+    "gis_shard_kept": (C.c_int32, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]),
+    "gis_shard_destroy": (None, [C.c_void_p]),
 }
 
 _lib = None
@@ -207,6 +218,8 @@ def options(p: dict | None = None, **kw) -> gis_options:
             o.band = p["band"]
         if "split_ring" in p:
             o.split_ring = int(p["split_ring"])
+        o.enclosure = ENCLOSURES[p.get("enclosure", "samples")]
+        o.split = SPLITS[p.get("split", "all")]
     for k, v in kw.items():
         setattr(o, k, v)
     return o
@@ -327,6 +340,8 @@ def batch_solve(problems: list[dict], stream: int | None = None, want_cells: boo
         r.rule = RULES[p.get("rule", "inner")]
         r.precision = PRECISIONS[p.get("precision", "fp32")]
         r.band = p.get("band", 0.0)
+        r.enclosure = ENCLOSURES[p.get("enclosure", "samples")]
+        r.split = SPLITS[p.get("split", "all")]
         if want_cells:
             cap = p.get("cells_cap", 2 * int(np.prod(p["n0"])) * (1 + r.levels))
             buf = (gis_cell * cap)()
@@ -363,6 +378,8 @@ def _request(p: dict, keep: list) -> gis_request:
     r.rule = RULES[p.get("rule", "inner")]
     r.precision = PRECISIONS[p.get("precision", "fp32")]
     r.band = p.get("band", 0.0)
+    r.enclosure = ENCLOSURES[p.get("enclosure", "samples")]
+    r.split = SPLITS[p.get("split", "all")]
     return r
 
 

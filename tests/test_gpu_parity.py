@@ -184,3 +184,108 @@ def test_nonfinite_images(gis, precision, rule):
     two = W.problem(W.linmap([[0.5]], [[1e308]]), [-1.0], [1.0], 8, 2, [[0.0], [2.0]], 1.0, 0, rule=rule,
                     precision=precision)
     assert run_both(gis, two, 1)[0][0] == 8
+
+
+# Def. 3 read literally (rule "scc"): the largest cycle-holding strongly
+# connected components and their ancestors, level by level against the
+# oracle's Tarjan search; the three problems of the OUTER / SCC / INNER
+# comparison with their kept counts.
+@pytest.mark.parametrize("case,levels,kept", [
+    (dict(W.vdp_64(), rule="scc"), 0, 3986),
+    (dict(W.cstr_256(levels=2, n0=64), rule="scc"), 2, 4517),
+    (dict(W.cstr_paper_problem(n0=(16, 16), levels=3), rule="scc", precision="fp64"), 3, 423),
+])
+def test_scc_rule_table(gis, case, levels, kept):
+    res = run_both(gis, case, levels)
+    assert res[-1][0] == kept
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_scc_rule_cartpole(gis, precision):
+    run_both(gis, dict(W.cartpole_48(levels=2, n0=7), rule="scc", precision=precision), 2)
+
+
+@pytest.mark.parametrize("A,B,u", [
+    ([[0.0, -1.0], [1.0, 0.0]], [[0.0], [0.0]], [[0.0]]),               # rotation: one ring per radius
+    ([[0.5, 0.0], [0.0, 0.5]], [[1.0], [0.0]], [[-0.3], [0.0], [0.3]]),  # contraction: DAG into the centre
+    ([[1.1, 0.3], [-0.2, 0.9]], [[0.5], [0.2]], [[-0.5], [0.5]]),
+])
+def test_scc_rule_linear_maps(gis, A, B, u):
+    prob = W.problem(W.linmap(A, B), [-1.0, -1.0], [1.0, 1.0], [11, 9], 3, u, 1.0, 0, rule="scc",
+                     precision="fp32")
+    run_both(gis, prob, 2)
+
+
+def test_scc_rule_doubling_and_empty(gis):
+    """x+ = 2x + u keeps all of X in both other rules; x+ = 2x + 3 has no
+    cycle at all, so nothing is kept."""
+    dbl = W.problem(W.linmap([[2.0]], [[1.0]]), [-1.0], [1.0], 16, 2, [[-0.5], [0.0], [0.5]], 1.0, 0, rule="scc",
+                    precision="fp32")
+    run_both(gis, dbl, 2)
+    none = W.problem(W.linmap([[2.0]], [[1.0]]), [-1.0], [1.0], 16, 2, [[3.0]], 1.0, 0, rule="scc",
+                     precision="fp32")
+    assert run_both(gis, none, 1)[0][0] == 0
+
+
+# The interval enclosure of each whole cell's image (Def. 1 with F(B_i)
+# enclosed, Prop. 1(iii)): the GPU's interval arithmetic and the oracle's
+# define every end by the same operations, so graphs and kept sets are equal
+# bit for bit on every dynamics id.
+@pytest.mark.parametrize("rule", ["inner", "outer"])
+@pytest.mark.parametrize("case,levels", [
+    (W.problem(W.vdp(1.0), [-3, -3], [3, 3], 24, 3, W.controls_grid(-1, 1, 5), 0.1, 10), 2),
+    (W.cstr_256(levels=2, n0=29), 2),
+    (W.cartpole_48(levels=1, n0=6), 1),
+    (W.cstr_paper_problem(n0=(12, 12)), 2),
+    (W.problem(W.linmap([[0.1, 1.0], [-0.9, -0.2]], [[0.0], [1.0]]), [-1, -1], [1, 1], 10, 2,
+               W.controls_grid(-0.5, 0.5, 3), 0.3, 3), 2),
+], ids=["vdp", "cstr_dl", "cartpole", "cstr_paper", "linear_rk4"])
+def test_interval_enclosure(gis, case, levels, rule):
+    run_both(gis, dict(case, enclosure="interval", rule=rule), levels)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_interval_enclosure_discrete_maps(gis, n):
+    rng = np.random.default_rng(20 + n)
+    A = (np.eye(n) * 0.9 + rng.uniform(-0.2, 0.2, (n, n))).tolist()
+    B = rng.uniform(-0.5, 0.5, (n, 1)).tolist()
+    prob = W.problem(W.linmap(A, B), [-1.0] * n, [1.0] * n, [9, 7, 5, 3][:n], 2, W.controls_grid(-0.4, 0.3, 3),
+                     1.0, 0, rule="outer")
+    prob["enclosure"] = "interval"
+    run_both(gis, prob, 2 if n < 4 else 1)
+
+
+# Cycled bisection (Sec. 2.1: a cell splits into 2 children, halving
+# dimension (depth mod n)): per-dimension depths in the widths, decisions,
+# descents, boundary rule and split, level by level against the oracle.
+@pytest.mark.parametrize("rule", ["inner", "outer"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cycled_cstr(gis, rule, precision):
+    run_both(gis, dict(W.cstr_256(levels=4, n0=23), rule=rule, precision=precision, split="cycled"), 4)
+
+
+def test_cycled_vdp_rings_and_scc(gis):
+    p = W.problem(W.vdp(1.0), [-3, -3], [3, 3], 20, 3, W.controls_grid(-1, 1, 5), 0.1, 10, rule="outer")
+    run_both(gis, dict(p, split="cycled", split_ring=1), 4)
+    run_both(gis, dict(p, split="cycled", rule="scc"), 3)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cycled_cartpole(gis, precision):
+    """Five refinements take every dimension of the 4-D state through one
+    cycle and start the next."""
+    run_both(gis, dict(W.cartpole_48(levels=5, n0=4), rule="outer", precision=precision, split="cycled"), 5)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_cycled_linear_maps(gis, n):
+    rng = np.random.default_rng(40 + n)
+    A = (np.eye(n) * 1.05 + rng.uniform(-0.2, 0.2, (n, n))).tolist()
+    B = rng.uniform(-0.5, 0.5, (n, 1)).tolist()
+    prob = W.problem(W.linmap(A, B), [-1.3] * n, [1.7] * n, [9, 7, 5][:n], 3, W.controls_grid(-0.4, 0.3, 4), 1.0,
+                     0, rule="outer", precision="fp32")
+    run_both(gis, dict(prob, split="cycled"), 4)
+
+
+def test_cycled_interval(gis):
+    run_both(gis, dict(W.cstr_256(levels=3, n0=17), rule="outer", enclosure="interval", split="cycled"), 3)
