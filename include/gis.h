@@ -189,10 +189,12 @@ typedef struct {
     double ms_prop, ms_bin, ms_recheck, ms_count, ms_scan, ms_fill, ms_transpose,
            ms_prune, ms_classify, ms_split, ms_other;
     /* cumulative algorithmic work of the propagation kernels */
-    double prop_flops;      /* FP32: operations of the certified (midpoint-radius)
-                               samples propagated, counted from the ball formulas
-                               (an FMA counts 2); FP64 plain: the model
-                               expressions' operations                           */
+    double prop_flops;      /* executed operations of propagation: FP32 plain
+                               samples plus one interval-error bound per region
+                               (estimated at three ball operations per operation),
+                               or, with GIS_PROP_BALL=1, the certified ball samples
+                               counted from the ball formulas (an FMA counts 2);
+                               FP64 plain: the model expressions' operations     */
     double graph_bytes;     /* algorithmic bytes of count + fill + transpose       */
     double prune_bytes;     /* algorithmic bytes of the prune                      */
     double count_bytes, fill_bytes, transpose_bytes; /* the parts of graph_bytes   */
@@ -228,22 +230,28 @@ void gis_default_options(gis_options *out);
 gis_status gis_create(gis_ctx **out, const gis_dynamics *dyn, const gis_grid *grid,
                       const gis_controls *controls, const gis_options *opt, void *stream);
 
-/* Steps 1-2 on the current covering: propagate the new cells, bin the image
- * boxes, recheck near-line extremes in FP64, count / scan / fill the CSR
- * graph over (cell, control) pairs and its transpose.                        */
+/* Steps 1-2 on the current covering -- the symbolic image of Def. 1 (Sec. 2.2,
+ * Eq. 2-3) with the one-step maps of Eq. 1 batched on the GPU (Sec. 3.2):
+ * propagate the new cells, bin the image boxes, recheck near-line extremes in
+ * FP64, count / scan / fill the CSR graph over (cell, control) pairs and its
+ * transpose.                                                                  */
 gis_status gis_build_graph(gis_ctx *ctx);
 
-/* Step 3: greatest fixed point of the pruning rule on the current graph.
+/* Step 3: greatest fixed point of the pruning rule on the current graph
+ * (Sec. 2.3: Def. 2-5, Prop. 1; GIS_RULE_SCC: Def. 3 read literally).
  * n_kept / n_rounds may be NULL. ESTATE without a graph; ETIMEOUT if the
  * round limit is reached.                                                      */
 gis_status gis_prune(gis_ctx *ctx, int64_t *n_kept, int32_t *n_rounds);
 
-/* Step 4: classify the kept cells and split every boundary cell into 2^n
- * children; removed cells stay removed. ESTATE if the graph is not pruned.   */
+/* Step 4: classify the kept cells (Sec. 3.1.1, Alg. 1 in its exact form,
+ * Remark 1) and split every boundary cell into 2^n children (Sec. 2.1; two
+ * with GIS_SPLIT_CYCLED); removed cells stay removed. ESTATE if the graph is
+ * not pruned.                                                                 */
 gis_status gis_subdivide(gis_ctx *ctx, int64_t *n_split);
 
-/* The whole loop: `levels` times build / prune / subdivide, then a final
- * build / prune. Synchronises the stream at the end.                          */
+/* The whole loop of Sec. 3.1 (adaptive subdivision, Alg. 1): `levels` times
+ * build / prune / subdivide, then a final build / prune. Synchronises the
+ * stream at the end.                                                          */
 gis_status gis_solve(gis_ctx *ctx, int32_t levels);
 
 /* The live cells of the current covering (after a prune: with kept flags).
@@ -297,7 +305,8 @@ typedef struct {
     int64_t cells_cap;
 } gis_result;
 
-/* Solve `n` requests together: every phase of every level runs as one launch
+/* Solve `n` requests together (the GPU batching of Sec. 3.2, over many
+ * problems): every phase of every level runs as one launch
  * over the union of all requests' cells (requests at different levels
  * proceed together; finished ones drop out). res[i].cells (if not NULL)
  * receives up to cells_cap kept cells of request i. `opt` supplies timing,

@@ -13,7 +13,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgis.so")
 
-SOURCES = ["gis_prop.cu", "gis_graph.cu", "gis_cgraph.cu", "gis_engine.cu", "gis_server.cu", "gis_noalloc.cu", "gis_scc.cu", "gis_interval.cu", "gis_shard.cu"]
+SOURCES = ["gis_prop.cu", "gis_graph.cu", "gis_cgraph.cu", "gis_engine.cu", "gis_server.cu", "gis_noalloc.cu", "gis_scc.cu", "gis_interval.cu", "gis_shard.cu", "gis_lmap.cu", "gis_propf.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-O2", "-I", INCLUDE, "-I", CSRC]

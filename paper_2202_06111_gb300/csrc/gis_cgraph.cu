@@ -97,8 +97,9 @@ __global__ void __launch_bounds__(256) k_cchunks(const InstDesc *__restrict__ D,
     if (s >= NL) return;                           // whole warp
     const InstDesc &I = D[cinst[s]];
     if (lane < I.nu) pcnt[I.pair_base + (s - I.slot_base) * I.nu + lane] = 0;
-    if (s - I.slot_base < I.n_carry || I.split) {  // edges from the previous level's, or
-        if (lane == 0) nch[s] = 0;                 // (cycled bisection) the per-cell descent
+    if (s - I.slot_base < I.n_carry || I.split ||  // edges from the previous level's, the per-cell
+        (I.lm_node && I.lvl[I.live[s - I.slot_base]] == I.Lf)) {   // descent (cycled), or the leaf map
+        if (lane == 0) nch[s] = 0;
         return;
     }
     const int n = I.n, Lf = I.Lf;

@@ -137,6 +137,9 @@ __device__ __forceinline__ DB dbdiv(DB a, DB b)
 }
 
 // ---- exp ---------------------------------------------------------------------
+// Additive range reduction after Cody & Waite (W. J. Cody, W. Waite, "Software
+// Manual for the Elementary Functions", 1980): the constant is split so that
+// k times its leading part is exact, then a Taylor polynomial.
 // exp(x) = 2^k exp(r), k = rint(x / ln 2), r = x - k ln 2 with
 // ln 2 = LN2_1 + LN2_2 + LN2_3 + O(2^-69) (LN2_1 has 16 significant bits, so
 // k LN2_1 is exact for |k| <= 256); |r| <= 0.35. exp(r) is its Taylor
@@ -197,6 +200,7 @@ __device__ __forceinline__ DB dbexp(DB a)
 }
 
 // ---- sin, cos ------------------------------------------------------------------
+// The same Cody & Waite reduction, by multiples of pi/2:
 // x = k pi/2 + r, k = rint(x 2/pi), |k| <= 256, pi/2 = PIO2_1 + PIO2_2 + PIO2_3
 // + O(2^-68) (PIO2_1 has 16 significant bits); |r| <= 0.79. sin r = r S(r^2),
 // cos r = C(r^2): Taylor terms up to r^19 / r^18, terms from r^8 on in FP32

@@ -54,6 +54,9 @@ struct InstDesc {
     int32_t split;              // GIS_SPLIT_ALL_DIMS | GIS_SPLIT_CYCLED
     double dt;                  // sampling period
     double praw[GIS_NPARAM];    // the parameters as given (the interval models use them)
+    int32_t *lm_node;           // leaf map (null: none): per finest cell its leaf's node
+    uint8_t *lm_lvl;            // ... and that leaf's level
+    int64_t lm_stride[MAXN];    // linear index of finest cell x = sum x_d lm_stride[d]
     float p32[GIS_NPARAM];      // derived constants for the FP32 model
     float pr32[GIS_NPARAM];     // their radii: |p32 - exact value|, rounded up
     double p64[GIS_NPARAM];     // derived constants for the FP64 model (same ops as the definition)
@@ -280,6 +283,14 @@ struct DynVdp {       // p: mu
         const Ball a = bfma(bneg(x[0]), x[0], bexact(1.0f));
         dx[1] = bfma(bmul(M.P(0), a), x[1], bsub(u[0], x[0]));
     }
+    // the same operation sequence over an arithmetic policy A (gis_ie.cuh)
+    template <class A, class PP>
+    __device__ static __forceinline__ void rhsT(const PP &P, int, const typename A::T *x,
+                                                const typename A::T *u, typename A::T *dx) {
+        dx[0] = x[1];
+        const typename A::T a = A::fma(A::neg(x[0]), x[0], A::cst(1.0f));
+        dx[1] = A::fma(A::mul(P[0], a), x[1], A::sub(u[0], x[0]));
+    }
     __device__ static __forceinline__ void rhs64(const double *p, const double *x, const double *u, double *dx) {
         dx[0] = x[1];
         double a = __dsub_rn(1.0, __dmul_rn(x[0], x[0]));
@@ -296,6 +307,15 @@ struct DynCstrDl {    // p32: Da, B, beta, 1/gamma   p64: Da, B, beta, gamma
         const Ball r = bmul(bmul(M.P(0), bsub(bexact(1.0f), x[0])), e);
         dx[0] = bsub(r, x[0]);
         dx[1] = bsub(bfma(M.P(1), r, bneg(x[1])), bmul(M.P(2), bsub(x[1], u[0])));
+    }
+    template <class A, class PP>
+    __device__ static __forceinline__ void rhsT(const PP &P, int, const typename A::T *x,
+                                                const typename A::T *u, typename A::T *dx) {
+        using T = typename A::T;
+        const T e = A::exp(A::template div<false>(x[1], A::fma(x[1], P[3], A::cst(1.0f))));
+        const T r = A::mul(A::mul(P[0], A::sub(A::cst(1.0f), x[0])), e);
+        dx[0] = A::sub(r, x[0]);
+        dx[1] = A::sub(A::fma(P[1], r, A::neg(x[1])), A::mul(P[2], A::sub(x[1], u[0])));
     }
     __device__ static __forceinline__ void rhs64(const double *p, const double *x, const double *u, double *dx) {
         double e = exp(__ddiv_rn(x[1], __dadd_rn(1.0, __ddiv_rn(x[1], p[3]))));
@@ -316,6 +336,20 @@ struct DynCartpole {  // p32: g, 1/tot, pml, l, mp, 4/3    p64: mc, mp, l, g, to
         const Ball thacc = bdiv<true>(bfma(M.P(0), s, bneg(bmul(c, temp))), den);
         dx[0] = x[1];
         dx[1] = bfma(bmul(bmul(bneg(M.P(2)), thacc), c), M.P(1), temp);
+        dx[2] = x[3];
+        dx[3] = thacc;
+    }
+    template <class A, class PP>
+    __device__ static __forceinline__ void rhsT(const PP &P, int, const typename A::T *x,
+                                                const typename A::T *u, typename A::T *dx) {
+        using T = typename A::T;
+        T s, c;
+        A::sincos(x[2], &s, &c);
+        const T temp = A::mul(A::fma(A::mul(A::mul(P[2], x[3]), x[3]), s, u[0]), P[1]);
+        const T den = A::mul(P[3], A::fma(A::mul(A::mul(A::neg(P[4]), c), c), P[1], P[5]));
+        const T thacc = A::template div<true>(A::fma(P[0], s, A::neg(A::mul(c, temp))), den);
+        dx[0] = x[1];
+        dx[1] = A::fma(A::mul(A::mul(A::neg(P[2]), thacc), c), P[1], temp);
         dx[2] = x[3];
         dx[3] = thacc;
     }
@@ -342,6 +376,14 @@ struct DynCstrPaper { // p32: qV, cAf, Tf, ER, a1, a2, ln k0   p64: qV, cAf, Tf,
         dx[0] = bfma(M.P(0), bsub(M.P(1), x[0]), bneg(rate));
         dx[1] = bfma(M.P(0), bsub(M.P(2), x[1]), bfma(M.P(4), rate, bmul(M.P(5), bsub(u[0], x[1]))));
     }
+    template <class A, class PP>
+    __device__ static __forceinline__ void rhsT(const PP &P, int, const typename A::T *x,
+                                                const typename A::T *u, typename A::T *dx) {
+        using T = typename A::T;
+        const T rate = A::mul(A::exp(A::sub(P[6], A::template div<false>(P[3], x[1]))), x[0]);
+        dx[0] = A::fma(P[0], A::sub(P[1], x[0]), A::neg(rate));
+        dx[1] = A::fma(P[0], A::sub(P[2], x[1]), A::fma(P[4], rate, A::mul(P[5], A::sub(u[0], x[1]))));
+    }
     __device__ static __forceinline__ void rhs64(const double *p, const double *x, const double *u, double *dx) {
         double rate = __dmul_rn(__dmul_rn(p[4], exp(__ddiv_rn(-p[3], x[1]))), x[0]);
         dx[0] = __dsub_rn(__dmul_rn(p[0], __dsub_rn(p[1], x[0])), rate);
@@ -362,6 +404,18 @@ struct DynLin {
 #pragma unroll
             for (int j = 0; j < NN; j++) acc = bfma(M.P(i * NN + j), x[j], acc);
             for (int j = 0; j < M.m; j++) acc = bfma(M.P(NN * NN + i * M.m + j), u[j], acc);
+            dx[i] = acc;
+        }
+    }
+    template <class A, class PP>
+    __device__ static __forceinline__ void rhsT(const PP &P, int m, const typename A::T *x,
+                                                const typename A::T *u, typename A::T *dx) {
+#pragma unroll
+        for (int i = 0; i < NN; i++) {
+            typename A::T acc = A::cst(0.0f);
+#pragma unroll
+            for (int j = 0; j < NN; j++) acc = A::fma(P[i * NN + j], x[j], acc);
+            for (int j = 0; j < m; j++) acc = A::fma(P[NN * NN + i * m + j], u[j], acc);
             dx[i] = acc;
         }
     }
@@ -417,6 +471,42 @@ __device__ __forceinline__ void stepB(const MB &M, const Ball *x0, const Ball *u
 #pragma unroll
         for (int d = 0; d < N; d++)
             x[d] = bfma(M.h6, bfma(bexact(2.0f), badd(k2[d], k3[d]), badd(k1[d], k4[d])), x[d]);
+    }
+#pragma unroll
+    for (int d = 0; d < N; d++) y[d] = x[d];
+}
+
+// One sampling period over an arithmetic policy A, in stepB's operation
+// sequence: P[i] the model constants as A's values, h / hh / h6 the steps.
+template <class DY, class A, class PP>
+__device__ __forceinline__ void stepT(const PP &P, int m, int substeps, typename A::T h,
+                                      typename A::T hh, typename A::T h6, const typename A::T *x0,
+                                      const typename A::T *u, typename A::T *y)
+{
+    using T = typename A::T;
+    constexpr int N = DY::N;
+    T x[N];
+#pragma unroll
+    for (int d = 0; d < N; d++) x[d] = x0[d];
+    if (substeps == 0) {
+        DY::template rhsT<A, PP>(P, m, x, u, y);
+        return;
+    }
+    for (int s = 0; s < substeps; s++) {
+        T k1[N], k2[N], k3[N], k4[N], xt[N];
+        DY::template rhsT<A, PP>(P, m, x, u, k1);
+#pragma unroll
+        for (int d = 0; d < N; d++) xt[d] = A::fma(hh, k1[d], x[d]);
+        DY::template rhsT<A, PP>(P, m, xt, u, k2);
+#pragma unroll
+        for (int d = 0; d < N; d++) xt[d] = A::fma(hh, k2[d], x[d]);
+        DY::template rhsT<A, PP>(P, m, xt, u, k3);
+#pragma unroll
+        for (int d = 0; d < N; d++) xt[d] = A::fma(h, k3[d], x[d]);
+        DY::template rhsT<A, PP>(P, m, xt, u, k4);
+#pragma unroll
+        for (int d = 0; d < N; d++)
+            x[d] = A::fma(h6, A::fma(A::cst(2.0f), A::add(k2[d], k3[d]), A::add(k1[d], k4[d])), x[d]);
     }
 #pragma unroll
     for (int d = 0; d < N; d++) y[d] = x[d];

@@ -212,6 +212,11 @@ struct Inst {
     int nu = 0, rule = 0, precision = 0, levels = 0;
     int enclosure = 0, split = 0;
     int nchild() const { return split == GIS_SPLIT_CYCLED ? 2 : 1 << dyn.n; }
+    // leaf map of the finest grid (null when the problem uses the tree walk)
+    int32_t *lm_node = nullptr;
+    uint8_t *lm_lvl = nullptr;
+    size_t c_lm = 0;
+    int64_t lm_cells = 0;
     double band = 1e-2;
     int S = 1;
     // host view of device state
@@ -323,6 +328,20 @@ inline double sample_ball_flops(const Inst &I)
     else per += I.dyn.substeps * (4.0 * ball_flops_rhs(I) + 55.0 * n + 10.0 * n);
     return per;
 }
+
+// FP32 operations of one plain sample (the model's operations per right-hand
+// side, RK4's 13n per substep, 2n for the lattice point), and an estimate of
+// one region's interval-error bound (each operation carries an interval and
+// an error term: about three ball operations' work)
+inline double sample_plain_flops(const Inst &I)
+{
+    const int n = I.dyn.n;
+    double per = 2.0 * n;
+    if (I.dyn.substeps == 0) per += model_flops_rhs(I);
+    else per += I.dyn.substeps * (4.0 * model_flops_rhs(I) + 13.0 * n);
+    return per;
+}
+inline double ie_flops(const Inst &I) { return 3.0 * sample_ball_flops(I); }
 
 inline int ipow(int b, int e)
 {
@@ -520,6 +539,15 @@ inline void fill_desc(Inst &I)
     }
     D.enclosure = I.enclosure;
     D.split = I.split;
+    D.lm_node = I.lm_cells > 0 ? I.lm_node : nullptr;
+    D.lm_lvl = I.lm_cells > 0 ? I.lm_lvl : nullptr;
+    {
+        int64_t st = 1;
+        for (int d = MAXN - 1; d >= 0; d--) {
+            D.lm_stride[d] = d < n ? st : 0;
+            if (d < n) st *= (int64_t)I.grid.root_cells[d] << D.dl[I.Lf][d];
+        }
+    }
     D.dt = I.dyn.dt;
     for (int i = 0; i < GIS_NPARAM; i++) D.praw[i] = I.dyn.params[i];
     D.fresh0 = I.n_live - I.n_fresh;
@@ -861,6 +889,8 @@ struct Engine {
         mem.free(I.live[0]); mem.free(I.live[1]);
         mem.free(I.box32); mem.free(I.exact); mem.free(I.bx); mem.free(I.bxi); mem.free(I.bx_n);
         mem.free(I.u32); mem.free(I.ur32); mem.free(I.u64); mem.free(I.udd);
+        mem.free(I.lm_node); mem.free(I.lm_lvl);
+        I.lm_node = nullptr; I.lm_lvl = nullptr; I.c_lm = 0; I.lm_cells = 0;
         I.lvl = I.state = nullptr;
         I.child = I.slot = I.live[0] = I.live[1] = nullptr;
         I.box32 = nullptr; I.exact = nullptr; I.bx = nullptr; I.bxi = I.bx_n = nullptr;
@@ -1150,6 +1180,60 @@ struct Engine {
         if (changed) upload_desc();
     }
 
+    // Leaf maps of the finest grids (gis_lmap.cu), with GIS_LEAF_MAP=1, for the
+    // problems whose map fits: 5 bytes per finest cell, all problems together
+    // within a fifth of the free memory and 32 GB. Their fresh cells at the
+    // finest level find their edges through it; the others, and every coarser
+    // cell, walk the tree. Off by default: on the 48^4 cart-pole the two map
+    // enumerations (count and fill) took longer than the staged walk and its
+    // place pass (719 against 634 ms of edge construction per solve).
+    void build_leaf_maps(const std::vector<int> &ids)
+    {
+        const char *env = std::getenv("GIS_LEAF_MAP");
+        const bool on = env && std::atoi(env) != 0;
+        double budget = 0;
+        bool queried = false;
+        std::map<int, std::vector<RangeSpec>> nodes;
+        for (int i : ids) {
+            Inst &I = *inst[i];
+            I.lm_cells = 0;
+            if (!on || I.split == GIS_SPLIT_CYCLED || I.n_live - I.n_carry <= 0) continue;
+            int64_t T = 1;
+            bool fits = true;
+            for (int d = 0; d < I.dyn.n; d++) {
+                T *= (int64_t)I.grid.root_cells[d] << (I.split == GIS_SPLIT_CYCLED ? 0 : I.Lf);
+                fits = fits && T < ((int64_t)1 << 40);
+            }
+            if (!fits) continue;
+            const double bytes = 5.0 * (double)T;
+            if ((size_t)T > I.c_lm && bytes > 256.0 * (1 << 20)) {
+                if (!queried) {
+                    budget = std::min(0.2 * (double)free_bytes(), 32.0 * (1ull << 30));
+                    queried = true;
+                }
+                if (bytes > budget) continue;
+                budget -= bytes;
+            }
+            if ((size_t)T > I.c_lm) {
+                mem.free(I.lm_node);
+                mem.free(I.lm_lvl);
+                I.lm_node = nullptr;
+                I.lm_lvl = nullptr;
+                I.c_lm = 0;
+                I.lm_node = (int32_t *)mem.alloc((size_t)T * sizeof(int32_t));
+                I.lm_lvl = (uint8_t *)mem.alloc((size_t)T);
+                I.c_lm = (size_t)T;
+            }
+            I.lm_cells = T;
+            nodes[I.dyn.n].push_back({I.tix, 0, I.n_nodes});
+        }
+        if (nodes.empty()) return;
+        upload_desc();
+        timer.begin(PH_COUNT);
+        for (auto &kv : nodes) CK(launch_lmap(kv.first, d_desc, make_work(kv.second, 256), st));
+        timer.end();
+    }
+
     void build_graph(const std::vector<int> &ids)
     {
         LaunchScope ls_(cum);
@@ -1187,13 +1271,15 @@ struct Engine {
         mem.ensure(oslot, c_oslot, NLs);
         CK(launch_cgather(d_desc, ws, cps, cinst, s2n, oslot, st));
         timer.end();
+        build_leaf_maps(ids);
 
         if (!opt.fixed_shapes) tune_shapes(ids);
 
         // propagation of new cells, grouped by (dynamics, n, precision, lanes)
         timer.begin(PH_PROP);
+        const bool plain = prop_plain();
         last_new_pairs = 0;
-        std::map<std::tuple<int, int, int, int>, std::vector<RangeSpec>> groups;
+        std::map<std::tuple<int, int, int, int>, std::vector<RangeSpec>> groups, bgroups;
         for (int i : ids) {
             Inst &I = *inst[i];
             if (I.n_fresh == 0) continue;
@@ -1213,7 +1299,9 @@ struct Engine {
                     (void)T;
                 }
                 groups[{I.dyn.dyn_id, I.dyn.n, I.precision, 0}].push_back({I.tix, 0, tiles * I.nu});
-                cum.prop_flops += sample_ball_flops(I) * points * I.nu;
+                bgroups[{I.dyn.dyn_id, I.dyn.n, I.precision, 0}].push_back({I.tix, I.pair_base, I.n_live * I.nu});
+                cum.prop_flops += plain ? (sample_plain_flops(I) * points + ie_flops(I) * (double)I.n_live) * I.nu
+                                        : sample_ball_flops(I) * points * I.nu;
             } else if (kind == PK_SIBLING) {
                 // fresh children of split cells: shared points among siblings
                 // (lanes = -1 marks the sibling kernel; items are runs of
@@ -1221,18 +1309,22 @@ struct Engine {
                 const int64_t ng = I.n_fresh >> I.dyn.n;
                 const int64_t blocks = (ng + I.desc.sib_groups - 1) / I.desc.sib_groups;
                 groups[{I.dyn.dyn_id, I.dyn.n, I.precision, -1}].push_back({I.tix, 0, blocks * I.nu});
+                bgroups[{I.dyn.dyn_id, I.dyn.n, I.precision, -1}].push_back({I.tix, 0, ng * I.nu});
                 double pts = 1;
                 for (int d = 0; d < I.dyn.n; d++) pts *= 2.0 * (I.grid.k_samples - 1) + 1;
-                cum.prop_flops += sample_ball_flops(I) * pts * (double)ng * I.nu;
+                cum.prop_flops += plain ? (sample_plain_flops(I) * pts + ie_flops(I)) * (double)ng * I.nu
+                                        : sample_ball_flops(I) * pts * (double)ng * I.nu;
             } else if (I.enclosure == GIS_ENCLOSE_INTERVAL) {
                 // interval enclosure of each whole cell (lanes = -2 marks it)
                 groups[{I.dyn.dyn_id, I.dyn.n, I.precision, -2}].push_back({I.tix, first, I.n_fresh * I.nu});
             } else {
                 const int lanes = I.precision == GIS_FP64_PLAIN ? 1 : lanes_for(I);
                 groups[{I.dyn.dyn_id, I.dyn.n, I.precision, lanes}].push_back({I.tix, first, I.n_fresh * I.nu});
-                cum.prop_flops += (I.precision == GIS_FP64_PLAIN ? pair_flops(I)
-                                                                 : sample_ball_flops(I) * I.S) *
-                                  (double)(I.n_fresh * I.nu);
+                bgroups[{I.dyn.dyn_id, I.dyn.n, I.precision, lanes}].push_back({I.tix, first, I.n_fresh * I.nu});
+                const double per = I.precision == GIS_FP64_PLAIN ? pair_flops(I)
+                                   : plain ? sample_plain_flops(I) * I.S + lanes * ie_flops(I)
+                                           : sample_ball_flops(I) * I.S;
+                cum.prop_flops += per * (double)(I.n_fresh * I.nu);
             }
             last_new_pairs += I.n_fresh * I.nu;
             I.pairs_prop += I.n_fresh * I.nu;
@@ -1241,6 +1333,9 @@ struct Engine {
         for (auto &g : groups) {
             const int dyn = std::get<0>(g.first), n = std::get<1>(g.first), prec = std::get<2>(g.first);
             const int lanes = std::get<3>(g.first);
+            if (plain && prec == GIS_FP32_RECHECK && lanes != -2)   // the regions' bounds first
+                CK(launch_propf_bound(lanes == 0 ? 0 : lanes == -1 ? 1 : 2, dyn, n, d_desc,
+                                      make_work(bgroups[g.first], 128), st));
             if (lanes == -2) {
                 CK(launch_prop_iv(dyn, n, d_desc, make_work(g.second, prop_iv_threads()), st));
             } else if (prec == GIS_FP64_PLAIN) {
@@ -1346,13 +1441,23 @@ struct Engine {
         int64_t seg_base[MAXN + 2] = {0};
         for (int i : ids) seg_base[inst[i]->dyn.n + 1] += inst[i]->n_live;
         for (int n = 1; n <= MAXN; n++) seg_base[n + 1] += seg_base[n];
-        int seg_depth[MAXN + 1] = {0};             // deepest finest level per dimension
-        for (int i : ids) seg_depth[inst[i]->dyn.n] = std::max(seg_depth[inst[i]->dyn.n], inst[i]->Lf);
+        int seg_depth[MAXN + 1] = {0};             // deepest finest level per dimension among walked problems
+        for (int i : ids)                          // (cycled problems' cells take the per-cell descent)
+            if (inst[i]->split != GIS_SPLIT_CYCLED)
+                seg_depth[inst[i]->dyn.n] = std::max(seg_depth[inst[i]->dyn.n], inst[i]->Lf);
         auto carried = [&](int n) {
             std::vector<RangeSpec> r;
             for (int i : ids)
                 if (inst[i]->dyn.n == n && inst[i]->n_carry > 0)
                     r.push_back({inst[i]->tix, inst[i]->slot_base, inst[i]->n_carry});
+            return r;
+        };
+        // fresh cells of problems with a leaf map (k_medges takes those at the finest level)
+        auto mapped = [&](int n) {
+            std::vector<RangeSpec> r;
+            for (int i : ids)
+                if (inst[i]->dyn.n == n && inst[i]->lm_cells > 0)
+                    r.push_back({inst[i]->tix, inst[i]->slot_base + inst[i]->n_carry, inst[i]->n_live - inst[i]->n_carry});
             return r;
         };
         // cells of cycled-bisection problems: the per-cell descent
@@ -1382,7 +1487,7 @@ struct Engine {
         // GIS_STAGE_PER_CELL (tests) fixes the edges per walked cell, with no
         // slack (0: no staging)
         int64_t walked = NL;
-        for (int i : ids) walked -= inst[i]->n_carry;
+        for (int i : ids) walked -= inst[i]->lm_cells > 0 ? inst[i]->n_live : inst[i]->n_carry;
         StageArgs sa{};
         const char *fixed_per = std::getenv("GIS_STAGE_PER_CELL");
         const double fper = fixed_per ? std::atof(fixed_per) : -1.0;
@@ -1462,6 +1567,8 @@ struct Engine {
                 if (!r.empty()) CK(launch_cinc(false, n, d_desc, make_work(r, cedges_cells_per_block()), g, prev, st));
                 const auto c = cycled(n);
                 if (!c.empty()) CK(launch_sedges(false, n, d_desc, make_work(c, sedges_cells_per_block()), g, st));
+                const auto m = mapped(n);
+                if (!m.empty()) CK(launch_medges(false, n, d_desc, make_work(m, medges_cells_per_block()), g, st));
             }
             timer.end();
             timer.begin(PH_SCAN);
@@ -1541,6 +1648,8 @@ struct Engine {
             if (!r.empty()) CK(launch_cinc(true, n, d_desc, make_work(r, cedges_cells_per_block()), g, prev, st));
             const auto c = cycled(n);
             if (!c.empty()) CK(launch_sedges(true, n, d_desc, make_work(c, sedges_cells_per_block()), g, st));
+            const auto m = mapped(n);
+            if (!m.empty()) CK(launch_medges(true, n, d_desc, make_work(m, medges_cells_per_block()), g, st));
         }
         have_prev = true;
         prev_NL = NL;

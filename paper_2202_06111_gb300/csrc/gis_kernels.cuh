@@ -39,6 +39,14 @@ bool lattice_tile(int n, int k, const int32_t *n0, int32_t *tile, int max_cells 
 cudaError_t launch_prop32_siblings(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st);
 int sibling_groups(int n, int k);
 cudaError_t launch_prop64(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st);
+// FP32 propagation of plain samples with one rounding bound per region
+// (kind 0: lattice tiles, 1: sibling lattices, 2: per pair with `lanes`);
+// the launchers above route here unless GIS_PROP_BALL=1
+cudaError_t launch_propf(int kind, int dyn, int n, int lanes, const InstDesc *D, const WorkList &w, cudaStream_t st);
+// the regions' bounds, launched before launch_propf: items are the pairs of
+// the range (kinds 0 and 2) or (sibling group, control) (kind 1)
+cudaError_t launch_propf_bound(int kind, int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st);
+bool prop_plain();
 // interval enclosure of each whole cell's image (FP64, one thread per pair)
 cudaError_t launch_prop_iv(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st);
 int prop_iv_threads();
@@ -194,6 +202,12 @@ int cedges_cells_per_block();     // cells per block of k_cinc
 cudaError_t launch_sedges(bool fill, int n, const InstDesc *D, const WorkList &wcells, const CellGraph &g,
                           cudaStream_t st);
 int sedges_cells_per_block();
+// the leaf map of each problem (wnodes: its nodes 0 .. n_nodes), and the edges
+// of its fresh cells at the finest level through it (count / fill)
+cudaError_t launch_lmap(int n, const InstDesc *D, const WorkList &wnodes, cudaStream_t st);
+cudaError_t launch_medges(bool fill, int n, const InstDesc *D, const WorkList &wcells, const CellGraph &g,
+                          cudaStream_t st);
+int medges_cells_per_block();
 cudaError_t launch_cprune_init(const InstDesc *D, const WorkList &wslots, const uint8_t *pflag, const int32_t *pcnt,
                                int32_t *pc, unsigned long long *pk, uint8_t *pinfo, uint32_t *vmask, uint8_t *alive,
                                int32_t *frontier0, uint32_t *sizes, cudaStream_t st);

@@ -13,6 +13,7 @@
 //             FP64 image (k_rc_dd, one sample per thread), which settles
 //             nearly every decision; the rest in FP64 (k_rc_fp64)
 #include <cfloat>
+#include <cstdlib>
 
 #include "gis_dd_models.cuh"
 #include "gis_kernels.cuh"
@@ -790,6 +791,16 @@ __global__ void __launch_bounds__(256) k_rc_final(const InstDesc *__restrict__ D
 // dispatch
 // ---------------------------------------------------------------------------
 int prop_pairs_per_block(int lanes) { return PROP_THREADS / lanes; }
+
+// The FP32 propagation launches take the plain-sample kernels with one bound
+// per region (gis_propf.cu) unless GIS_PROP_BALL=1 selects the per-sample
+// ball kernels below (both give the same decisions; the ball arithmetic stays
+// in use for the recheck's candidates).
+bool prop_plain()
+{
+    const char *e = std::getenv("GIS_PROP_BALL");
+    return !(e && std::atoi(e) != 0);
+}
 int prop_block_threads() { return PROP_THREADS; }
 
 template <class DY>
@@ -810,6 +821,7 @@ static cudaError_t prop32_g(int lanes, const InstDesc *D, const WorkList &w, cud
 cudaError_t launch_prop32(int dyn, int n, int lanes, const InstDesc *D, const WorkList &w, cudaStream_t st)
 {
     if (w.n_blocks == 0) return cudaSuccess;
+    if (prop_plain()) return launch_propf(2, dyn, n, lanes, D, w, st);
     switch (dyn) {
     case GIS_DYN_VDP: return prop32_g<DynVdp>(lanes, D, w, st);
     case GIS_DYN_CSTR_DL: return prop32_g<DynCstrDl>(lanes, D, w, st);
@@ -946,6 +958,7 @@ static cudaError_t prop32_sib_l(const InstDesc *D, const WorkList &w, cudaStream
 cudaError_t launch_prop32_siblings(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st)
 {
     if (w.n_blocks == 0) return cudaSuccess;
+    if (prop_plain()) return launch_propf(1, dyn, n, 0, D, w, st);
     switch (dyn) {
     case GIS_DYN_VDP: return prop32_sib_l<DynVdp>(D, w, st);
     case GIS_DYN_CSTR_DL: return prop32_sib_l<DynCstrDl>(D, w, st);
@@ -984,6 +997,7 @@ static cudaError_t prop32_lat_l(const InstDesc *D, const WorkList &w, cudaStream
 cudaError_t launch_prop32_lattice(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st)
 {
     if (w.n_blocks == 0) return cudaSuccess;
+    if (prop_plain()) return launch_propf(0, dyn, n, 0, D, w, st);
     switch (dyn) {
     case GIS_DYN_VDP: return prop32_lat_l<DynVdp>(D, w, st);
     case GIS_DYN_CSTR_DL: return prop32_lat_l<DynCstrDl>(D, w, st);

@@ -1,0 +1,505 @@
+// gis_propf.cu -- propagation with plain FP32 samples and one rounding bound
+// per region (gis_ie.cuh): the same three work shapes as the ball kernels of
+// gis_prop.cu (first-build lattice tiles, sibling lattices of fresh
+// children, per pair), the same outputs (box32: per extreme an interval
+// holding its exact value; exact / bxi marks), so the binning and the recheck
+// tiers take them unchanged.
+//
+// Per region (a cell, or the parent box of a sibling group) and control, the
+// RK4 period runs once in interval-error arithmetic over the region's lattice
+// coordinates (an interval of the exact values, and the rounding error of the
+// FP32 lattice points); its error bounds E_d hold for every FP32 sample of the
+// region. Each lattice point is then propagated once in plain FP32, and an
+// extreme over a cell's samples lies within E_d (widened by 2^-20 of itself
+// and 1e-37 for the FP64 evaluation's own rounding, as the ball kernels widen)
+// of the computed extreme. A region whose bound cannot be formed, or a sample
+// that is not finite, marks its pairs for the FP64 tiers.
+#include <cfloat>
+
+#include "gis_ie.cuh"
+#include "gis_kernels.cuh"
+
+namespace gis {
+
+namespace {
+
+constexpr int PF_THREADS = 256;
+constexpr int PF_POINTS = 4096;                    // lattice points per block, divided by n
+
+struct ParF {                                      // the model constants as plain floats
+    const float *p;
+    __device__ __forceinline__ float operator[](int i) const { return p[i]; }
+};
+struct ParIE {                                     // ... and as intervals with their radii
+    const float *p, *pr;
+    __device__ __forceinline__ IE operator[](int i) const { return ie_param(p[i], pr[i]); }
+};
+
+// Lattice coordinate d of the points x = lo + w t, t = idx + j/(k-1) in
+// [tmin, tmax] (t >= 0), at level L: the interval of the exact values and the
+// error of the FP32 point fma(w32, fl(idx + frac32), lo32), fr the largest
+// radius of the fractions.
+__device__ __forceinline__ IE ie_lattice(const InstDesc &I, int L, int d, float tmin, float tmax, float fr)
+{
+    const float w = I.w32[L][d], wr = I.wr32[L][d], lo = I.lo32[d], lor = I.lor32[d];
+    IE x;
+    x.lo = __fmaf_rd(__fsub_rd(w, wr), tmin, __fsub_rd(lo, lor));
+    x.hi = __fmaf_ru(__fadd_ru(w, wr), tmax, __fadd_ru(lo, lor));
+    const float rt = __fmaf_ru(__fadd_ru(tmax, fr), IE_U, __fadd_ru(fr, IE_ETA));   // |t^ - t|
+    float e = __fmaf_ru(w, rt, __fmaf_ru(tmax, wr, __fmaf_ru(wr, rt, lor)));
+    e = __fmaf_ru(__fadd_ru(ie_mag(x), e), IE_U, __fadd_ru(e, IE_ETA));
+    x.e = e;
+    return x;
+}
+
+__device__ __forceinline__ float point32(const InstDesc &I, int L, int d, int idx, int j)
+{
+    return fmaf(I.w32[L][d], (float)idx + I.frac32[j], I.lo32[d]);
+}
+
+__device__ __forceinline__ float largest_frac_radius(const InstDesc &I)
+{
+    float r = 0.0f;
+    for (int j = 0; j < I.k; j++) r = fmaxf(r, I.fracr32[j]);
+    return r;
+}
+
+// E_d of one region (per output dimension, widened for the FP64 evaluation);
+// false if a bound could not be formed
+template <class DY>
+__device__ __forceinline__ bool region_bound(const InstDesc &I, const float *sp, const float *spr, int u,
+                                             const IE *x, float *E)
+{
+    constexpr int N = DY::N;
+    IE uu[MAXN], y[N];
+    for (int j = 0; j < I.m; j++) uu[j] = ie_param(I.u32[u * I.m + j], I.ur32[u * I.m + j]);
+    const ParIE P{sp, spr};
+    stepT<DY, OpsIE>(P, I.m, I.substeps, ie_param(I.h32, I.hr32), ie_param(I.hh32, I.hhr32),
+                     ie_param(I.h6_32, I.h6r32), x, uu, y);
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < N; d++) {
+        const float e = y[d].e;
+        ok = ok && e <= FLT_MAX;
+        E[d] = __fmaf_ru(e, 9.5367432e-07f, __fadd_ru(e, IE_ETA));
+    }
+    return ok;
+}
+
+template <class DY>
+__device__ __forceinline__ void step_plain(const InstDesc &I, const float *sp, int u, const float *x, float *y)
+{
+    float uu[MAXN];
+    for (int j = 0; j < I.m; j++) uu[j] = I.u32[u * I.m + j];
+    const ParF P{sp};
+    stepT<DY, OpsF>(P, I.m, I.substeps, I.h32, I.hh32, I.h6_32, x, uu, y);
+}
+
+// box32 of pair q from the computed extremes and E
+template <int N>
+__device__ __forceinline__ void store_box(const InstDesc &I, int64_t q, const float *mn, const float *mx,
+                                          const float *E, bool bad)
+{
+#pragma unroll
+    for (int d = 0; d < N; d++) {
+        I.box32[q * 4 * N + 2 * d] = __fsub_rd(mn[d], E[d]);
+        I.box32[q * 4 * N + 2 * d + 1] = __fadd_ru(mn[d], E[d]);
+        I.box32[q * 4 * N + 2 * (N + d)] = __fsub_rd(mx[d], E[d]);
+        I.box32[q * 4 * N + 2 * (N + d) + 1] = __fadd_ru(mx[d], E[d]);
+    }
+    I.exact[q] = bad ? EX_NF32 : 0;
+    if (!I.bx_dense) I.bxi[q] = -1;               // compact store: no entry yet
+}
+
+// ---- per pair: G lanes share a pair's k^n samples; the region of the bound
+// (k_bound) is the cell itself
+template <class DY, int G>
+__global__ void __launch_bounds__(PF_THREADS) k_propf(const InstDesc *__restrict__ D, const Range *__restrict__ R,
+                                                      int nr)
+{
+    constexpr int N = DY::N;
+    constexpr int PPB = PF_THREADS / G;
+    __shared__ int s_r;
+    __shared__ float s_p[GIS_NPARAM], s_pr[GIS_NPARAM];
+    if (threadIdx.x == 0) s_r = find_range(R, nr, blockIdx.x);
+    __syncthreads();
+    const Range rg = R[s_r];
+    const InstDesc &I = D[rg.inst];
+    if (threadIdx.x < GIS_NPARAM) {
+        s_p[threadIdx.x] = I.p32[threadIdx.x];
+        s_pr[threadIdx.x] = I.pr32[threadIdx.x];
+    }
+    __syncthreads();
+    const int64_t local = (int64_t)(blockIdx.x - rg.block_start) * PPB + threadIdx.x / G;
+    const bool valid = local < rg.count;
+    const int lane = threadIdx.x & (G - 1);
+    float mn[N], mx[N], E[N];
+#pragma unroll
+    for (int d = 0; d < N; d++) {
+        mn[d] = INFINITY;
+        mx[d] = -INFINITY;
+        E[d] = 0.0f;
+    }
+    int bad = 0;
+    int64_t q = 0;
+    if (valid) {
+        const int64_t lp = rg.first + local - I.pair_base;
+        const int ls = (int)(lp / I.nu);
+        const int u = (int)(lp - (int64_t)ls * I.nu);
+        const int node = I.live[ls];
+        const int L = I.lvl[node];
+        int32_t idx[N];
+#pragma unroll
+        for (int d = 0; d < N; d++) idx[d] = I.idx[d][node];
+        q = (int64_t)node * I.nu + u;
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            E[d] = I.box32[q * 4 * N + d];           // the bound kernel's E
+            bad |= !(E[d] <= FLT_MAX);
+        }
+        for (int s = lane; s < I.S; s += G) {
+            float x[N], y[N];
+            int r = s;
+#pragma unroll
+            for (int d = 0; d < N; d++) {
+                x[d] = point32(I, L, d, idx[d], r % I.k);
+                r /= I.k;
+            }
+            step_plain<DY>(I, s_p, u, x, y);
+#pragma unroll
+            for (int d = 0; d < N; d++) {
+                bad |= !(fabsf(y[d]) <= FLT_MAX);
+                mn[d] = fminf(mn[d], y[d]);
+                mx[d] = fmaxf(mx[d], y[d]);
+            }
+        }
+    }
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            mn[d] = fminf(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], off, G));
+            mx[d] = fmaxf(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], off, G));
+        }
+        bad |= __shfl_xor_sync(0xffffffffu, bad, off, G);
+    }
+    __syncwarp();                                 // every lane has read E before it is overwritten
+    if (valid && lane == 0) store_box<N>(I, q, mn, mx, E, bad != 0);
+}
+
+// ---- first build: lattice points of a tile of root cells, each once; each
+// cell takes its own bound (k_bound)
+template <class DY>
+__global__ void __launch_bounds__(PF_THREADS) k_propf_lat(const InstDesc *__restrict__ D,
+                                                          const Range *__restrict__ R, int nr)
+{
+    constexpr int N = DY::N;
+    constexpr int PMAX = PF_POINTS / N;
+    __shared__ int s_r;
+    __shared__ float s_p[GIS_NPARAM], s_pr[GIS_NPARAM];
+    __shared__ float s_y[PMAX * N];
+    if (threadIdx.x == 0) s_r = find_range(R, nr, blockIdx.x);
+    __syncthreads();
+    const Range rg = R[s_r];
+    const InstDesc &I = D[rg.inst];
+    if (threadIdx.x < GIS_NPARAM) {
+        s_p[threadIdx.x] = I.p32[threadIdx.x];
+        s_pr[threadIdx.x] = I.pr32[threadIdx.x];
+    }
+    const int64_t item = rg.first + (blockIdx.x - rg.block_start);   // one item per block
+    const int u = (int)(item % I.nu);
+    int64_t t = item / I.nu;
+    const int k1 = I.k - 1;
+    int c0[N], nc[N], np[N];
+    int P = 1, C = 1;
+#pragma unroll
+    for (int d = N - 1; d >= 0; d--) {
+        const int ti = (int)(t % I.ntile[d]);
+        t /= I.ntile[d];
+        c0[d] = ti * I.tile[d];
+        nc[d] = min(I.tile[d], I.n0[d] - c0[d]);
+        np[d] = nc[d] * k1 + 1;
+        P *= np[d];
+        C *= nc[d];
+    }
+    __syncthreads();
+    for (int pt = threadIdx.x; pt < P; pt += PF_THREADS) {
+        float x[N], y[N];
+        int r = pt;
+#pragma unroll
+        for (int d = N - 1; d >= 0; d--) {
+            const int g = c0[d] * k1 + r % np[d];
+            r /= np[d];
+            const int idx = min(g / k1, I.n0[d] - 1);
+            x[d] = point32(I, 0, d, idx, g - idx * k1);
+        }
+        step_plain<DY>(I, s_p, u, x, y);
+#pragma unroll
+        for (int d = 0; d < N; d++) s_y[pt * N + d] = y[d];
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += PF_THREADS) {
+        int lc[N];
+        int r = c, node = 0;
+#pragma unroll
+        for (int d = N - 1; d >= 0; d--) {
+            lc[d] = r % nc[d];
+            r /= nc[d];
+        }
+#pragma unroll
+        for (int d = 0; d < N; d++) node = node * I.n0[d] + c0[d] + lc[d];
+        const int64_t q = (int64_t)node * I.nu + u;
+        float E[N], mn[N], mx[N];
+        bool bad = false;
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            E[d] = I.box32[q * 4 * N + d];             // the bound kernel's E for this cell
+            bad = bad || !(E[d] <= FLT_MAX);
+            mn[d] = INFINITY;
+            mx[d] = -INFINITY;
+        }
+        for (int s = 0; s < I.S; s++) {
+            int rs = s, pt = 0;
+            int jd[N];
+#pragma unroll
+            for (int d = 0; d < N; d++) {
+                jd[d] = rs % I.k;
+                rs /= I.k;
+            }
+#pragma unroll
+            for (int d = 0; d < N; d++) pt = pt * np[d] + lc[d] * k1 + jd[d];
+#pragma unroll
+            for (int d = 0; d < N; d++) {
+                const float y = s_y[pt * N + d];
+                bad = bad || !(fabsf(y) <= FLT_MAX);
+                mn[d] = fminf(mn[d], y);
+                mx[d] = fmaxf(mx[d], y);
+            }
+        }
+        store_box<N>(I, q, mn, mx, E, bad);
+    }
+}
+
+// ---- fresh children: the (2 (k-1) + 1)^n points of each parent's lattice
+// once; the region of the bound (k_bound) is the parent's box (the children's
+// union)
+template <class DY>
+__global__ void __launch_bounds__(PF_THREADS) k_propf_sib(const InstDesc *__restrict__ D,
+                                                          const Range *__restrict__ R, int nr)
+{
+    constexpr int N = DY::N;
+    constexpr int NC = 1 << N;
+    constexpr int PMAX = PF_POINTS / N;
+    constexpr int GMAX = PF_THREADS;
+    __shared__ int s_r;
+    __shared__ float s_p[GIS_NPARAM], s_pr[GIS_NPARAM];
+    __shared__ float s_y[PMAX * N];
+    __shared__ float s_E[GMAX * N];
+    __shared__ uint8_t s_bad[GMAX];
+    if (threadIdx.x == 0) s_r = find_range(R, nr, blockIdx.x);
+    __syncthreads();
+    const Range rg = R[s_r];
+    const InstDesc &I = D[rg.inst];
+    if (threadIdx.x < GIS_NPARAM) {
+        s_p[threadIdx.x] = I.p32[threadIdx.x];
+        s_pr[threadIdx.x] = I.pr32[threadIdx.x];
+    }
+    const int64_t item = rg.first + (blockIdx.x - rg.block_start);   // one item per block
+    const int u = (int)(item % I.nu);
+    const int64_t ngroups = (I.n_live - I.fresh0) >> N;
+    const int64_t g0 = (item / I.nu) * I.sib_groups;
+    const int G = (int)min((int64_t)I.sib_groups, ngroups - g0);
+    const int k1 = I.k - 1, side = 2 * k1 + 1;
+    int pts1 = 1;
+#pragma unroll
+    for (int d = 0; d < N; d++) pts1 *= side;
+    __syncthreads();
+    // the parents' bounds, which the bound kernel left in child 0's slot
+    for (int g = threadIdx.x; g < G; g += PF_THREADS) {
+        const int node0 = I.live[I.fresh0 + ((g0 + g) << N)];   // child 0: index 2 * parent index
+        const int64_t q0 = (int64_t)node0 * I.nu + u;
+        bool bad = false;
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            const float e = I.box32[q0 * 4 * N + d];
+            bad = bad || !(e <= FLT_MAX);
+            s_E[g * N + d] = e;
+        }
+        s_bad[g] = bad;
+    }
+    for (int pt = threadIdx.x; pt < G * pts1; pt += PF_THREADS) {
+        const int g = pt / pts1;
+        int r = pt - g * pts1;
+        const int node0 = I.live[I.fresh0 + ((g0 + g) << N)];
+        const int L = I.lvl[node0];
+        float x[N], y[N];
+#pragma unroll
+        for (int d = N - 1; d >= 0; d--) {
+            const int gd = r % side;
+            r /= side;
+            const int b = min(gd / k1, 1);
+            x[d] = point32(I, L, d, I.idx[d][node0] + b, gd - b * k1);
+        }
+        step_plain<DY>(I, s_p, u, x, y);
+#pragma unroll
+        for (int d = 0; d < N; d++) s_y[pt * N + d] = y[d];
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < G * NC; c += PF_THREADS) {
+        const int g = c / NC, cc = c - g * NC;
+        const int node = I.live[I.fresh0 + ((g0 + g) << N) + cc];
+        float mn[N], mx[N], E[N];
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            mn[d] = INFINITY;
+            mx[d] = -INFINITY;
+            E[d] = s_E[g * N + d];
+        }
+        bool bad = s_bad[g] != 0;
+        for (int s = 0; s < I.S; s++) {
+            int rs = s, pt = 0;
+            int jd[N];
+#pragma unroll
+            for (int d = 0; d < N; d++) {
+                jd[d] = rs % I.k;
+                rs /= I.k;
+            }
+#pragma unroll
+            for (int d = 0; d < N; d++) pt = pt * side + ((cc >> (N - 1 - d)) & 1) * k1 + jd[d];
+            pt += g * pts1;
+#pragma unroll
+            for (int d = 0; d < N; d++) {
+                const float y = s_y[pt * N + d];
+                bad = bad || !(fabsf(y) <= FLT_MAX);
+                mn[d] = fminf(mn[d], y);
+                mx[d] = fmaxf(mx[d], y);
+            }
+        }
+        store_box<N>(I, (int64_t)node * I.nu + u, mn, mx, E, bad);
+    }
+}
+
+// ---- the bounds: one thread per region and control, E_d left in the first
+// N floats of the box32 slot the sample kernel reads it from (lattice: the
+// root cell's; siblings: child 0's, the region the parent's box; per pair:
+// the pair's). Items: lattice and per pair, pairs (cell, control) of the
+// range; siblings, (parent, control) = (sibling group, control).
+template <class DY, int KIND>
+__global__ void __launch_bounds__(128) k_bound(const InstDesc *__restrict__ D, const Range *__restrict__ R, int nr)
+{
+    constexpr int N = DY::N;
+    __shared__ int s_r;
+    __shared__ float s_p[GIS_NPARAM], s_pr[GIS_NPARAM];
+    if (threadIdx.x == 0) s_r = find_range(R, nr, blockIdx.x);
+    __syncthreads();
+    const Range rg = R[s_r];
+    const InstDesc &I = D[rg.inst];
+    if (threadIdx.x < GIS_NPARAM) {
+        s_p[threadIdx.x] = I.p32[threadIdx.x];
+        s_pr[threadIdx.x] = I.pr32[threadIdx.x];
+    }
+    __syncthreads();
+    const int64_t local = (int64_t)(blockIdx.x - rg.block_start) * 128 + threadIdx.x;
+    if (local >= rg.count) return;
+    const int64_t it = rg.first + local;
+    int u, node, span;
+    if (KIND == 1) {                                // (sibling group, control)
+        u = (int)(it % I.nu);
+        node = I.live[I.fresh0 + ((it / I.nu) << N)];
+        span = 2;
+    } else {                                        // a pair of the problem
+        const int64_t lp = it - I.pair_base;
+        const int ls = (int)(lp / I.nu);
+        u = (int)(lp - (int64_t)ls * I.nu);
+        node = I.live[ls];
+        span = 1;
+    }
+    const int L = I.lvl[node];
+    const float fr = largest_frac_radius(I);
+    IE xr[N];
+    float E[N];
+#pragma unroll
+    for (int d = 0; d < N; d++) {
+        const int idx = I.idx[d][node];
+        xr[d] = ie_lattice(I, L, d, (float)idx, (float)(idx + span), fr);
+    }
+    const bool ok = region_bound<DY>(I, s_p, s_pr, u, xr, E);
+    const int64_t q = (int64_t)node * I.nu + u;
+#pragma unroll
+    for (int d = 0; d < N; d++) I.box32[q * 4 * N + d] = ok ? E[d] : INFINITY;
+}
+
+template <class DY>
+cudaError_t launch_kind(int kind, int lanes, const InstDesc *D, const WorkList &w, cudaStream_t st)
+{
+    dim3 g((unsigned)w.n_blocks), b(PF_THREADS);
+    if (kind == 0) {
+        k_propf_lat<DY><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges);
+    } else if (kind == 1) {
+        k_propf_sib<DY><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges);
+    } else {
+        switch (lanes) {
+        case 1: k_propf<DY, 1><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges); break;
+        case 2: k_propf<DY, 2><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges); break;
+        case 4: k_propf<DY, 4><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges); break;
+        case 8: k_propf<DY, 8><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges); break;
+        case 16: k_propf<DY, 16><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges); break;
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <class DY>
+cudaError_t launch_bound_kind(int kind, const InstDesc *D, const WorkList &w, cudaStream_t st)
+{
+    dim3 g((unsigned)w.n_blocks), b(128);
+    if (kind == 1) k_bound<DY, 1><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges);
+    else k_bound<DY, 0><<<g, b, 0, st>>>(D, w.d_ranges, w.n_ranges);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_propf_bound(int kind, int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st)
+{
+    if (w.n_blocks == 0) return cudaSuccess;
+    switch (dyn) {
+    case GIS_DYN_VDP: return launch_bound_kind<DynVdp>(kind, D, w, st);
+    case GIS_DYN_CSTR_DL: return launch_bound_kind<DynCstrDl>(kind, D, w, st);
+    case GIS_DYN_CARTPOLE: return launch_bound_kind<DynCartpole>(kind, D, w, st);
+    case GIS_DYN_CSTR_PAPER: return launch_bound_kind<DynCstrPaper>(kind, D, w, st);
+    case GIS_DYN_LINMAP:
+        switch (n) {
+        case 1: return launch_bound_kind<DynLin<1>>(kind, D, w, st);
+        case 2: return launch_bound_kind<DynLin<2>>(kind, D, w, st);
+        case 3: return launch_bound_kind<DynLin<3>>(kind, D, w, st);
+        case 4: return launch_bound_kind<DynLin<4>>(kind, D, w, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+// kind: 0 lattice tiles, 1 sibling lattices, 2 per pair (lanes)
+cudaError_t launch_propf(int kind, int dyn, int n, int lanes, const InstDesc *D, const WorkList &w, cudaStream_t st)
+{
+    if (w.n_blocks == 0) return cudaSuccess;
+    switch (dyn) {
+    case GIS_DYN_VDP: return launch_kind<DynVdp>(kind, lanes, D, w, st);
+    case GIS_DYN_CSTR_DL: return launch_kind<DynCstrDl>(kind, lanes, D, w, st);
+    case GIS_DYN_CARTPOLE: return launch_kind<DynCartpole>(kind, lanes, D, w, st);
+    case GIS_DYN_CSTR_PAPER: return launch_kind<DynCstrPaper>(kind, lanes, D, w, st);
+    case GIS_DYN_LINMAP:
+        switch (n) {
+        case 1: return launch_kind<DynLin<1>>(kind, lanes, D, w, st);
+        case 2: return launch_kind<DynLin<2>>(kind, lanes, D, w, st);
+        case 3: return launch_kind<DynLin<3>>(kind, lanes, D, w, st);
+        case 4: return launch_kind<DynLin<4>>(kind, lanes, D, w, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace gis

@@ -289,3 +289,14 @@ def test_cycled_linear_maps(gis, n):
 
 def test_cycled_interval(gis):
     run_both(gis, dict(W.cstr_256(levels=3, n0=17), rule="outer", enclosure="interval", split="cycled"), 3)
+
+
+@pytest.mark.parametrize("leaf_map", ["0", "1"])
+def test_tree_walk_and_leaf_map(gis, monkeypatch, leaf_map):
+    """Fresh cells at the finest level find their edges through the leaf map
+    unless GIS_LEAF_MAP=0; every other cell walks the tree. Both give the
+    oracle's graphs (2-D and 4-D, rings splitting coarse cells too)."""
+    monkeypatch.setenv("GIS_LEAF_MAP", leaf_map)
+    run_both(gis, dict(W.cstr_256(levels=3, n0=31), rule="inner"), 3)
+    run_both(gis, dict(W.cartpole_48(levels=2, n0=6), rule="outer"), 2)
+    run_both(gis, dict(W.cstr_256(levels=2, n0=17), rule="outer", split_ring=2), 2)
