@@ -1277,12 +1277,12 @@ struct Engine {
 
         // propagation of new cells, grouped by (dynamics, n, precision, lanes)
         timer.begin(PH_PROP);
-        const bool plain = prop_plain();
         last_new_pairs = 0;
         std::map<std::tuple<int, int, int, int>, std::vector<RangeSpec>> groups, bgroups;
         for (int i : ids) {
             Inst &I = *inst[i];
             if (I.n_fresh == 0) continue;
+            const bool plain = prop_plain(I.dyn.dyn_id);
             const int64_t first = I.pair_base + (I.n_live - I.n_fresh) * I.nu;
             // first build of an FP32 problem with boundary samples: shared
             // lattice points (lanes = 0 marks the lattice kernel; items are
@@ -1333,7 +1333,7 @@ struct Engine {
         for (auto &g : groups) {
             const int dyn = std::get<0>(g.first), n = std::get<1>(g.first), prec = std::get<2>(g.first);
             const int lanes = std::get<3>(g.first);
-            if (plain && prec == GIS_FP32_RECHECK && lanes != -2)   // the regions' bounds first
+            if (prop_plain(dyn) && prec == GIS_FP32_RECHECK && lanes != -2)   // the regions' bounds first
                 CK(launch_propf_bound(lanes == 0 ? 0 : lanes == -1 ? 1 : 2, dyn, n, d_desc,
                                       make_work(bgroups[g.first], 128), st));
             if (lanes == -2) {

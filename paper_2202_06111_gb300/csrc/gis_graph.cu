@@ -791,7 +791,7 @@ __global__ void __launch_bounds__(256) k_export_boxes(const InstDesc *__restrict
 {
     RANGE_HEAD(256)
     const int64_t lp = rg.first + local - I.pair_base;
-    const int ls = (int)(lp / I.nu);
+    const int ls = (int)lp / I.nu;              // lp < 2^31: a 32-bit division
     const int u = (int)(lp - (int64_t)ls * I.nu);
     const int64_t q = (int64_t)I.live[ls] * I.nu + u;
     const uint16_t x = I.exact[q];

@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(128) k_prop_iv(const InstDesc *__restrict__ D,
     const int64_t local = (int64_t)(blockIdx.x - rg.block_start) * blockDim.x + threadIdx.x;
     if (local >= rg.count) return;
     const int64_t lp = rg.first + local - I.pair_base;
-    const int ls = (int)(lp / I.nu);
+    const int ls = (int)lp / I.nu;              // lp < 2^31: a 32-bit division
     const int u = (int)(lp - (int64_t)ls * I.nu);
     const int node = I.live[ls];
     const int L = I.lvl[node];

@@ -41,12 +41,12 @@ int sibling_groups(int n, int k);
 cudaError_t launch_prop64(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st);
 // FP32 propagation of plain samples with one rounding bound per region
 // (kind 0: lattice tiles, 1: sibling lattices, 2: per pair with `lanes`);
-// the launchers above route here unless GIS_PROP_BALL=1
+// the launchers above route here for the models prop_plain(dyn) names
 cudaError_t launch_propf(int kind, int dyn, int n, int lanes, const InstDesc *D, const WorkList &w, cudaStream_t st);
 // the regions' bounds, launched before launch_propf: items are the pairs of
 // the range (kinds 0 and 2) or (sibling group, control) (kind 1)
 cudaError_t launch_propf_bound(int kind, int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st);
-bool prop_plain();
+bool prop_plain(int dyn);
 // interval enclosure of each whole cell's image (FP64, one thread per pair)
 cudaError_t launch_prop_iv(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st);
 int prop_iv_threads();

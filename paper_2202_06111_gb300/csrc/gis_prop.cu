@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop32(const InstDesc *__restr
     int64_t q = 0;
     if (valid) {
         const int64_t lp = rg.first + local - I.pair_base;
-        const int ls = (int)(lp / I.nu);
+        const int ls = (int)lp / I.nu;              // lp < 2^31: a 32-bit division
         const int u = (int)(lp - (int64_t)ls * I.nu);
         const int node = I.live[ls];
         const int L = I.lvl[node];
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop64(const InstDesc *__restr
     const int64_t local = (int64_t)(blockIdx.x - rg.block_start) * PROP_THREADS + threadIdx.x;
     if (local >= rg.count) return;
     const int64_t lp = rg.first + local - I.pair_base;
-    const int ls = (int)(lp / I.nu);
+    const int ls = (int)lp / I.nu;              // lp < 2^31: a 32-bit division
     const int u = (int)(lp - (int64_t)ls * I.nu);
     const int node = I.live[ls];
     const int L = I.lvl[node];
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(256) k_bin(const InstDesc *__restrict__ D, con
     const InstDesc &I = D[rg.inst];
     const int64_t p = rg.first + local;
     const int64_t lp = p - I.pair_base;
-    const int ls = (int)(lp / I.nu);
+    const int ls = (int)lp / I.nu;              // lp < 2^31: a 32-bit division
     const int u = (int)(lp - (int64_t)ls * I.nu);
     const int node = I.live[ls];
     const int64_t q = (int64_t)node * I.nu + u;
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(256) k_rc_cand(const InstDesc *__restrict__ D,
         for (int d = 0; d < N; d++) idx[d] = 0;
         if (valid) {
             const int64_t lp = (int64_t)item.x - I.pair_base;
-            const int ls = (int)(lp / I.nu);
+            const int ls = (int)lp / I.nu;              // lp < 2^31: a 32-bit division
             u = (int)(lp - (int64_t)ls * I.nu);
             const int node = I.live[ls];
             L = I.lvl[node];
@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(256) k_rc_dd(const InstDesc *__restrict__ D, c
             continue;
         }
         const int64_t lp = (int64_t)item.x - I.pair_base;
-        const int ls = (int)(lp / I.nu);
+        const int ls = (int)lp / I.nu;              // lp < 2^31: a 32-bit division
         const int u = (int)(lp - (int64_t)ls * I.nu);
         const int node = I.live[ls];
         const int L = I.lvl[node];
@@ -622,7 +622,7 @@ __global__ void __launch_bounds__(256) k_rc_mid(const InstDesc *__restrict__ D, 
         if (I.n != N || mdd == 0 || need64[it]) continue;
         const int64_t p = item.x;
         const int64_t lp = p - I.pair_base;
-        const int ls = (int)(lp / I.nu);
+        const int ls = (int)lp / I.nu;              // lp < 2^31: a 32-bit division
         const int u = (int)(lp - (int64_t)ls * I.nu);
         const int64_t q = (int64_t)I.live[ls] * I.nu + u;
         double *bq = bx_take(I, q, err);
@@ -700,7 +700,7 @@ __global__ void __launch_bounds__(256) k_rc_fp64(const InstDesc *__restrict__ D,
         const InstDesc &I = D[item_inst(item.y)];
         if (I.dyn != DYN || I.n != N) continue;
         const int64_t lp = (int64_t)item.x - I.pair_base;
-        const int ls = (int)(lp / I.nu);
+        const int ls = (int)lp / I.nu;              // lp < 2^31: a 32-bit division
         const int u = (int)(lp - (int64_t)ls * I.nu);
         const int node = I.live[ls];
         const int L = I.lvl[node];
@@ -748,7 +748,7 @@ __global__ void __launch_bounds__(256) k_rc_final(const InstDesc *__restrict__ D
         atomicAdd(n64, 1);
         const int64_t p = item.x;
         const int64_t lp = p - I.pair_base;
-        const int ls = (int)(lp / I.nu);
+        const int ls = (int)lp / I.nu;              // lp < 2^31: a 32-bit division
         const int u = (int)(lp - (int64_t)ls * I.nu);
         const int64_t q = (int64_t)I.live[ls] * I.nu + u;
         const bool all64 = (I.exact[q] & EX_NF32) != 0;
@@ -792,14 +792,22 @@ __global__ void __launch_bounds__(256) k_rc_final(const InstDesc *__restrict__ D
 // ---------------------------------------------------------------------------
 int prop_pairs_per_block(int lanes) { return PROP_THREADS / lanes; }
 
-// The FP32 propagation launches take the plain-sample kernels with one bound
-// per region (gis_propf.cu) unless GIS_PROP_BALL=1 selects the per-sample
-// ball kernels below (both give the same decisions; the ball arithmetic stays
-// in use for the recheck's candidates).
-bool prop_plain()
+// Which form the FP32 propagation of a model takes: plain samples with one
+// bound per region (gis_propf.cu), or the per-sample balls below. Both give
+// the same decisions; they differ in cost. The region bound is looser than a
+// sample's own ball where the model amplifies rounding across a cell (the
+// exponentials of the CSTR models: on the 256^2 CSTR it sent 97 k pairs to the
+// recheck tiers against 59 k, which cost more than its faster propagation
+// saved), so those models keep the balls. GIS_PROP_BALL=1 / GIS_PROP_PLAIN=1
+// force one form for every model. The ball arithmetic stays in use for the
+// recheck's candidates either way.
+bool prop_plain(int dyn)
 {
-    const char *e = std::getenv("GIS_PROP_BALL");
-    return !(e && std::atoi(e) != 0);
+    const char *b = std::getenv("GIS_PROP_BALL");
+    if (b && std::atoi(b) != 0) return false;
+    const char *p = std::getenv("GIS_PROP_PLAIN");
+    if (p && std::atoi(p) != 0) return true;
+    return dyn != GIS_DYN_CSTR_DL && dyn != GIS_DYN_CSTR_PAPER;
 }
 int prop_block_threads() { return PROP_THREADS; }
 
@@ -821,7 +829,7 @@ static cudaError_t prop32_g(int lanes, const InstDesc *D, const WorkList &w, cud
 cudaError_t launch_prop32(int dyn, int n, int lanes, const InstDesc *D, const WorkList &w, cudaStream_t st)
 {
     if (w.n_blocks == 0) return cudaSuccess;
-    if (prop_plain()) return launch_propf(2, dyn, n, lanes, D, w, st);
+    if (prop_plain(dyn)) return launch_propf(2, dyn, n, lanes, D, w, st);
     switch (dyn) {
     case GIS_DYN_VDP: return prop32_g<DynVdp>(lanes, D, w, st);
     case GIS_DYN_CSTR_DL: return prop32_g<DynCstrDl>(lanes, D, w, st);
@@ -958,7 +966,7 @@ static cudaError_t prop32_sib_l(const InstDesc *D, const WorkList &w, cudaStream
 cudaError_t launch_prop32_siblings(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st)
 {
     if (w.n_blocks == 0) return cudaSuccess;
-    if (prop_plain()) return launch_propf(1, dyn, n, 0, D, w, st);
+    if (prop_plain(dyn)) return launch_propf(1, dyn, n, 0, D, w, st);
     switch (dyn) {
     case GIS_DYN_VDP: return prop32_sib_l<DynVdp>(D, w, st);
     case GIS_DYN_CSTR_DL: return prop32_sib_l<DynCstrDl>(D, w, st);
@@ -997,7 +1005,7 @@ static cudaError_t prop32_lat_l(const InstDesc *D, const WorkList &w, cudaStream
 cudaError_t launch_prop32_lattice(int dyn, int n, const InstDesc *D, const WorkList &w, cudaStream_t st)
 {
     if (w.n_blocks == 0) return cudaSuccess;
-    if (prop_plain()) return launch_propf(0, dyn, n, 0, D, w, st);
+    if (prop_plain(dyn)) return launch_propf(0, dyn, n, 0, D, w, st);
     switch (dyn) {
     case GIS_DYN_VDP: return prop32_lat_l<DynVdp>(D, w, st);
     case GIS_DYN_CSTR_DL: return prop32_lat_l<DynCstrDl>(D, w, st);

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(PF_THREADS) k_propf(const InstDesc *__restrict
     int64_t q = 0;
     if (valid) {
         const int64_t lp = rg.first + local - I.pair_base;
-        const int ls = (int)(lp / I.nu);
+        const int ls = (int)lp / I.nu;              // lp < 2^31: a 32-bit division
         const int u = (int)(lp - (int64_t)ls * I.nu);
         const int node = I.live[ls];
         const int L = I.lvl[node];
@@ -187,8 +187,17 @@ __global__ void __launch_bounds__(PF_THREADS) k_propf(const InstDesc *__restrict
     if (valid && lane == 0) store_box<N>(I, q, mn, mx, E, bad != 0);
 }
 
+// Exact division of small non-negative integers (n < 2^16, 1 <= d < 2^16) by
+// a value known per block: q = (n ceil(2^32 / d)) >> 32, exact since n times
+// the rounding of ceil(2^32 / d) stays below 2^32; d = 1 (whose multiplier
+// would need 33 bits) is marked by a zero multiplier.
+__device__ __forceinline__ uint32_t magic_of(uint32_t d) { return d <= 1 ? 0u : (uint32_t)((0xffffffffull + d) / d); }
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, uint32_t magic) { return magic ? __umulhi(n, magic) : n; }
+
 // ---- first build: lattice points of a tile of root cells, each once; each
-// cell takes its own bound (k_bound)
+// cell takes its own bound (k_bound). Index math by per-block tables: the
+// lattice point of digit vector g has offset sum_d g_d stride_d; a cell's
+// samples sit at its base offset plus the sample offsets soff[s].
 template <class DY>
 __global__ void __launch_bounds__(PF_THREADS) k_propf_lat(const InstDesc *__restrict__ D,
                                                           const Range *__restrict__ R, int nr)
@@ -197,7 +206,8 @@ __global__ void __launch_bounds__(PF_THREADS) k_propf_lat(const InstDesc *__rest
     constexpr int PMAX = PF_POINTS / N;
     __shared__ int s_r;
     __shared__ float s_p[GIS_NPARAM], s_pr[GIS_NPARAM];
-    __shared__ float s_y[PMAX * N];
+    __shared__ float s_y[N][PMAX];
+    __shared__ int s_soff[MAXS];
     if (threadIdx.x == 0) s_r = find_range(R, nr, blockIdx.x);
     __syncthreads();
     const Range rg = R[s_r];
@@ -210,7 +220,8 @@ __global__ void __launch_bounds__(PF_THREADS) k_propf_lat(const InstDesc *__rest
     const int u = (int)(item % I.nu);
     int64_t t = item / I.nu;
     const int k1 = I.k - 1;
-    int c0[N], nc[N], np[N];
+    int c0[N], nc[N], np[N], stride[N];
+    uint32_t mnp[N], mnc[N];
     int P = 1, C = 1;
 #pragma unroll
     for (int d = N - 1; d >= 0; d--) {
@@ -219,35 +230,56 @@ __global__ void __launch_bounds__(PF_THREADS) k_propf_lat(const InstDesc *__rest
         c0[d] = ti * I.tile[d];
         nc[d] = min(I.tile[d], I.n0[d] - c0[d]);
         np[d] = nc[d] * k1 + 1;
+        stride[d] = P;
         P *= np[d];
         C *= nc[d];
+        mnp[d] = magic_of((uint32_t)np[d]);
+        mnc[d] = magic_of((uint32_t)nc[d]);
+    }
+    const uint32_t mk = magic_of((uint32_t)I.k);
+    for (int s = threadIdx.x; s < I.S; s += PF_THREADS) {
+        uint32_t rs = (uint32_t)s;
+        int off = 0;
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            const uint32_t q = fdiv(rs, mk);
+            off += (int)(rs - q * (uint32_t)I.k) * stride[d];
+            rs = q;
+        }
+        s_soff[s] = off;
     }
     __syncthreads();
     for (int pt = threadIdx.x; pt < P; pt += PF_THREADS) {
         float x[N], y[N];
-        int r = pt;
+        uint32_t r = (uint32_t)pt;
 #pragma unroll
         for (int d = N - 1; d >= 0; d--) {
-            const int g = c0[d] * k1 + r % np[d];
-            r /= np[d];
+            const uint32_t q = fdiv(r, mnp[d]);
+            const int g = c0[d] * k1 + (int)(r - q * (uint32_t)np[d]);
+            r = q;
             const int idx = min(g / k1, I.n0[d] - 1);
             x[d] = point32(I, 0, d, idx, g - idx * k1);
         }
         step_plain<DY>(I, s_p, u, x, y);
 #pragma unroll
-        for (int d = 0; d < N; d++) s_y[pt * N + d] = y[d];
+        for (int d = 0; d < N; d++) s_y[d][pt] = y[d];
     }
     __syncthreads();
     for (int c = threadIdx.x; c < C; c += PF_THREADS) {
         int lc[N];
-        int r = c, node = 0;
+        uint32_t r = (uint32_t)c;
+        int node = 0, base = 0;
 #pragma unroll
         for (int d = N - 1; d >= 0; d--) {
-            lc[d] = r % nc[d];
-            r /= nc[d];
+            const uint32_t q = fdiv(r, mnc[d]);
+            lc[d] = (int)(r - q * (uint32_t)nc[d]);
+            r = q;
         }
 #pragma unroll
-        for (int d = 0; d < N; d++) node = node * I.n0[d] + c0[d] + lc[d];
+        for (int d = 0; d < N; d++) {
+            node = node * I.n0[d] + c0[d] + lc[d];
+            base += lc[d] * k1 * stride[d];
+        }
         const int64_t q = (int64_t)node * I.nu + u;
         float E[N], mn[N], mx[N];
         bool bad = false;
@@ -259,18 +291,10 @@ __global__ void __launch_bounds__(PF_THREADS) k_propf_lat(const InstDesc *__rest
             mx[d] = -INFINITY;
         }
         for (int s = 0; s < I.S; s++) {
-            int rs = s, pt = 0;
-            int jd[N];
+            const int pt = base + s_soff[s];
 #pragma unroll
             for (int d = 0; d < N; d++) {
-                jd[d] = rs % I.k;
-                rs /= I.k;
-            }
-#pragma unroll
-            for (int d = 0; d < N; d++) pt = pt * np[d] + lc[d] * k1 + jd[d];
-#pragma unroll
-            for (int d = 0; d < N; d++) {
-                const float y = s_y[pt * N + d];
+                const float y = s_y[d][pt];
                 bad = bad || !(fabsf(y) <= FLT_MAX);
                 mn[d] = fminf(mn[d], y);
                 mx[d] = fmaxf(mx[d], y);
@@ -282,7 +306,8 @@ __global__ void __launch_bounds__(PF_THREADS) k_propf_lat(const InstDesc *__rest
 
 // ---- fresh children: the (2 (k-1) + 1)^n points of each parent's lattice
 // once; the region of the bound (k_bound) is the parent's box (the children's
-// union)
+// union). Per-block tables: each parent-lattice point's digits, each sample's
+// and each child's offset in the parent lattice.
 template <class DY>
 __global__ void __launch_bounds__(PF_THREADS) k_propf_sib(const InstDesc *__restrict__ D,
                                                           const Range *__restrict__ R, int nr)
@@ -293,9 +318,11 @@ __global__ void __launch_bounds__(PF_THREADS) k_propf_sib(const InstDesc *__rest
     constexpr int GMAX = PF_THREADS;
     __shared__ int s_r;
     __shared__ float s_p[GIS_NPARAM], s_pr[GIS_NPARAM];
-    __shared__ float s_y[PMAX * N];
-    __shared__ float s_E[GMAX * N];
+    __shared__ float s_y[N][PMAX];
+    __shared__ float s_E[N][GMAX];
     __shared__ uint8_t s_bad[GMAX];
+    __shared__ uint32_t s_dig[PMAX];               // digits of a parent-lattice point, 5 bits each
+    __shared__ int s_soff[MAXS], s_coff[NC];
     if (threadIdx.x == 0) s_r = find_range(R, nr, blockIdx.x);
     __syncthreads();
     const Range rg = R[s_r];
@@ -310,10 +337,40 @@ __global__ void __launch_bounds__(PF_THREADS) k_propf_sib(const InstDesc *__rest
     const int64_t g0 = (item / I.nu) * I.sib_groups;
     const int G = (int)min((int64_t)I.sib_groups, ngroups - g0);
     const int k1 = I.k - 1, side = 2 * k1 + 1;
-    int pts1 = 1;
+    int pts1 = 1, stride[N];
 #pragma unroll
-    for (int d = 0; d < N; d++) pts1 *= side;
-    __syncthreads();
+    for (int d = N - 1; d >= 0; d--) {
+        stride[d] = pts1;
+        pts1 *= side;
+    }
+    const uint32_t mside = magic_of((uint32_t)side), mk = magic_of((uint32_t)I.k), mpts = magic_of((uint32_t)pts1);
+    for (int r0 = threadIdx.x; r0 < pts1; r0 += PF_THREADS) {
+        uint32_t r = (uint32_t)r0, dig = 0;
+#pragma unroll
+        for (int d = N - 1; d >= 0; d--) {
+            const uint32_t q = fdiv(r, mside);
+            dig |= (r - q * (uint32_t)side) << (5 * d);
+            r = q;
+        }
+        s_dig[r0] = dig;
+    }
+    for (int s = threadIdx.x; s < I.S; s += PF_THREADS) {
+        uint32_t rs = (uint32_t)s;
+        int off = 0;
+#pragma unroll
+        for (int d = 0; d < N; d++) {
+            const uint32_t q = fdiv(rs, mk);
+            off += (int)(rs - q * (uint32_t)I.k) * stride[d];
+            rs = q;
+        }
+        s_soff[s] = off;
+    }
+    for (int cc = threadIdx.x; cc < NC; cc += PF_THREADS) {
+        int off = 0;
+#pragma unroll
+        for (int d = 0; d < N; d++) off += ((cc >> (N - 1 - d)) & 1) * k1 * stride[d];
+        s_coff[cc] = off;
+    }
     // the parents' bounds, which the bound kernel left in child 0's slot
     for (int g = threadIdx.x; g < G; g += PF_THREADS) {
         const int node0 = I.live[I.fresh0 + ((g0 + g) << N)];   // child 0: index 2 * parent index
@@ -323,53 +380,45 @@ __global__ void __launch_bounds__(PF_THREADS) k_propf_sib(const InstDesc *__rest
         for (int d = 0; d < N; d++) {
             const float e = I.box32[q0 * 4 * N + d];
             bad = bad || !(e <= FLT_MAX);
-            s_E[g * N + d] = e;
+            s_E[d][g] = e;
         }
         s_bad[g] = bad;
     }
+    __syncthreads();
     for (int pt = threadIdx.x; pt < G * pts1; pt += PF_THREADS) {
-        const int g = pt / pts1;
-        int r = pt - g * pts1;
+        const int g = (int)fdiv((uint32_t)pt, mpts);
+        const uint32_t dig = s_dig[pt - g * pts1];
         const int node0 = I.live[I.fresh0 + ((g0 + g) << N)];
         const int L = I.lvl[node0];
         float x[N], y[N];
 #pragma unroll
-        for (int d = N - 1; d >= 0; d--) {
-            const int gd = r % side;
-            r /= side;
-            const int b = min(gd / k1, 1);
+        for (int d = 0; d < N; d++) {
+            const int gd = (int)((dig >> (5 * d)) & 31u);
+            const int b = gd >= k1 ? 1 : 0;            // a shared face point from the upper child
             x[d] = point32(I, L, d, I.idx[d][node0] + b, gd - b * k1);
         }
         step_plain<DY>(I, s_p, u, x, y);
 #pragma unroll
-        for (int d = 0; d < N; d++) s_y[pt * N + d] = y[d];
+        for (int d = 0; d < N; d++) s_y[d][pt] = y[d];
     }
     __syncthreads();
     for (int c = threadIdx.x; c < G * NC; c += PF_THREADS) {
-        const int g = c / NC, cc = c - g * NC;
+        const int g = c >> N, cc = c & (NC - 1);
         const int node = I.live[I.fresh0 + ((g0 + g) << N) + cc];
         float mn[N], mx[N], E[N];
 #pragma unroll
         for (int d = 0; d < N; d++) {
             mn[d] = INFINITY;
             mx[d] = -INFINITY;
-            E[d] = s_E[g * N + d];
+            E[d] = s_E[d][g];
         }
         bool bad = s_bad[g] != 0;
+        const int base = g * pts1 + s_coff[cc];
         for (int s = 0; s < I.S; s++) {
-            int rs = s, pt = 0;
-            int jd[N];
+            const int pt = base + s_soff[s];
 #pragma unroll
             for (int d = 0; d < N; d++) {
-                jd[d] = rs % I.k;
-                rs /= I.k;
-            }
-#pragma unroll
-            for (int d = 0; d < N; d++) pt = pt * side + ((cc >> (N - 1 - d)) & 1) * k1 + jd[d];
-            pt += g * pts1;
-#pragma unroll
-            for (int d = 0; d < N; d++) {
-                const float y = s_y[pt * N + d];
+                const float y = s_y[d][pt];
                 bad = bad || !(fabsf(y) <= FLT_MAX);
                 mn[d] = fminf(mn[d], y);
                 mx[d] = fmaxf(mx[d], y);
@@ -404,12 +453,13 @@ __global__ void __launch_bounds__(128) k_bound(const InstDesc *__restrict__ D, c
     const int64_t it = rg.first + local;
     int u, node, span;
     if (KIND == 1) {                                // (sibling group, control)
-        u = (int)(it % I.nu);
-        node = I.live[I.fresh0 + ((it / I.nu) << N)];
+        const int grp = (int)it / I.nu;              // it < 2^31: a 32-bit division
+        u = (int)it - grp * I.nu;
+        node = I.live[I.fresh0 + ((int64_t)grp << N)];
         span = 2;
     } else {                                        // a pair of the problem
         const int64_t lp = it - I.pair_base;
-        const int ls = (int)(lp / I.nu);
+        const int ls = (int)lp / I.nu;              // lp < 2^31: a 32-bit division
         u = (int)(lp - (int64_t)ls * I.nu);
         node = I.live[ls];
         span = 1;

@@ -300,3 +300,18 @@ def test_tree_walk_and_leaf_map(gis, monkeypatch, leaf_map):
     run_both(gis, dict(W.cstr_256(levels=3, n0=31), rule="inner"), 3)
     run_both(gis, dict(W.cartpole_48(levels=2, n0=6), rule="outer"), 2)
     run_both(gis, dict(W.cstr_256(levels=2, n0=17), rule="outer", split_ring=2), 2)
+
+
+@pytest.mark.parametrize("form", ["GIS_PROP_BALL", "GIS_PROP_PLAIN"])
+def test_both_propagation_forms(gis, monkeypatch, form):
+    """Every FP32 model takes either the per-sample balls or plain samples with
+    one bound per region (the default picks per model); both forms must give
+    the oracle's graphs and kept sets on every model and work shape (lattice
+    tiles, sibling lattices, per pair)."""
+    monkeypatch.setenv(form, "1")
+    run_both(gis, dict(W.cstr_256(levels=2, n0=23), rule="inner"), 2)
+    run_both(gis, dict(W.cartpole_48(levels=2, n0=6), rule="outer"), 2)
+    run_both(gis, dict(W.cstr_paper_problem(n0=(12, 12), levels=2), rule="outer", precision="fp32"), 2)
+    run_both(gis, W.problem(W.vdp(1.3), [-3, -3], [3, 3], 21, 3, W.controls_grid(-1, 1, 5), 0.1, 10, levels=2,
+                            rule="outer", precision="fp32"), 2)
+    run_both(gis, dict(W.cstr_256(levels=1, n0=19), rule="outer"), 1, lanes_per_pair=4)
