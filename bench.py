@@ -312,7 +312,8 @@ def _roofline(prob, name, agg, steps, peaks, src, sms):
     t_a5 = (agg["ms_prop"] + agg["ms_bin"] + agg["ms_recheck"]) / 1e3
     alg_flops = flops_pp * pairs_prop
     if t_prop > 0:
-        phases["prop"] = {"kernels": "k_prop32_lat / k_prop32_sib / k_prop32 (or k_prop64)",
+        phases["prop"] = {"kernels": "k_bound + k_propf_lat / k_propf_sib / k_propf (plain samples), "
+                                     "k_prop32_lat / k_prop32_sib / k_prop32 (balls), k_prop64",
                           "ms_per_step": 1e3 * t_prop / steps, "bound": "alu", "unit": "TFLOP/s",
                           "achieved": alg_flops / t_prop / 1e12, "frac": alg_flops / t_prop / 1e12 / fp32_peak,
                           "flops_per_pair": flops_pp, "sfu_ops_per_pair": sfu_pp,
