@@ -63,19 +63,13 @@ constexpr int CE_WARPS = 8;      // cells (warps) per block
 constexpr int CE_TAB = 512;      // per-warp tables of control sets per dimension (entries)
 constexpr int CE_GRAB = 4;       // fewest chunks a warp takes at a time
 constexpr int CE_EB = CE_EB_HOST;   // staged edges a warp buffers in shared memory
+#ifndef CE_MINB
+#define CE_MINB 3                // blocks per SM the walk's registers are sized for
+#endif
 
-__device__ __forceinline__ int warp_min(int v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-__device__ __forceinline__ int warp_max(int v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
+// one redux instruction each (integer warp reductions, sm_80 and later)
+__device__ __forceinline__ int warp_min(int v) { return __reduce_min_sync(0xffffffffu, v); }
+__device__ __forceinline__ int warp_max(int v) { return __reduce_max_sync(0xffffffffu, v); }
 
 // Work of the edge kernels comes in chunks of CE_CHUNK root cells of a
 // cell's union box (the union over its controls of their level-0 index
@@ -86,49 +80,90 @@ __device__ __forceinline__ int warp_max(int v)
 // the previous level have no chunks (k_cinc builds their edges).
 constexpr int64_t CE_CHUNK = 64;
 
-// One warp per cell (lane = control), as the edge kernels read the boxes.
+// One thread per cell, over its controls: the union box needs a few loads and
+// compares per control, so one lane per control left most of a warp idle and
+// its reductions cost more than the work.
 __global__ void __launch_bounds__(256) k_cchunks(const InstDesc *__restrict__ D, int64_t NL,
                                                  const int32_t *__restrict__ cinst, const int32_t *__restrict__ rng,
                                                  const uint8_t *__restrict__ pflag, int32_t *__restrict__ nch,
                                                  int32_t *__restrict__ pcnt)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t s = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (s >= NL) return;                           // whole warp
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= NL) return;
     const InstDesc &I = D[cinst[s]];
-    if (lane < I.nu) pcnt[I.pair_base + (s - I.slot_base) * I.nu + lane] = 0;
-    if (s - I.slot_base < I.n_carry || I.split ||  // edges from the previous level's, the per-cell
-        (I.lm_node && I.lvl[I.live[s - I.slot_base]] == I.Lf)) {   // descent (cycled), or the leaf map
-        if (lane == 0) nch[s] = 0;
+    const int nu = I.nu;
+    const int64_t ls = s - I.slot_base, p0 = I.pair_base + ls * nu;
+    for (int u = 0; u < nu; u++) pcnt[p0 + u] = 0;
+    if (ls < I.n_carry || I.split ||               // edges from the previous level's, the per-cell
+        (I.lm_node && I.lvl[I.live[ls]] == I.Lf)) {   // descent (cycled), or the leaf map
+        nch[s] = 0;
         return;
     }
     const int n = I.n, Lf = I.Lf;
-    bool live = false;
-    int a[MAXN], b[MAXN];
-    for (int d = 0; d < MAXN; d++) { a[d] = INT_MAX; b[d] = INT_MIN; }
-    if (lane < I.nu) {
-        const int64_t p = I.pair_base + (s - I.slot_base) * I.nu + lane;
-        live = !(pflag[p] & PF_NONFINITE);
-        if (live)
-            for (int d = 0; d < n; d++) {
-                level_range(rng[p * 2 * MAXN + d], rng[p * 2 * MAXN + n + d], Lf, I.n0[d], a[d], b[d]);
+    int lo[MAXN], hi[MAXN], n0[MAXN];
+#pragma unroll
+    for (int d = 0; d < MAXN; d++) {
+        lo[d] = INT_MAX;
+        hi[d] = INT_MIN;
+        n0[d] = d < n ? I.n0[d] : 1;
+    }
+    bool any = false;
+    for (int u = 0; u < nu; u++) {
+        const int64_t p = p0 + u;
+        if (pflag[p] & PF_NONFINITE) continue;
+        // the pair's decisions: c_0..c_{n-1}, f_0..f_{n-1} (2 MAXN ints a pair, 16-byte aligned)
+        int cf[2 * MAXN];
+        const int4 *v = (const int4 *)(rng + p * 2 * MAXN);
+#pragma unroll
+        for (int w = 0; w < MAXN / 2; w++) {
+            if (4 * w < 2 * n) {
+                const int4 t = v[w];
+                cf[4 * w] = t.x;
+                cf[4 * w + 1] = t.y;
+                cf[4 * w + 2] = t.z;
+                cf[4 * w + 3] = t.w;
+            } else {
+                cf[4 * w] = cf[4 * w + 1] = cf[4 * w + 2] = cf[4 * w + 3] = 0;
+            }
+        }
+        int a[MAXN], b[MAXN];
+        bool live = true;
+#pragma unroll
+        for (int d = 0; d < MAXN; d++) {
+            a[d] = 0;
+            b[d] = 0;
+            if (d < n) {
+                int cd = 0, fd = 0;
+#pragma unroll
+                for (int e = 0; e < 2 * MAXN; e++) {   // cf[d] and cf[n + d] without a dynamic index
+                    if (e == d) cd = cf[e];
+                    if (e == n + d) fd = cf[e];
+                }
+                level_range(cd, fd, Lf, n0[d], a[d], b[d]);
                 live = live && a[d] <= b[d];
             }
+        }
+        if (!live) continue;
+        any = true;
+#pragma unroll
+        for (int d = 0; d < MAXN; d++)
+            if (d < n) {
+                lo[d] = min(lo[d], a[d]);
+                hi[d] = max(hi[d], b[d]);
+            }
     }
-    const bool any = __any_sync(0xffffffffu, live);
     int64_t roots = any ? 1 : 0;
-    for (int d = 0; d < n; d++) {
-        const int lo = warp_min(live ? a[d] : INT_MAX), hi = warp_max(live ? b[d] : INT_MIN);
-        if (any) roots *= (int64_t)(hi - lo + 1);
-    }
-    if (lane == 0) nch[s] = (int32_t)max((int64_t)1, (roots + CE_CHUNK - 1) / CE_CHUNK);
+#pragma unroll
+    for (int d = 0; d < MAXN; d++)
+        if (any && d < n) roots *= (int64_t)(hi[d] - lo[d] + 1);
+    nch[s] = (int32_t)max((int64_t)1, (roots + CE_CHUNK - 1) / CE_CHUNK);
 }
 
 cudaError_t launch_cchunks(const InstDesc *D, int64_t NL, const int32_t *cinst, const int32_t *rng,
                            const uint8_t *pflag, int32_t *nch, int32_t *pcnt, cudaStream_t st)
 {
     if (NL == 0) return cudaSuccess;
-    k_cchunks<<<(unsigned)((NL + 7) / 8), 256, 0, st>>>(D, NL, cinst, rng, pflag, nch, pcnt);
+    k_cchunks<<<(unsigned)((NL + 255) / 256), 256, 0, st>>>(D, NL, cinst, rng, pflag, nch, pcnt);
     note_launch();
     return cudaGetLastError();
 }
@@ -238,12 +273,12 @@ __host__ __device__ constexpr int walk_words(int n) { return 2 + 3 * n; }
 // coff[cell] + the edges of the cell's earlier chunks (cent, cmask; carried
 // from chunk to chunk within a run, from chk_off = the exclusive scan of
 // chk_cnt at a run's start; no scan is needed when every cell has one chunk),
-// reverse edges at rcur[target]++ (rsrc, rmask). *stop (set when the chunk
+// reverse edges at rcur[target]++ (rev). *stop (set when the chunk
 // arrays are too small) makes both passes return at once. With sa.stg the
 // count pass also stages its edges (StageArgs), in a buffer of CE_EB per warp
 // after the stacks in dynamic shared memory.
 template <int N, bool FILL>
-__global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__restrict__ D, int64_t c0, int64_t c1,
+__global__ void __launch_bounds__(CE_WARPS * 32, CE_MINB) k_cedges(const InstDesc *__restrict__ D, int64_t c0, int64_t c1,
                                                             const int64_t *__restrict__ cbase,
                                                             const int32_t *__restrict__ chk_cell,
                                                             int32_t *__restrict__ chk_cnt,
@@ -258,7 +293,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
                                                             const int64_t *__restrict__ coff,
                                                             int32_t *__restrict__ cent, uint32_t *__restrict__ cmask,
                                                             unsigned long long *__restrict__ rcur,
-                                                            int32_t *__restrict__ rsrc, uint32_t *__restrict__ rmask,
+                                                            uint2 *__restrict__ rev,
                                                             unsigned long long *__restrict__ pair_edges,
                                                             int32_t *__restrict__ err, int64_t ecap,
                                                             const StageArgs sa)
@@ -583,8 +618,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
                     if (pos < ecap && r < (unsigned long long)ecap) {
                         cent[pos] = t;
                         cmask[pos] = m;
-                        rsrc[r] = (int32_t)s;
-                        rmask[r] = m;
+                        rev[r] = make_uint2((uint32_t)s, m);
                     } else {
                         atomicExch(err, GIS_EBOUNDS);
                     }
@@ -597,15 +631,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
                 if (emit) eb[nbuf + __popc(b & lt)] = make_uint2((uint32_t)tslot, m);
                 nbuf += __popc(b);
             }
-            if (!FILL && b) {
-                // targets per control: one ballot per control present in the step
-                const uint32_t orm = __reduce_or_sync(FULL, emit ? m : 0u);
-                for (uint32_t mm = orm; mm; mm &= mm - 1) {
-                    const int u = __ffs(mm) - 1;
-                    const uint32_t bu = __ballot_sync(FULL, emit && ((m >> u) & 1u));
-                    if (lane == u) myc += __popc(bu);
-                }
-            }
+            if (!FILL && b) myc += warp_bit_counts(emit ? m : 0u, lane, nu);   // targets per control
             wpos += __popc(b);
             nent += __popc(b);
         }
@@ -641,7 +667,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32, 3) k_cedges(const InstDesc *__r
 // as do the flags the cell's pairs had before.
 // FILL = false: edges per cell (ccnt), targets per pair (pcnt), in-degrees
 // (rcnt), removed-leaf flags, pair-edge total. FILL = true: edges at coff[cell]
-// (cent, cmask) and reverse edges at rcur[target]++ (rsrc, rmask).
+// (cent, cmask) and reverse edges at rcur[target]++ (rev).
 template <int N, bool FILL>
 __global__ void __launch_bounds__(CE_WARPS * 32) k_cinc(const InstDesc *__restrict__ D, const Range *__restrict__ R,
                                                        int nr, const int32_t *__restrict__ rng,
@@ -650,7 +676,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cinc(const InstDesc *__restri
                                                        const int64_t *__restrict__ coff, int32_t *__restrict__ cent,
                                                        uint32_t *__restrict__ cmask,
                                                        unsigned long long *__restrict__ rcur,
-                                                       int32_t *__restrict__ rsrc, uint32_t *__restrict__ rmask,
+                                                       uint2 *__restrict__ rev,
                                                        unsigned long long *__restrict__ pair_edges,
                                                        int32_t *__restrict__ err, int64_t ecap,
                                                        const CellPrev prev)
@@ -658,7 +684,6 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cinc(const InstDesc *__restri
     constexpr uint32_t FULL = 0xffffffffu;
     constexpr int NC = 1 << N;
     __shared__ CtlBox<N> s_box[CE_WARPS][32];
-    __shared__ int s_cnt[CE_WARPS][32];
     CRANGE_HEAD(CE_WARPS)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
@@ -688,13 +713,12 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cinc(const InstDesc *__restri
             box[lane] = b;
         }
         if (prev.pflag[prev.cps[so] + lane] & PF_TOUCH_DEAD) tch = 1u << lane;
-        if (!FILL) s_cnt[warp][lane] = 0;
     }
     const uint32_t live = __ballot_sync(FULL, live_box);
     __syncwarp();
     const int64_t e0 = prev.coff[so], e1 = prev.coff[so + 1];
     int64_t wpos = FILL ? coff[s] : 0;
-    int32_t nent = 0;
+    int32_t nent = 0, myc = 0;
     unsigned long long pe = 0;
     for (int64_t eb = e0; eb < e1; eb += 32) {
         const int64_t e = eb + lane;
@@ -750,16 +774,21 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cinc(const InstDesc *__restri
                 if (base + j < ecap && r < (unsigned long long)ecap) {
                     cent[base + j] = t;
                     cmask[base + j] = mm;
-                    rsrc[r] = (int32_t)s;
-                    rmask[r] = mm;
+                    rev[r] = make_uint2((uint32_t)s, mm);
                 } else {
                     atomicExch(err, GIS_EBOUNDS);
                 }
             } else {
                 atomicAdd(&rcnt[t], 1);
-                for (uint32_t b = mm; b; b &= b - 1) atomicAdd(&s_cnt[warp][__ffs(b) - 1], 1);
                 pe += (unsigned long long)__popc(mm);
             }
+        }
+        if (!FILL) {
+            // targets per control: the lanes' j-th edges counted per control
+            const int mx = __reduce_max_sync(FULL, (unsigned)ne);
+#pragma unroll
+            for (int j = 0; j < NC; j++)
+                if (j < mx) myc += warp_bit_counts(j < ne ? tm[j] : 0u, lane, nu);
         }
         wpos += tot;
         nent += tot;
@@ -770,7 +799,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cinc(const InstDesc *__restri
         const unsigned long long pet = __reduce_add_sync(FULL, (unsigned)pe);
         __syncwarp();
         if (lane < nu) {
-            pcnt[p] = s_cnt[warp][lane];
+            pcnt[p] = myc;
             if ((touched >> lane) & 1) pflag[p] |= PF_TOUCH_DEAD;
         }
         if (lane == 0) {
@@ -789,11 +818,11 @@ cudaError_t launch_cinc(bool fill, int n, const InstDesc *D, const WorkList &w, 
     case NN:                                                                                                 \
         if (fill)                                                                                            \
             k_cinc<NN, true><<<gr, b, 0, st>>>(D, w.d_ranges, w.n_ranges, g.rng, g.pflag, g.pcnt, g.ccnt,    \
-                                               g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rsrc, g.rmask,     \
+                                               g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rev,     \
                                                g.pair_edges, g.err, g.ecap, prev);                           \
         else                                                                                                 \
             k_cinc<NN, false><<<gr, b, 0, st>>>(D, w.d_ranges, w.n_ranges, g.rng, g.pflag, g.pcnt, g.ccnt,   \
-                                                g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rsrc, g.rmask,    \
+                                                g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rev,    \
                                                 g.pair_edges, g.err, g.ecap, prev);                          \
         note_launch();                                                                                       \
         break;
@@ -849,12 +878,12 @@ cudaError_t launch_cedges(bool fill, int n, int depth, const InstDesc *D, int64_
         if (fill)                                                                                          \
             k_cedges<NN, true><<<cedges_grid<NN, true>(dev, depth, smem), b, smem, st>>>(                   \
                 D, c0, c1, cbase, cw.cell, cw.cnt, cw.off, cw.only, grab, cw.stop, S, cinst, g.rng, g.pflag, g.pcnt, \
-                g.ccnt, g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rsrc, g.rmask, g.pair_edges, g.err,      \
+                g.ccnt, g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rev, g.pair_edges, g.err,      \
                 g.ecap, StageArgs{});                                                                              \
         else                                                                                               \
             k_cedges<NN, false><<<cedges_grid<NN, false>(dev, depth, smem), b, smem, st>>>(                 \
                 D, c0, c1, cbase, cw.cell, cw.cnt, cw.off, cw.only, grab, cw.stop, S, cinst, g.rng, g.pflag, g.pcnt, \
-                g.ccnt, g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rsrc, g.rmask, g.pair_edges, g.err,      \
+                g.ccnt, g.rcnt, g.coff, g.cent, g.cmask, g.rcur, g.rev, g.pair_edges, g.err,      \
                 g.ecap, sa);                                                                               \
         note_launch();                                                                                     \
         break;                                                                                             \
@@ -880,7 +909,7 @@ __global__ void __launch_bounds__(256) k_place(const int64_t *__restrict__ cbase
                                                int32_t *__restrict__ err,
                                                const int64_t *__restrict__ coff, int32_t *__restrict__ cent,
                                                uint32_t *__restrict__ cmask, unsigned long long *__restrict__ rcur,
-                                               int32_t *__restrict__ rsrc, uint32_t *__restrict__ rmask)
+                                               uint2 *__restrict__ rev)
 {
     const int lane = threadIdx.x & 31;
     const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -906,8 +935,7 @@ __global__ void __launch_bounds__(256) k_place(const int64_t *__restrict__ cbase
         cmask[dst + j] = m;
         const unsigned long long q = atomicAdd(&rcur[t], 1ull);
         if (q < (unsigned long long)ecap) {
-            rsrc[q] = s;
-            rmask[q] = m;
+            rev[q] = make_uint2((uint32_t)s, m);
         } else {
             atomicExch(err, GIS_EBOUNDS);
         }
@@ -921,7 +949,7 @@ cudaError_t launch_place(const int64_t *cbase, const int32_t *chk_cell, const in
     if (nseg <= 0) return cudaSuccess;
     k_place<<<(unsigned)((nseg + 7) / 8), 256, 0, st>>>(cbase, chk_cell, chk_off, sa.stg, nchunks, sa.seg, nseg,
                                                         any_lost ? sa.lost : nullptr, g.ecap, g.err, g.coff, g.cent,
-                                                        g.cmask, g.rcur, g.rsrc, g.rmask);
+                                                        g.cmask, g.rcur, g.rev);
     note_launch();
     return cudaGetLastError();
 }
@@ -1099,12 +1127,14 @@ __global__ void __launch_bounds__(256) k_cprune(CPruneArgs a)
                 int i0 = 0, i1 = 0;
                 uint32_t m0 = 0, m1 = 0;
                 if (h0) {
-                    i0 = __ldcs(&a.rsrc[e]);
-                    m0 = __ldcs(&a.rmask[e]);
+                    const uint2 v = __ldcs(&a.rev[e]);
+                    i0 = (int)v.x;
+                    m0 = v.y;
                 }
                 if (h1) {
-                    i1 = __ldcs(&a.rsrc[e + 32]);
-                    m1 = __ldcs(&a.rmask[e + 32]);
+                    const uint2 v = __ldcs(&a.rev[e + 32]);
+                    i1 = (int)v.x;
+                    m1 = v.y;
                 }
                 const bool d0 = h0 && cprune_visit(a, i0, m0);
                 const bool d1 = h1 && cprune_visit(a, i1, m1);

@@ -145,6 +145,31 @@ __device__ __forceinline__ int find_range(const Range *__restrict__ R, int nr, i
     return lo;
 }
 
+// Division by a divisor d >= 1 known ahead (per block or per cell): q = (n m)
+// >> 32 with m = ceil(2^32 / d). With e = m d - 2^32 (0 <= e < d), n m / 2^32 =
+// n / d + n e / (d 2^32), so the floor is exact while n e < 2^32, in particular
+// whenever n (d - 1) < 2^32. d = 1 (whose multiplier would need 33 bits) is
+// marked by a zero multiplier.
+__device__ __forceinline__ uint32_t magic_of(uint32_t d) { return d <= 1 ? 0u : (uint32_t)((0xffffffffull + d) / d); }
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, uint32_t magic) { return magic ? __umulhi(n, magic) : n; }
+
+// Per control u < nu: how many lanes of the warp have bit u set in m, returned
+// on lane u. Each mask's bits go into 6-bit fields, five controls to a word
+// (multiplying 5 bits by 1 + 2^5 + 2^10 + 2^15 + 2^20 puts bit i at 6i, and
+// no two partial products share a bit, so nothing carries), one redux add sums
+// a word over the warp (a field reaches 32 at most), and lane u reads its field.
+__device__ __forceinline__ int warp_bit_counts(uint32_t m, int lane, int nu)
+{
+    int r = 0;
+    for (int g = 0; 5 * g < nu; g++) {
+        const uint32_t w = (((m >> (5 * g)) & 31u) * 0x108421u) & 0x01041041u;
+        const uint32_t t = __reduce_add_sync(0xffffffffu, w);
+        const int f = lane - 5 * g;
+        if (f >= 0 && f < 5) r = (int)((t >> (6 * f)) & 63u);
+    }
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // Models. FP32: written for speed (contractions allowed). FP64: the defining
 // operation order, every operation rounded on its own (_rn intrinsics, no

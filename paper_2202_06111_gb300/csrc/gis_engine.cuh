@@ -625,7 +625,6 @@ struct Engine {
     int64_t *coff = nullptr; size_t c_coff = 0;
     int32_t *cent = nullptr; size_t c_cent = 0;
     uint32_t *cmask = nullptr; size_t c_cmask = 0;
-    uint32_t *rmask = nullptr; size_t c_rmask = 0;
     uint32_t *vmask = nullptr; size_t c_vmask = 0;
     int32_t *cinst = nullptr; size_t c_cinst = 0;
     int32_t *cnch = nullptr; size_t c_cnch = 0;
@@ -664,7 +663,7 @@ struct Engine {
     int32_t *rcnt = nullptr; size_t c_rcnt = 0;
     int64_t *roff = nullptr; size_t c_roff = 0;
     int64_t *rcur = nullptr; size_t c_rcur = 0;
-    int32_t *rsrc = nullptr; size_t c_rsrc = 0;
+    uint2 *rev = nullptr; size_t c_rev = 0;
     int32_t *pstate = nullptr; size_t c_pstate = 0;
     int32_t *ncnt = nullptr; size_t c_ncnt = 0;
     uint8_t *alive = nullptr; size_t c_alive = 0;
@@ -1435,7 +1434,7 @@ struct Engine {
         mem.ensure(cnch, c_cnch, NLs);
         mem.ensure(cbase, c_cbase, NLs + 1);
         CellGraph g{rng, pflag, pcnt, ccnt, rcnt, coff, nullptr, nullptr, (unsigned long long *)rcur, nullptr,
-                    nullptr, (unsigned long long *)(ctl + 12), ctl + 7};
+                    (unsigned long long *)(ctl + 12), ctl + 7};
         unsigned long long *grab = (unsigned long long *)(ctl + 24);   // 8 chunk counters
         const CellPrev prev{oslot, coff_o, cent_o, cmask_o, s2n_o, cps_o, pflag_o, prev_NL};
         int64_t seg_base[MAXN + 2] = {0};
@@ -1616,12 +1615,10 @@ struct Engine {
         Ecell = hEc;
         mem.ensure(cent, c_cent, (size_t)std::max<int64_t>(Ecell, 1));
         mem.ensure(cmask, c_cmask, (size_t)std::max<int64_t>(Ecell, 1));
-        mem.ensure(rsrc, c_rsrc, (size_t)std::max<int64_t>(Ecell, 1));
-        mem.ensure(rmask, c_rmask, (size_t)std::max<int64_t>(Ecell, 1));
+        mem.ensure(rev, c_rev, (size_t)std::max<int64_t>(Ecell, 1));
         g.cent = cent;
         g.cmask = cmask;
-        g.rsrc = rsrc;
-        g.rmask = rmask;
+        g.rev = rev;
         g.ecap = Ecell;
         // a cell of several chunks writes each chunk after the earlier ones
         int64_t *koff = nullptr;
@@ -1706,8 +1703,7 @@ struct Engine {
                               st));
         CPruneArgs a{};
         a.roff = roff;
-        a.rsrc = rsrc;
-        a.rmask = rmask;
+        a.rev = rev;
         a.cps = cps;
         a.pinfo = pinfo;
         a.pk = pk;
@@ -1757,7 +1753,7 @@ struct Engine {
         a.coff = coff;
         a.cent = cent;
         a.roff = roff;
-        a.rsrc = rsrc;
+        a.rev = rev;
         a.color = scc_color;
         a.kin = scc_kin;
         a.mark = scc_mark;

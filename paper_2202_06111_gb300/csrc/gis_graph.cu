@@ -684,8 +684,7 @@ __global__ void __launch_bounds__(128) k_sedges(const InstDesc *__restrict__ D, 
                 if (w < g.ecap && r < (unsigned long long)g.ecap) {
                     g.cent[w] = t;
                     g.cmask[w] = m;
-                    g.rsrc[r] = (int32_t)s;
-                    g.rmask[r] = m;
+                    g.rev[r] = make_uint2((uint32_t)s, m);
                 } else {
                     atomicExch(g.err, GIS_EBOUNDS);
                 }

@@ -125,11 +125,10 @@ struct CellGraph {
     int32_t *cent;               // edge target (global slot)
     uint32_t *cmask;             // edge control mask
     unsigned long long *rcur;    // reverse cursor per cell (fill pass)
-    int32_t *rsrc;               // reverse edge source
-    uint32_t *rmask;             // reverse edge control mask
+    uint2 *rev;                  // reverse edge: (source slot, control mask), one 8-byte store
     unsigned long long *pair_edges;  // total (cell, control) -> cell edges
     int32_t *err;
-    int64_t ecap = 0;            // fill: edges allocated (cent, cmask, rsrc, rmask); a write
+    int64_t ecap = 0;            // fill: edges allocated (cent, cmask, rev); a write
                                  // beyond sets *err = GIS_EBOUNDS and is skipped
 };
 cudaError_t launch_cgather(const InstDesc *D, const WorkList &wslots, int32_t *cps, int32_t *cinst,
@@ -213,8 +212,7 @@ cudaError_t launch_cprune_init(const InstDesc *D, const WorkList &wslots, const 
                                int32_t *frontier0, uint32_t *sizes, cudaStream_t st);
 struct CPruneArgs {
     const int64_t *roff;
-    const int32_t *rsrc;
-    const uint32_t *rmask;
+    const uint2 *rev;            // reverse edges: (source slot, control mask)
     const int32_t *cps;          // first pair of each cell
     const uint8_t *pinfo;        // per cell: packed OUTER counts, OUTER, field width - 1
     int32_t *pc;                 // OUTER, unpacked: kept targets per pair
@@ -238,8 +236,8 @@ struct SccArgs {
     int64_t s0, s1;
     const int64_t *coff;         // forward cell edges (global slots)
     const int32_t *cent;
-    const int64_t *roff;         // reverse cell edges
-    const int32_t *rsrc;
+    const int64_t *roff;         // reverse cell edges: (source slot, control mask)
+    const uint2 *rev;
     int32_t *color;              // per slot: part (>= 0), -1 outside every part
     uint8_t *kin;                // per slot: in the OUTER fixed point
     uint32_t *mark;              // per slot: closure bits (1 forward, 2 backward, 4 kept)

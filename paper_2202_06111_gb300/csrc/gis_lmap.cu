@@ -262,8 +262,7 @@ __global__ void __launch_bounds__(ME_WARPS * 32) k_medges(const InstDesc *__rest
                 if (pos < g.ecap && q < (unsigned long long)g.ecap) {
                     g.cent[pos] = t;
                     g.cmask[pos] = m;
-                    g.rsrc[q] = (int32_t)s;
-                    g.rmask[q] = m;
+                    g.rev[q] = make_uint2((uint32_t)s, m);
                 } else {
                     atomicExch(g.err, GIS_EBOUNDS);
                 }
@@ -271,14 +270,7 @@ __global__ void __launch_bounds__(ME_WARPS * 32) k_medges(const InstDesc *__rest
                 atomicAdd(&g.rcnt[t], 1);
             }
         }
-        if (!FILL && b) {
-            const uint32_t orm = __reduce_or_sync(FULL, emit ? m : 0u);
-            for (uint32_t mm = orm; mm; mm &= mm - 1) {
-                const int u = __ffs(mm) - 1;
-                const uint32_t bu = __ballot_sync(FULL, emit && ((m >> u) & 1u));
-                if (lane == u) myc += __popc(bu);
-            }
-        }
+        if (!FILL && b) myc += warp_bit_counts(emit ? m : 0u, lane, nu);   // targets per control
         wpos += __popc(b);
         nent += __popc(b);
     }

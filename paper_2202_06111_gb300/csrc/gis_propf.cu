@@ -187,12 +187,8 @@ __global__ void __launch_bounds__(PF_THREADS) k_propf(const InstDesc *__restrict
     if (valid && lane == 0) store_box<N>(I, q, mn, mx, E, bad != 0);
 }
 
-// Exact division of small non-negative integers (n < 2^16, 1 <= d < 2^16) by
-// a value known per block: q = (n ceil(2^32 / d)) >> 32, exact since n times
-// the rounding of ceil(2^32 / d) stays below 2^32; d = 1 (whose multiplier
-// would need 33 bits) is marked by a zero multiplier.
-__device__ __forceinline__ uint32_t magic_of(uint32_t d) { return d <= 1 ? 0u : (uint32_t)((0xffffffffull + d) / d); }
-__device__ __forceinline__ uint32_t fdiv(uint32_t n, uint32_t magic) { return magic ? __umulhi(n, magic) : n; }
+// (the divisions by values known per block use magic_of / fdiv, gis_device.cuh;
+// here n < 2^16 and d < 2^16, well inside their exact range)
 
 // ---- first build: lattice points of a tile of root cells, each once; each
 // cell takes its own bound (k_bound). Index math by per-block tables: the

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) k_scc_tcount(SccArgs a, int32_t c)
     const int64_t s = a.s0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= a.s1 || a.color[s] != c) return;
     int32_t in = 0, out = 0;
-    for (int64_t e = a.roff[s]; e < a.roff[s + 1]; e++) in += a.color[a.rsrc[e]] == c;
+    for (int64_t e = a.roff[s]; e < a.roff[s + 1]; e++) in += a.color[a.rev[e].x] == c;
     for (int64_t e = a.coff[s]; e < a.coff[s + 1]; e++) out += a.color[a.cent[e]] == c;
     a.din[s] = in;
     a.dout[s] = out;
@@ -112,7 +112,9 @@ __global__ void __launch_bounds__(256) k_scc_trim(SccArgs a, int32_t c)
             const int v = __ldcg(&F[it]);
             for (int dir = 0; dir < 2; dir++) {
                 const int64_t *off = dir == 0 ? a.coff : a.roff;
-                const int32_t *nb = dir == 0 ? a.cent : a.rsrc;
+                // neighbours: cent[e], or the source (x) of rev[e], int 2e of rev
+                const int32_t *nb = dir == 0 ? a.cent : (const int32_t *)a.rev;
+                const int nsh = dir == 0 ? 0 : 1;
                 int32_t *cnt = dir == 0 ? a.din : a.dout;
                 const int64_t e0 = off[v], e1 = off[v + 1];
                 for (int64_t eb = e0; eb < e1; eb += 32) {
@@ -120,7 +122,7 @@ __global__ void __launch_bounds__(256) k_scc_trim(SccArgs a, int32_t c)
                     bool take = false;
                     int w = 0;
                     if (e < e1) {
-                        w = nb[e];
+                        w = nb[e << nsh];
                         if (*(volatile int32_t *)&a.color[w] == c && atomicSub(&cnt[w], 1) == 1)
                             take = atomicCAS(&a.color[w], c, -1) == c;
                     }
@@ -178,7 +180,7 @@ __global__ void k_scc_seed(SccArgs a)
     }
 }
 
-// Closure from the frontier: forward over cent or backward over rsrc, into
+// Closure from the frontier: forward over cent or backward over rev, into
 // cells of colour c (c >= 0) or, for c = -2, into the kept-aside OUTER set;
 // a cell reached for the first time (bit b newly set) joins the next frontier.
 __global__ void __launch_bounds__(256) k_scc_reach(SccArgs a, int32_t c, int backward, uint32_t b)
@@ -194,7 +196,9 @@ __global__ void __launch_bounds__(256) k_scc_reach(SccArgs a, int32_t c, int bac
     uint32_t *sizes = backward ? a.sizes2 : a.sizes;
     uint32_t *bar = backward ? a.bar2 : a.bar;
     const int64_t *off = backward ? a.roff : a.coff;
-    const int32_t *nb = backward ? a.rsrc : a.cent;
+    // neighbours: cent[e], or the source (x) of rev[e], int 2e of rev
+    const int32_t *nb = backward ? (const int32_t *)a.rev : a.cent;
+    const int nsh = backward ? 1 : 0;
     uint32_t target = 0;
     for (int round = 0;; round++) {
         target += gridDim.x;
@@ -216,7 +220,7 @@ __global__ void __launch_bounds__(256) k_scc_reach(SccArgs a, int32_t c, int bac
                 bool take = false;
                 int w = 0;
                 if (e < e1) {
-                    w = nb[e];
+                    w = nb[e << nsh];
                     const bool in = c >= 0 ? a.color[w] == c : a.kin[w] != 0;
                     if (in && !(*(volatile uint32_t *)&a.mark[w] & b)) take = !(atomicOr(&a.mark[w], b) & b);
                 }
