@@ -400,6 +400,24 @@ __global__ void __launch_bounds__(256) k_bin(const InstDesc *__restrict__ D, con
     const int u = (int)(lp - (int64_t)ls * I.nu);
     const int node = I.live[ls];
     const int64_t q = (int64_t)node * I.nu + u;
+    // the pair's FP32 box (4N floats, 16-byte aligned) is loaded beside its
+    // exact bits, so the two memory round trips overlap (FP64-plain problems
+    // keep no FP32 boxes)
+    float bx[4 * N];
+    if (I.box32) {
+        const float4 *b4 = (const float4 *)(I.box32 + q * 4 * N);
+#pragma unroll
+        for (int w = 0; w < N; w++) {
+            const float4 t = b4[w];
+            bx[4 * w] = t.x;
+            bx[4 * w + 1] = t.y;
+            bx[4 * w + 2] = t.z;
+            bx[4 * w + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int w = 0; w < 4 * N; w++) bx[w] = 0.0f;
+    }
     const uint16_t ex = I.exact[q];
     constexpr unsigned FULL = (1u << (2 * N)) - 1u;
     if (ex & EX_NF64) {
@@ -419,8 +437,7 @@ __global__ void __launch_bounds__(256) k_bin(const InstDesc *__restrict__ D, con
             if ((ex >> e) & 1) {
                 const double *b = bx_get(I, q);
                 if (!decide_enc<N>(I, e, b[2 * e], b[2 * e + 1], out[e], inx)) m64 |= 1u << e;
-            } else if (!decide_approx<N>(I, e, I.box32[q * 4 * N + 2 * e], I.box32[q * 4 * N + 2 * e + 1], out[e],
-                                         inx)) {
+            } else if (!decide_approx<N>(I, e, bx[2 * e], bx[2 * e + 1], out[e], inx)) {
                 mdd |= 1u << e;
             }
         }
@@ -431,8 +448,15 @@ __global__ void __launch_bounds__(256) k_bin(const InstDesc *__restrict__ D, con
         pflag[p] = PF_RECHECK;
         return;
     }
+    // 2 MAXN ints a pair, 16-byte aligned: whole vectors where N allows
+    if ((2 * N) % 4 == 0) {
+        int4 *r4 = (int4 *)(rng + p * 2 * MAXN);
 #pragma unroll
-    for (int e = 0; e < 2 * N; e++) rng[p * 2 * MAXN + e] = out[e];
+        for (int w = 0; w < (2 * N) / 4; w++) r4[w] = make_int4(out[4 * w], out[4 * w + 1], out[4 * w + 2], out[4 * w + 3]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 2 * N; e++) rng[p * 2 * MAXN + e] = out[e];
+    }
     pflag[p] = inx ? PF_INX : 0;
 }
 
