@@ -358,16 +358,19 @@ __global__ void __launch_bounds__(CE_WARPS * 32, CE_MINB) k_cedges(const InstDes
 #pragma unroll
         for (int d = 0; d < N; d++) { a0[d] = INT_MAX; b0[d] = INT_MIN; }
         if (lane < nu) {
+            // the decisions are read with the flag, not after it (one memory
+            // round trip); a non-finite pair's are not used
+            int cc[N], ff[N];
+            load_decisions<N>(rng, p, cc, ff);
             live_box = !(pflag[p] & PF_NONFINITE);
             if (live_box) {
                 CtlBox<N> cb_;
 #pragma unroll
                 for (int d = 0; d < N; d++) {
-                    const int c = rng[p * 2 * MAXN + d], f = rng[p * 2 * MAXN + N + d];
-                    cb_.cf[2 * d] = c;
-                    cb_.cf[2 * d + 1] = f;
+                    cb_.cf[2 * d] = cc[d];
+                    cb_.cf[2 * d + 1] = ff[d];
                     int a, b;
-                    level_range(c, f, Lf, n0[d], a, b);
+                    level_range(cc[d], ff[d], Lf, n0[d], a, b);
                     live_box = live_box && a <= b;
                     a0[d] = a;
                     b0[d] = b;
@@ -444,7 +447,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32, CE_MINB) k_cedges(const InstDes
                     const uint2 v = eb[j];
                     sa.stg[base + j] = (unsigned long long)v.y << 32 | v.x;
                 }
-                if (lane == 0) sa.seg[sidx] = SegRec{(long long)base, (int32_t)k, soff, nbuf, 0};
+                if (lane == 0) sa.seg[sidx] = SegRec{(long long)base, (int32_t)k, soff, nbuf, (int32_t)s};
             } else if (lane == 0) {
                 // out of room: the chunk is walked again by the fill (its record,
                 // if it has a slot, is written empty)
@@ -693,6 +696,16 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cinc(const InstDesc *__restri
     const int ls = (int)(s - I.slot_base);
     const int nu = I.nu, Lf = I.Lf;
     const int64_t p = I.pair_base + (int64_t)ls * nu + lane;
+    // the pair's decisions and flag are requested with the previous slot, not
+    // after its check (their round trips overlap)
+    int cc[N], ff[N];
+    uint8_t pf = PF_NONFINITE;
+#pragma unroll
+    for (int d = 0; d < N; d++) cc[d] = ff[d] = 0;
+    if (lane < nu) {
+        load_decisions<N>(rng, p, cc, ff);
+        pf = pflag[p];
+    }
     const int64_t so = prev.oslot[s];
     if (so < 0 || so >= prev.n_old) {              // not a slot of the previous build
         if (lane == 0) atomicExch(err, GIS_EBOUNDS);
@@ -702,13 +715,13 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cinc(const InstDesc *__restri
     bool live_box = false;
     uint32_t tch = 0;
     if (lane < nu) {
-        live_box = !(pflag[p] & PF_NONFINITE);
+        live_box = !(pf & PF_NONFINITE);
         if (live_box) {
             CtlBox<N> b;
 #pragma unroll
             for (int d = 0; d < N; d++) {
-                b.cf[2 * d] = rng[p * 2 * MAXN + d];
-                b.cf[2 * d + 1] = rng[p * 2 * MAXN + N + d];
+                b.cf[2 * d] = cc[d];
+                b.cf[2 * d + 1] = ff[d];
             }
             box[lane] = b;
         }
@@ -904,8 +917,8 @@ __global__ void __launch_bounds__(256) k_place(const int64_t *__restrict__ cbase
                                                const int32_t *__restrict__ chk_cell,
                                                const int64_t *__restrict__ chk_off,
                                                const unsigned long long *__restrict__ stg,
-                                               int64_t nchunks, const SegRec *__restrict__ seg, int64_t nseg,
-                                               const uint8_t *__restrict__ lost, int64_t ecap,
+                                               int64_t nchunks, int64_t ncells, const SegRec *__restrict__ seg,
+                                               int64_t nseg, const uint8_t *__restrict__ lost, int64_t ecap,
                                                int32_t *__restrict__ err,
                                                const int64_t *__restrict__ coff, int32_t *__restrict__ cent,
                                                uint32_t *__restrict__ cmask, unsigned long long *__restrict__ rcur,
@@ -920,10 +933,18 @@ __global__ void __launch_bounds__(256) k_place(const int64_t *__restrict__ cbase
         return;
     }
     if (lost && lost[r.chunk]) return;            // the fill walks this chunk
-    const int32_t s = chk_cell[r.chunk];
-    int64_t dst = coff[s] + r.soff;
+    // the record names its cell, so the cell's offsets are requested together
+    // with the chunk's cell (checked against it) instead of after it
+    const int32_t s = r.cell;
+    if (s < 0 || s >= ncells) {
+        if (lane == 0) atomicExch(err, GIS_EBOUNDS);
+        return;
+    }
+    const int32_t sc = chk_cell[r.chunk];
+    const int64_t o0 = coff[s], o1 = coff[s + 1];
+    int64_t dst = o0 + r.soff;
     if (chk_off) dst += chk_off[r.chunk] - chk_off[cbase[s]];
-    if (dst < coff[s] || dst + r.len > coff[s + 1]) {
+    if (sc != s || dst < o0 || dst + r.len > o1) {
         if (lane == 0) atomicExch(err, GIS_EBOUNDS);
         return;
     }
@@ -943,11 +964,12 @@ __global__ void __launch_bounds__(256) k_place(const int64_t *__restrict__ cbase
 }
 
 cudaError_t launch_place(const int64_t *cbase, const int32_t *chk_cell, const int64_t *chk_off, int64_t nchunks,
-                         const StageArgs &sa, bool any_lost, int64_t nseg, const CellGraph &g, cudaStream_t st)
+                         int64_t ncells, const StageArgs &sa, bool any_lost, int64_t nseg, const CellGraph &g, cudaStream_t st)
 {
     nseg = std::min(nseg, sa.seg_cap);            // the counter also counts records that found no slot
     if (nseg <= 0) return cudaSuccess;
-    k_place<<<(unsigned)((nseg + 7) / 8), 256, 0, st>>>(cbase, chk_cell, chk_off, sa.stg, nchunks, sa.seg, nseg,
+    k_place<<<(unsigned)((nseg + 7) / 8), 256, 0, st>>>(cbase, chk_cell, chk_off, sa.stg, nchunks, ncells, sa.seg,
+                                                        nseg,
                                                         any_lost ? sa.lost : nullptr, g.ecap, g.err, g.coff, g.cent,
                                                         g.cmask, g.rcur, g.rev);
     note_launch();

@@ -153,6 +153,29 @@ __device__ __forceinline__ int find_range(const Range *__restrict__ R, int nr, i
 __device__ __forceinline__ uint32_t magic_of(uint32_t d) { return d <= 1 ? 0u : (uint32_t)((0xffffffffull + d) / d); }
 __device__ __forceinline__ uint32_t fdiv(uint32_t n, uint32_t magic) { return magic ? __umulhi(n, magic) : n; }
 
+// A pair's finest-level decisions c_0..c_{N-1}, f_0..f_{N-1}: the first 2N of
+// its 2 MAXN ints (a 16-byte aligned slot), read as whole vectors.
+template <int N>
+__device__ __forceinline__ void load_decisions(const int32_t *__restrict__ rng, int64_t p, int *c, int *f)
+{
+    static_assert(MAXN == 4 && N >= 1 && N <= MAXN, "decision slots of 8 ints");
+    const int4 *q = (const int4 *)(rng + p * 2 * MAXN);
+    const int4 a = q[0];
+    int v[8] = {a.x, a.y, a.z, a.w, 0, 0, 0, 0};
+    if (2 * N > 4) {
+        const int4 b = q[1];
+        v[4] = b.x;
+        v[5] = b.y;
+        v[6] = b.z;
+        v[7] = b.w;
+    }
+#pragma unroll
+    for (int d = 0; d < N; d++) {
+        c[d] = v[d];
+        f[d] = v[N + d];
+    }
+}
+
 // Per control u < nu: how many lanes of the warp have bit u set in m, returned
 // on lane u. Each mask's bits go into 6-bit fields, five controls to a word
 // (multiplying 5 bits by 1 + 2^5 + 2^10 + 2^15 + 2^20 puts bit i at 6i, and

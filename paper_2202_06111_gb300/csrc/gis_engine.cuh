@@ -1632,7 +1632,7 @@ struct Engine {
         }
         timer.begin(PH_FILL);
         CK(cudaMemcpyAsync(rcur, roff, NLs * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
-        if (placed) CK(launch_place(cbase, chk_cell, koff, K, sa, sover != 0, (int64_t)nseg, g, st));
+        if (placed) CK(launch_place(cbase, chk_cell, koff, K, NL, sa, sover != 0, (int64_t)nseg, g, st));
         if (!placed || sover) {
             ChunkWork cw{chk_cell, chk_cnt, koff, ctl + 18, cap};
             cw.only = placed ? chk_lost : nullptr;

@@ -171,7 +171,7 @@ struct ChunkWork {
 constexpr int CE_EB_HOST = 256;  // edges a warp buffers before a flush (CE_EB)
 struct SegRec {
     long long pos;
-    int32_t chunk, soff, len, pad;
+    int32_t chunk, soff, len, cell;
 };
 struct StageArgs {
     unsigned long long *stg = nullptr;   // null: no staging
@@ -184,7 +184,7 @@ struct StageArgs {
     uint8_t *lost = nullptr;     // per chunk, zeroed
 };
 cudaError_t launch_place(const int64_t *cbase, const int32_t *chk_cell, const int64_t *chk_off, int64_t nchunks,
-                         const StageArgs &sa, bool any_lost, int64_t nseg, const CellGraph &g, cudaStream_t st);
+                         int64_t ncells, const StageArgs &sa, bool any_lost, int64_t nseg, const CellGraph &g, cudaStream_t st);
 // the cell of each chunk; zeroes the per-cell counts ccnt and rcnt and, with
 // lost, the chunks' lost marks
 cudaError_t launch_cexpand(const int64_t *cbase, int64_t NL, const ChunkWork &cw, int32_t *ccnt, int32_t *rcnt,
