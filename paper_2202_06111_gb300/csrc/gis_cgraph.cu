@@ -110,22 +110,12 @@ __global__ void __launch_bounds__(256) k_cchunks(const InstDesc *__restrict__ D,
     bool any = false;
     for (int u = 0; u < nu; u++) {
         const int64_t p = p0 + u;
+        int cs[MAXN], fs[MAXN];
+        if (n == 4) load_decisions<4>(rng, p, cs, fs);   // with the flag, not after it
+        else if (n == 3) load_decisions<3>(rng, p, cs, fs);
+        else if (n == 2) load_decisions<2>(rng, p, cs, fs);
+        else load_decisions<1>(rng, p, cs, fs);
         if (pflag[p] & PF_NONFINITE) continue;
-        // the pair's decisions: c_0..c_{n-1}, f_0..f_{n-1} (2 MAXN ints a pair, 16-byte aligned)
-        int cf[2 * MAXN];
-        const int4 *v = (const int4 *)(rng + p * 2 * MAXN);
-#pragma unroll
-        for (int w = 0; w < MAXN / 2; w++) {
-            if (4 * w < 2 * n) {
-                const int4 t = v[w];
-                cf[4 * w] = t.x;
-                cf[4 * w + 1] = t.y;
-                cf[4 * w + 2] = t.z;
-                cf[4 * w + 3] = t.w;
-            } else {
-                cf[4 * w] = cf[4 * w + 1] = cf[4 * w + 2] = cf[4 * w + 3] = 0;
-            }
-        }
         int a[MAXN], b[MAXN];
         bool live = true;
 #pragma unroll
@@ -133,13 +123,7 @@ __global__ void __launch_bounds__(256) k_cchunks(const InstDesc *__restrict__ D,
             a[d] = 0;
             b[d] = 0;
             if (d < n) {
-                int cd = 0, fd = 0;
-#pragma unroll
-                for (int e = 0; e < 2 * MAXN; e++) {   // cf[d] and cf[n + d] without a dynamic index
-                    if (e == d) cd = cf[e];
-                    if (e == n + d) fd = cf[e];
-                }
-                level_range(cd, fd, Lf, n0[d], a[d], b[d]);
+                level_range(cs[d], fs[d], Lf, n0[d], a[d], b[d]);
                 live = live && a[d] <= b[d];
             }
         }

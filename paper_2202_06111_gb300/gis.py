@@ -276,14 +276,16 @@ class Context:
         _check(load().gis_solve(self._h, self.prob.get("levels", 0) if levels is None else levels), self._h)
 
     def cells(self):
-        """(level[N], flags[N], idx[N, n]) of the live cells, in slot order."""
+        """(level[N], flags[N], idx[N, n]) of the live cells, in slot order:
+        column views of one (N, 2 + MAXN) int32 array that the library fills
+        (gis_cell rows; not zeroed first, nothing copied after)."""
         L = load()
         n = C.c_int64()
         _check(L.gis_get_cells(self._h, None, 0, C.byref(n)), self._h)
-        buf = (gis_cell * max(n.value, 1))()
-        _check(L.gis_get_cells(self._h, buf, n.value, C.byref(n)), self._h)
-        a = np.frombuffer(buf, dtype=np.int32).reshape(-1, 2 + MAXN)[:n.value]
-        return a[:, 0].copy(), a[:, 1].copy(), a[:, 2:2 + self.n].copy()
+        a = np.empty((max(n.value, 1), 2 + MAXN), np.int32)
+        _check(L.gis_get_cells(self._h, a.ctypes.data_as(C.POINTER(gis_cell)), n.value, C.byref(n)), self._h)
+        a = a[:n.value]
+        return a[:, 0], a[:, 1], a[:, 2:2 + self.n]
 
     def kept_cells(self):
         lv, fl, idx = self.cells()
