@@ -100,13 +100,17 @@ template <int N>
 __device__ __forceinline__ void store_box(const InstDesc &I, int64_t q, const float *mn, const float *mx,
                                           const float *E, bool bad)
 {
+    float v[4 * N];
 #pragma unroll
     for (int d = 0; d < N; d++) {
-        I.box32[q * 4 * N + 2 * d] = __fsub_rd(mn[d], E[d]);
-        I.box32[q * 4 * N + 2 * d + 1] = __fadd_ru(mn[d], E[d]);
-        I.box32[q * 4 * N + 2 * (N + d)] = __fsub_rd(mx[d], E[d]);
-        I.box32[q * 4 * N + 2 * (N + d) + 1] = __fadd_ru(mx[d], E[d]);
+        v[2 * d] = __fsub_rd(mn[d], E[d]);
+        v[2 * d + 1] = __fadd_ru(mn[d], E[d]);
+        v[2 * (N + d)] = __fsub_rd(mx[d], E[d]);
+        v[2 * (N + d) + 1] = __fadd_ru(mx[d], E[d]);
     }
+    float4 *o = (float4 *)(I.box32 + q * 4 * N);   // 4N floats a pair: 16-byte aligned
+#pragma unroll
+    for (int w = 0; w < N; w++) o[w] = make_float4(v[4 * w], v[4 * w + 1], v[4 * w + 2], v[4 * w + 3]);
     I.exact[q] = bad ? EX_NF32 : 0;
     if (!I.bx_dense) I.bxi[q] = -1;               // compact store: no entry yet
 }
@@ -316,6 +320,8 @@ __global__ void __launch_bounds__(PF_THREADS) k_propf_sib(const InstDesc *__rest
     __shared__ float s_p[GIS_NPARAM], s_pr[GIS_NPARAM];
     __shared__ float s_y[N][PMAX];
     __shared__ float s_E[N][GMAX];
+    __shared__ float s_w[N][GMAX];                 // per parent: cell width at its level
+    __shared__ int s_ix[N][GMAX];                  // per parent: child 0's index
     __shared__ uint8_t s_bad[GMAX];
     __shared__ uint32_t s_dig[PMAX];               // digits of a parent-lattice point, 5 bits each
     __shared__ int s_soff[MAXS], s_coff[NC];
@@ -367,16 +373,20 @@ __global__ void __launch_bounds__(PF_THREADS) k_propf_sib(const InstDesc *__rest
         for (int d = 0; d < N; d++) off += ((cc >> (N - 1 - d)) & 1) * k1 * stride[d];
         s_coff[cc] = off;
     }
-    // the parents' bounds, which the bound kernel left in child 0's slot
+    // the parents' bounds, which the bound kernel left in child 0's slot, and
+    // child 0's index and level width (read once here, not at every point)
     for (int g = threadIdx.x; g < G; g += PF_THREADS) {
         const int node0 = I.live[I.fresh0 + ((g0 + g) << N)];   // child 0: index 2 * parent index
         const int64_t q0 = (int64_t)node0 * I.nu + u;
+        const int L = I.lvl[node0];
         bool bad = false;
 #pragma unroll
         for (int d = 0; d < N; d++) {
             const float e = I.box32[q0 * 4 * N + d];
             bad = bad || !(e <= FLT_MAX);
             s_E[d][g] = e;
+            s_ix[d][g] = I.idx[d][node0];
+            s_w[d][g] = I.w32[L][d];
         }
         s_bad[g] = bad;
     }
@@ -384,14 +394,13 @@ __global__ void __launch_bounds__(PF_THREADS) k_propf_sib(const InstDesc *__rest
     for (int pt = threadIdx.x; pt < G * pts1; pt += PF_THREADS) {
         const int g = (int)fdiv((uint32_t)pt, mpts);
         const uint32_t dig = s_dig[pt - g * pts1];
-        const int node0 = I.live[I.fresh0 + ((g0 + g) << N)];
-        const int L = I.lvl[node0];
         float x[N], y[N];
 #pragma unroll
         for (int d = 0; d < N; d++) {
             const int gd = (int)((dig >> (5 * d)) & 31u);
             const int b = gd >= k1 ? 1 : 0;            // a shared face point from the upper child
-            x[d] = point32(I, L, d, I.idx[d][node0] + b, gd - b * k1);
+            // point32 with child 0's level and index from shared memory
+            x[d] = fmaf(s_w[d][g], (float)(s_ix[d][g] + b) + I.frac32[gd - b * k1], I.lo32[d]);
         }
         step_plain<DY>(I, s_p, u, x, y);
 #pragma unroll
