@@ -95,6 +95,32 @@ __device__ __forceinline__ void step_plain(const InstDesc &I, const float *sp, i
     stepT<DY, OpsF>(P, I.m, I.substeps, I.h32, I.hh32, I.h6_32, x, uu, y);
 }
 
+// The step's constants for one control, read once per block into registers
+// (the sample loops then read no descriptor field per point)
+struct StepC {
+    float uu[MAXN];
+    float h, hh, h6;
+    int m, substeps;
+};
+__device__ __forceinline__ StepC step_consts(const InstDesc &I, int u)
+{
+    StepC c;
+    c.m = I.m;
+#pragma unroll
+    for (int j = 0; j < MAXN; j++) c.uu[j] = j < c.m ? I.u32[u * c.m + j] : 0.0f;
+    c.h = I.h32;
+    c.hh = I.hh32;
+    c.h6 = I.h6_32;
+    c.substeps = I.substeps;
+    return c;
+}
+template <class DY>
+__device__ __forceinline__ void step_plain(const StepC &c, const float *sp, const float *x, float *y)
+{
+    const ParF P{sp};
+    stepT<DY, OpsF>(P, c.m, c.substeps, c.h, c.hh, c.h6, x, c.uu, y);
+}
+
 // box32 of pair q from the computed extremes and E
 template <int N>
 __device__ __forceinline__ void store_box(const InstDesc &I, int64_t q, const float *mn, const float *mx,
@@ -249,6 +275,7 @@ __global__ void __launch_bounds__(PF_THREADS) k_propf_lat(const InstDesc *__rest
         s_soff[s] = off;
     }
     __syncthreads();
+    const StepC sc = step_consts(I, u);
     for (int pt = threadIdx.x; pt < P; pt += PF_THREADS) {
         float x[N], y[N];
         uint32_t r = (uint32_t)pt;
@@ -260,7 +287,7 @@ __global__ void __launch_bounds__(PF_THREADS) k_propf_lat(const InstDesc *__rest
             const int idx = min(g / k1, I.n0[d] - 1);
             x[d] = point32(I, 0, d, idx, g - idx * k1);
         }
-        step_plain<DY>(I, s_p, u, x, y);
+        step_plain<DY>(sc, s_p, x, y);
 #pragma unroll
         for (int d = 0; d < N; d++) s_y[d][pt] = y[d];
     }
@@ -322,6 +349,7 @@ __global__ void __launch_bounds__(PF_THREADS) k_propf_sib(const InstDesc *__rest
     __shared__ float s_E[N][GMAX];
     __shared__ float s_w[N][GMAX];                 // per parent: cell width at its level
     __shared__ int s_ix[N][GMAX];                  // per parent: child 0's index
+    __shared__ float s_fr[MAXK];                   // sample fractions j / (k - 1)
     __shared__ uint8_t s_bad[GMAX];
     __shared__ uint32_t s_dig[PMAX];               // digits of a parent-lattice point, 5 bits each
     __shared__ int s_soff[MAXS], s_coff[NC];
@@ -373,6 +401,7 @@ __global__ void __launch_bounds__(PF_THREADS) k_propf_sib(const InstDesc *__rest
         for (int d = 0; d < N; d++) off += ((cc >> (N - 1 - d)) & 1) * k1 * stride[d];
         s_coff[cc] = off;
     }
+    for (int j = threadIdx.x; j < I.k; j += PF_THREADS) s_fr[j] = I.frac32[j];
     // the parents' bounds, which the bound kernel left in child 0's slot, and
     // child 0's index and level width (read once here, not at every point)
     for (int g = threadIdx.x; g < G; g += PF_THREADS) {
@@ -391,6 +420,10 @@ __global__ void __launch_bounds__(PF_THREADS) k_propf_sib(const InstDesc *__rest
         s_bad[g] = bad;
     }
     __syncthreads();
+    const StepC sc = step_consts(I, u);
+    float lo[N];
+#pragma unroll
+    for (int d = 0; d < N; d++) lo[d] = I.lo32[d];
     for (int pt = threadIdx.x; pt < G * pts1; pt += PF_THREADS) {
         const int g = (int)fdiv((uint32_t)pt, mpts);
         const uint32_t dig = s_dig[pt - g * pts1];
@@ -400,9 +433,9 @@ __global__ void __launch_bounds__(PF_THREADS) k_propf_sib(const InstDesc *__rest
             const int gd = (int)((dig >> (5 * d)) & 31u);
             const int b = gd >= k1 ? 1 : 0;            // a shared face point from the upper child
             // point32 with child 0's level and index from shared memory
-            x[d] = fmaf(s_w[d][g], (float)(s_ix[d][g] + b) + I.frac32[gd - b * k1], I.lo32[d]);
+            x[d] = fmaf(s_w[d][g], (float)(s_ix[d][g] + b) + s_fr[gd - b * k1], lo[d]);
         }
-        step_plain<DY>(I, s_p, u, x, y);
+        step_plain<DY>(sc, s_p, x, y);
 #pragma unroll
         for (int d = 0; d < N; d++) s_y[d][pt] = y[d];
     }
