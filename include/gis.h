@@ -420,7 +420,7 @@ void gis_shard_destroy(gis_shard *sh);   /* NULL-safe */
  * This is the layout gis_get_graph returns. Sizes above GIS_NOALLOC_MAX_* are
  * rejected with GIS_EUNSUPPORTED before any work is queued. The first call on
  * a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture. The
+ * that device current. The
  * address is cached per device and looked up again when the device's context
  * has changed (after a cudaDeviceReset the next call is again such a first
  * call). Every call uses the same array, so calls that overlap on the GPU
