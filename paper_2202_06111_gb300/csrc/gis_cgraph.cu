@@ -60,7 +60,7 @@ cudaError_t launch_cgather(const InstDesc *D, const WorkList &w, int32_t *cps, i
 }
 
 constexpr int CE_WARPS = 8;      // cells (warps) per block
-constexpr int CE_TAB = 512;      // per-warp tables of control sets per dimension (entries)
+constexpr int CE_TAB = 256;      // per-warp tables of control sets per dimension (entries)
 constexpr int CE_GRAB = 4;       // fewest chunks a warp takes at a time
 constexpr int CE_EB = CE_EB_HOST;   // staged edges a warp buffers in shared memory
 #ifndef CE_MINB
@@ -567,8 +567,23 @@ __global__ void __launch_bounds__(CE_WARPS * 32, CE_MINB) k_cedges(const InstDes
                     } else {
                         child_masks<N>(box, nu, m, idx, Lf - L - 1, md);
                     }
+                    if (N == 4) {
+                        // child (h0 h1 h2 h3) = the pair (h0 h1) of dimensions 0-1
+                        // with the pair (h2 h3) of dimensions 2-3
+                        uint32_t a[4], b[4];
 #pragma unroll
-                    for (int cc = 0; cc < (1 << N); cc++) cmap |= (uint32_t)(child_mask<N>(md, cc) != 0u) << cc;
+                        for (int i = 0; i < 4; i++) {
+                            a[i] = md[0][i >> 1] & md[1 % N][i & 1];
+                            b[i] = md[2 % N][i >> 1] & md[3 % N][i & 1];
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; i++)
+#pragma unroll
+                            for (int j = 0; j < 4; j++) cmap |= (uint32_t)((a[i] & b[j]) != 0u) << (4 * i + j);
+                    } else {
+#pragma unroll
+                        for (int cc = 0; cc < (1 << N); cc++) cmap |= (uint32_t)(child_mask<N>(md, cc) != 0u) << cc;
+                    }
                     push = cmap != 0;
                 } else if (m && st == ST_DEAD) {
                     tch |= m;

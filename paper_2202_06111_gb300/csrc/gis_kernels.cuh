@@ -168,7 +168,7 @@ struct ChunkWork {
 // scatters the reverse edges. *top counts every edge (also past cap); when
 // stg or seg runs out, *over is set and the chunk is marked in lost[] (its
 // segments are skipped and the fill walks it again).
-constexpr int CE_EB_HOST = 256;  // edges a warp buffers before a flush (CE_EB)
+constexpr int CE_EB_HOST = 128;  // edges a warp buffers before a flush (CE_EB)
 struct SegRec {
     long long pos;
     int32_t chunk, soff, len, cell;
