@@ -78,7 +78,7 @@ __device__ __forceinline__ int warp_max(int v) { return __reduce_max_sync(0xffff
 // max(1, ceil(roots / CE_CHUNK)) chunks; the exclusive scan of these counts
 // numbers the chunks of a run of cells contiguously. Cells carried over from
 // the previous level have no chunks (k_cinc builds their edges).
-constexpr int64_t CE_CHUNK = 64;
+constexpr int64_t CE_CHUNK = 256;
 
 // One thread per cell, over its controls: the union box needs a few loads and
 // compares per control, so one lane per control left most of a warp idle and

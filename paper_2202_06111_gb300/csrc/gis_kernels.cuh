@@ -164,7 +164,7 @@ struct ChunkWork {
 // Edges staged by the count pass, so that one walk serves both passes: a
 // warp collects its chunk's edges in shared memory and flushes them to stg
 // (target | mask << 32) as a segment (chunk, offset in the chunk, position,
-// length); the place pass then copies every segment to its CSR position and
+// length, the chunk's cell); the place pass then copies every segment to its CSR position and
 // scatters the reverse edges. *top counts every edge (also past cap); when
 // stg or seg runs out, *over is set and the chunk is marked in lost[] (its
 // segments are skipped and the fill walks it again).
@@ -184,7 +184,8 @@ struct StageArgs {
     uint8_t *lost = nullptr;     // per chunk, zeroed
 };
 cudaError_t launch_place(const int64_t *cbase, const int32_t *chk_cell, const int64_t *chk_off, int64_t nchunks,
-                         int64_t ncells, const StageArgs &sa, bool any_lost, int64_t nseg, const CellGraph &g, cudaStream_t st);
+                         int64_t ncells, const StageArgs &sa, bool any_lost, int64_t nseg, const CellGraph &g,
+                         cudaStream_t st);
 // the cell of each chunk; zeroes the per-cell counts ccnt and rcnt and, with
 // lost, the chunks' lost marks
 cudaError_t launch_cexpand(const int64_t *cbase, int64_t NL, const ChunkWork &cw, int32_t *ccnt, int32_t *rcnt,

@@ -154,6 +154,20 @@ def test_split_rings_4d(gis):
     run_both(gis, dict(W.cartpole_48(levels=1, n0=5), rule="outer", split_ring=1), 1)
 
 
+def test_cells_of_several_chunks(gis):
+    """Union boxes wider than one chunk of root cells (and wider than the walk's
+    control-mask tables): controls that shift the image far apart along a
+    diagonal, and an expanding 1-D map. The walk cuts such a cell into several
+    chunks whose edges are concatenated per cell."""
+    eye = [[1.0, 0.0], [0.0, 1.0]]
+    prob = W.problem(W.linmap(eye, eye), [-1.0, -1.0], [1.0, 1.0], 64, 2,
+                     [[-0.5, -0.5], [0.0, 0.0], [0.5, 0.5]], 1.0, 0, levels=2, rule="outer", precision="fp32")
+    run_both(gis, prob, 2)
+    prob = W.problem(W.linmap([[300.0]], [[1.0]]), [-1.0], [1.0], 1024, 2, [[0.0], [0.3]], 1.0, 0, levels=2,
+                     rule="outer", precision="fp32")
+    run_both(gis, prob, 2)
+
+
 def test_everything_leaves(gis):
     """x+ = 2x + 3: every image leaves X, nothing is kept, no split."""
     prob = W.problem(W.linmap([[2.0]], [[1.0]]), [-1.0], [1.0], 16, 2, [[3.0]], 1.0, 0, precision="fp32")
