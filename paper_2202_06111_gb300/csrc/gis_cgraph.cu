@@ -59,12 +59,12 @@ cudaError_t launch_cgather(const InstDesc *D, const WorkList &w, int32_t *cps, i
     return cudaGetLastError();
 }
 
-constexpr int CE_WARPS = 8;      // cells (warps) per block
+constexpr int CE_WARPS = 4;      // cells (warps) per block
 constexpr int CE_TAB = 256;      // per-warp tables of control sets per dimension (entries)
 constexpr int CE_GRAB = 4;       // fewest chunks a warp takes at a time
 constexpr int CE_EB = CE_EB_HOST;   // staged edges a warp buffers in shared memory
 #ifndef CE_MINB
-#define CE_MINB 3                // blocks per SM the walk's registers are sized for
+#define CE_MINB 6                // blocks per SM the walk's registers are sized for
 #endif
 
 // one redux instruction each (integer warp reductions, sm_80 and later)
