@@ -59,7 +59,9 @@ cudaError_t launch_cgather(const InstDesc *D, const WorkList &w, int32_t *cps, i
     return cudaGetLastError();
 }
 
-constexpr int CE_WARPS = 4;      // cells (warps) per block
+constexpr int CE_WARPS = 4;      // cells (warps) per block of the walk
+constexpr int CI_WARPS = 4;      // cells (warps) per block of the carried cells' edges
+constexpr int PL_WARPS = 8;      // staged segments (warps) per block of the place pass
 constexpr int CE_TAB = 256;      // per-warp tables of control sets per dimension (entries)
 constexpr int CE_GRAB = 4;       // fewest chunks a warp takes at a time
 constexpr int CE_EB = CE_EB_HOST;   // staged edges a warp buffers in shared memory
@@ -671,7 +673,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32, CE_MINB) k_cedges(const InstDes
 // (rcnt), removed-leaf flags, pair-edge total. FILL = true: edges at coff[cell]
 // (cent, cmask) and reverse edges at rcur[target]++ (rev).
 template <int N, bool FILL>
-__global__ void __launch_bounds__(CE_WARPS * 32) k_cinc(const InstDesc *__restrict__ D, const Range *__restrict__ R,
+__global__ void __launch_bounds__(CI_WARPS * 32) k_cinc(const InstDesc *__restrict__ D, const Range *__restrict__ R,
                                                        int nr, const int32_t *__restrict__ rng,
                                                        uint8_t *__restrict__ pflag, int32_t *__restrict__ pcnt,
                                                        int32_t *__restrict__ ccnt, int32_t *__restrict__ rcnt,
@@ -685,11 +687,11 @@ __global__ void __launch_bounds__(CE_WARPS * 32) k_cinc(const InstDesc *__restri
 {
     constexpr uint32_t FULL = 0xffffffffu;
     constexpr int NC = 1 << N;
-    __shared__ CtlBox<N> s_box[CE_WARPS][32];
-    CRANGE_HEAD(CE_WARPS)
+    __shared__ CtlBox<N> s_box[CI_WARPS][32];
+    CRANGE_HEAD(CI_WARPS)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
-    const int64_t local = (int64_t)(blockIdx.x - rg.block_start) * CE_WARPS + warp;
+    const int64_t local = (int64_t)(blockIdx.x - rg.block_start) * CI_WARPS + warp;
     if (local >= rg.count) return;                 // whole warp
     const int64_t s = rg.first + local;
     const int ls = (int)(s - I.slot_base);
@@ -825,7 +827,7 @@ cudaError_t launch_cinc(bool fill, int n, const InstDesc *D, const WorkList &w, 
                         const CellPrev &prev, cudaStream_t st)
 {
     if (w.n_blocks == 0) return cudaSuccess;
-    dim3 gr((unsigned)w.n_blocks), b(CE_WARPS * 32);
+    dim3 gr((unsigned)w.n_blocks), b(CI_WARPS * 32);
 #define CI_CASE(NN)                                                                                          \
     case NN:                                                                                                 \
         if (fill)                                                                                            \
@@ -912,7 +914,7 @@ cudaError_t launch_cedges(bool fill, int n, int depth, const InstDesc *D, int64_
 // position (the cell's offset, plus the edges of the cell's earlier chunks,
 // plus the segment's offset in its chunk) and scatters the reverse edges at
 // rcur[target]++.
-__global__ void __launch_bounds__(256) k_place(const int64_t *__restrict__ cbase,
+__global__ void __launch_bounds__(PL_WARPS * 32) k_place(const int64_t *__restrict__ cbase,
                                                const int32_t *__restrict__ chk_cell,
                                                const int64_t *__restrict__ chk_off,
                                                const unsigned long long *__restrict__ stg,
@@ -924,7 +926,7 @@ __global__ void __launch_bounds__(256) k_place(const int64_t *__restrict__ cbase
                                                uint2 *__restrict__ rev)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int64_t w = (int64_t)blockIdx.x * PL_WARPS + (threadIdx.x >> 5);
     if (w >= nseg) return;
     const SegRec r = seg[w];
     if (r.chunk < 0 || r.chunk >= nchunks || r.len < 0 || r.len > CE_EB) {
@@ -967,7 +969,7 @@ cudaError_t launch_place(const int64_t *cbase, const int32_t *chk_cell, const in
 {
     nseg = std::min(nseg, sa.seg_cap);            // the counter also counts records that found no slot
     if (nseg <= 0) return cudaSuccess;
-    k_place<<<(unsigned)((nseg + 7) / 8), 256, 0, st>>>(cbase, chk_cell, chk_off, sa.stg, nchunks, ncells, sa.seg,
+    k_place<<<(unsigned)((nseg + PL_WARPS - 1) / PL_WARPS), PL_WARPS * 32, 0, st>>>(cbase, chk_cell, chk_off, sa.stg, nchunks, ncells, sa.seg,
                                                         nseg,
                                                         any_lost ? sa.lost : nullptr, g.ecap, g.err, g.coff, g.cent,
                                                         g.cmask, g.rcur, g.rev);
@@ -1007,7 +1009,7 @@ cudaError_t launch_cexpand(const int64_t *cbase, int64_t NL, const ChunkWork &cw
     return cudaGetLastError();
 }
 
-int cedges_cells_per_block() { return CE_WARPS; }
+int cedges_cells_per_block() { return CI_WARPS; }
 
 // ---------------------------------------------------------------------------
 // Prune on the cell graph. A cell dies when no control is left viable:
