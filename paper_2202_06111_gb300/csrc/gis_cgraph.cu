@@ -287,6 +287,10 @@ __global__ void __launch_bounds__(CE_WARPS * 32, CE_MINB) k_cedges(const InstDes
     constexpr uint32_t FULL = 0xffffffffu;
     __shared__ CtlBox<N> s_box[CE_WARPS][32];
     __shared__ uint32_t s_tab[CE_WARPS][CE_TAB];
+    // the cell's per-dimension constants, warp-uniform, kept here instead of in
+    // registers: grid size n0, union-box corner ua and extent ext (level 0),
+    // table offset toff
+    __shared__ int s_cc[CE_WARPS][4][N];
     extern __shared__ uint32_t s_walk[];
     uint2 *const eb = (uint2 *)(s_walk + (size_t)CE_WARPS * S * walk_words(N)) + (threadIdx.x >> 5) * CE_EB;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -306,11 +310,10 @@ __global__ void __launch_bounds__(CE_WARPS * 32, CE_MINB) k_cedges(const InstDes
     const InstDesc *Ip = D;
     int ls = 0, nu = 0, Lf = 0;
     int64_t p = 0, nroots = 0, cb = 0, ce = 0;
-    int n0[N], ua[N], ext[N], toff[N];
+    int (*const cn0)[N] = &s_cc[warp][0], (*const cua)[N] = &s_cc[warp][1];
+    int (*const cext)[N] = &s_cc[warp][2], (*const ctoff)[N] = &s_cc[warp][3];
     uint32_t live = 0;
     bool use_tab = false;
-#pragma unroll
-    for (int d = 0; d < N; d++) n0[d] = ua[d] = ext[d] = toff[d] = 0;
     const int64_t nw8 = 8 * (int64_t)gridDim.x * CE_WARPS;
     int64_t seen = 0;                              // lane 0: the counter as last seen
     for (;;) {
@@ -336,6 +339,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32, CE_MINB) k_cedges(const InstDes
         nu = I.nu;
         Lf = I.Lf;
         p = I.pair_base + (int64_t)ls * nu + lane;
+        int n0[N], ua[N], ext[N], toff[N];
 #pragma unroll
         for (int d = 0; d < N; d++) n0[d] = I.n0[d];
         // control `lane`: finest-level decisions, level-0 box
@@ -386,6 +390,15 @@ __global__ void __launch_bounds__(CE_WARPS * 32, CE_MINB) k_cedges(const InstDes
             toff[d] = tsum;
             tsum += live ? 2 * ((ext[d] << Lf) + 1) : 0;
         }
+        if (lane == 0) {
+#pragma unroll
+            for (int d = 0; d < N; d++) {
+                (*cn0)[d] = n0[d];
+                (*cua)[d] = ua[d];
+                (*cext)[d] = ext[d];
+                (*ctoff)[d] = toff[d];
+            }
+        }
         use_tab = live && tsum <= CE_TAB;
         if (use_tab) {
             uint32_t *tab = s_tab[warp];
@@ -405,6 +418,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32, CE_MINB) k_cedges(const InstDes
             }
             __syncwarp();
         }
+        __syncwarp();                              // the cell's constants are in s_cc
         cb = cbase[s];
         ce = cbase[s + 1];
         }
@@ -501,22 +515,22 @@ __global__ void __launch_bounds__(CE_WARPS * 32, CE_MINB) k_cedges(const InstDes
                         uint32_t q = (uint32_t)rr;
 #pragma unroll
                         for (int d = N - 1; d > 0; d--) {
-                            const uint32_t qq = q / (uint32_t)ext[d];
-                            idx[d] = ua[d] + (int)(q - qq * (uint32_t)ext[d]);
+                            const uint32_t qq = q / (uint32_t)(*cext)[d];
+                            idx[d] = (*cua)[d] + (int)(q - qq * (uint32_t)(*cext)[d]);
                             q = qq;
                         }
-                        idx[0] = ua[0] + (int)q;
+                        idx[0] = (*cua)[0] + (int)q;
                     } else {
                         int64_t q = rr;
 #pragma unroll
                         for (int d = N - 1; d >= 0; d--) {
-                            idx[d] = ua[d] + (int)(q % ext[d]);
-                            q /= ext[d];
+                            idx[d] = (*cua)[d] + (int)(q % (*cext)[d]);
+                            q /= (*cext)[d];
                         }
                     }
                     int r = 0;
 #pragma unroll
-                    for (int d = 0; d < N; d++) r = r * n0[d] + idx[d];
+                    for (int d = 0; d < N; d++) r = r * (*cn0)[d] + idx[d];
                     node = r;
                     root = true;
                 }
@@ -541,7 +555,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32, CE_MINB) k_cedges(const InstDes
                         const uint32_t *tab = s_tab[warp];
 #pragma unroll
                         for (int d = 0; d < N; d++) {
-                            const int r = 2 * ((idx[d] - ua[d]) << Lf) + toff[d];
+                            const int r = 2 * ((idx[d] - (*cua)[d]) << Lf) + (*ctoff)[d];
                             m &= tab[r + (2 << Lf)] & tab[r + 1];
                         }
                     } else {
@@ -561,7 +575,7 @@ __global__ void __launch_bounds__(CE_WARPS * 32, CE_MINB) k_cedges(const InstDes
                         const int sh = Lf - L - 1;
 #pragma unroll
                         for (int d = 0; d < N; d++) {
-                            const int r = toff[d] + 2 * ((2 * idx[d] - (ua[d] << (L + 1))) << sh);
+                            const int r = (*ctoff)[d] + 2 * ((2 * idx[d] - ((*cua)[d] << (L + 1))) << sh);
                             const int w = 2 << sh;
                             md[d][0] = tab[r + w] & tab[r + 1] & m;
                             md[d][1] = tab[r + 2 * w] & tab[r + w + 1] & m;
